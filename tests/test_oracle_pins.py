@@ -1,0 +1,270 @@
+"""Pins of the CPU oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the paper's
+printed Gauss-Legendre table (Fig. 2 caption), exactness of Gauss quadrature,
+closed forms of the contour filter, the V = 0 tensor-product spectrum, the
+spectral form of Q from a dense pencil eigendecomposition, LAPACK/SuperLU on
+tiny inputs, Sylvester inertia and the k-fold multiplicity construction of
+Sec. IV.B.
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+
+import oracle
+import workloads
+from conftest import GOLDEN
+
+
+def _paper_gl8():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "gl8_paper.txt")) if l.strip() and not l.startswith("#")]
+    return {int(r[0]): (float(r[1]), float(r[2])) for r in rows}
+
+
+# ---------------------------------------------------------------- quadrature
+
+def test_gl8_matches_paper_table():
+    """Fig. 2 caption: the printed Ne = 8 nodes/weights (15 digits)."""
+    x, w = oracle.gauss_legendre(8)
+    tab = _paper_gl8()
+    for i, (xp, wp) in tab.items():
+        assert abs(x[i - 1] - xp) < 2e-15, (i, x[i - 1], xp)
+        assert abs(w[i - 1] - wp) < 2e-15
+        assert x[i] == -x[i - 1] and w[i] == w[i - 1]   # x_{2i} = -x_{2i-1}
+
+
+@pytest.mark.parametrize("Ne", [1, 2, 3, 4, 5, 8, 12, 16])
+def test_gauss_legendre_exact_on_polynomials(Ne):
+    """An Ne-point Gauss rule integrates x^k exactly for k <= 2 Ne - 1."""
+    x, w = oracle.gauss_legendre(Ne)
+    assert len(x) == Ne and np.all(np.abs(x) < 1)
+    for k in range(2 * Ne):
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert abs(np.dot(w, x ** k) - exact) < 1e-14
+    # and not for k = 2 Ne (the rule has degree exactly 2 Ne - 1)
+    assert abs(np.dot(w, x ** (2 * Ne)) - 2.0 / (2 * Ne + 1)) > 1e-12
+
+
+def test_contour_points_on_upper_half_circle():
+    """Eqs. 13-14: Z_e = c + r e^{i theta_e}, theta_e in (0, pi)."""
+    lmin, lmax = 3.0, 11.0
+    x, w, theta, Z, r = oracle.contour_points(lmin, lmax, 8)
+    assert r == 4.0
+    assert np.allclose(np.abs(Z - 7.0), 4.0, atol=1e-14, rtol=0)
+    assert np.all(Z.imag > 0) and np.all((theta > 0) & (theta < math.pi))
+    assert np.allclose(theta, (math.pi / 2) * (1 - x))
+
+
+def test_filter_closed_forms():
+    """The rational filter of Eq. 15: f = -1 at the centre (each node term
+    reduces to w_e/2), f(c + r t) + f(c + r/t) = -1 (so -1/2 at both ends),
+    f symmetric about the centre, small far outside the interval."""
+    lmin, lmax = -2.0, 6.0
+    c, r = 2.0, 4.0
+    f = lambda lam: oracle.filter_value(np.array([lam]), lmin, lmax, 8)[0]  # noqa: E731
+    assert abs(f(c) + 1.0) < 1e-15
+    assert abs(f(lmin) + 0.5) < 1e-14 and abs(f(lmax) + 0.5) < 1e-14
+    for d in (0.3, 1.7, 3.9, 5.0, 9.0):
+        assert abs(f(c + d) - f(c - d)) < 1e-14
+    # inversion through the circle: with u = e^{i theta} on the unit circle,
+    # Re{u/(u - t)} + Re{u/(u - 1/t)} = 1 for real t != 0, so summing the node
+    # terms with sum_e w_e = 2 gives f(c + r t) + f(c + r/t) = -1 exactly
+    for t in (0.2, 0.5, 0.9, -0.7, 1.3, -3.0):
+        assert abs(f(c + r * t) + f(c + r / t) + 1.0) < 1e-13
+    assert abs(f(c + 2 * r)) < 1e-4 and abs(f(c + 3 * r)) < 1e-6
+
+
+# ---------------------------------------------------------------- operators
+
+def test_v0_spectrum_closed_form_matches_dense_pencil():
+    """Assembled Q1 operator at V = 0 vs the tensor-product closed form: two
+    independent derivations of the same spectrum."""
+    for (nx, ny, nz) in [(3, 4, 5), (5, 5, 3), (2, 3, 7)]:
+        op = workloads.q1_operator(nx, ny, nz)
+        lam = oracle.dense_generalized_eigh(op)[0]
+        cf = oracle.closed_form_eigenvalues_v0(nx, ny, nz)
+        assert np.allclose(lam, cf, rtol=1e-12, atol=0)
+
+
+def test_operator_symmetric_and_B_spd():
+    op = workloads.q1_operator(4, 3, 5, workloads.gaussian_potential(4, 7, 4, 3, 5))
+    A = oracle.assemble(op.A27, 4, 3, 5).toarray()
+    B = oracle.assemble(op.B27, 4, 3, 5).toarray()
+    assert np.abs(A - A.T).max() < 1e-14 and np.abs(B - B.T).max() < 1e-15
+    assert np.linalg.eigvalsh(B).min() > 0
+
+
+# ---------------------------------------------------------------- step 2
+
+def _tiny():
+    op = workloads.q1_operator(4, 3, 6, workloads.gaussian_potential(3, 11, 4, 3, 6))
+    A = oracle.assemble(op.A27, 4, 3, 6)
+    B = oracle.assemble(op.B27, 4, 3, 6)
+    return op, A, B
+
+
+def test_block_tridiag_solve_matches_sparse_lu():
+    """Node solve (Fig. 2 step 2) vs SuperLU on the assembled complex matrix,
+    and its residual via the independent sparse product."""
+    op, A, B = _tiny()
+    rng = np.random.default_rng(3)
+    Z = 30.0 + 4.5j
+    M = (Z * B - A).astype(np.complex128)
+    rhs = rng.standard_normal((op.N, 5))
+    fac = oracle.block_tridiag_factor(M, op.n, op.nz)
+    q = fac.solve(rhs.astype(np.complex128))
+    ref = spla.splu(M.tocsc()).solve(rhs.astype(np.complex128))
+    assert np.abs(q - ref).max() / np.abs(ref).max() < 1e-12
+    assert np.abs(M @ q - rhs).max() / np.abs(rhs).max() < 1e-12
+
+
+def test_quadrature_matches_spectral_form():
+    """Eq. 15 on a tiny pencil equals Q = X f(Lambda) X^T RHS, with X, Lambda
+    from the dense LAPACK pencil solve and f the scalar filter."""
+    op, A, B = _tiny()
+    lam, X = oracle.dense_generalized_eigh(op)
+    lmin, lmax = lam[2] - 0.3, 0.5 * (lam[7] + lam[8])
+    rhs = np.random.default_rng(5).standard_normal((op.N, 4))
+    Q, _ = oracle.quadrature_subspace(A, B, rhs, lmin, lmax, 8, op.n, op.nz)
+    f = oracle.filter_value(lam, lmin, lmax, 8)
+    Qref = X @ (f[:, None] * (X.T @ rhs))
+    assert np.abs(Q - Qref).max() / np.abs(Qref).max() < 1e-12
+
+
+# ---------------------------------------------------------------- steps 3-5
+
+def test_rayleigh_ritz_2x2_closed_form():
+    """A 2x2 reduced problem: eigenvalues of B^{-1}A from the characteristic
+    polynomial det(A - eps B) = 0 written out by hand."""
+    AQ = np.array([[2.0, 1.0], [1.0, 3.0]])
+    BQ = np.array([[2.0, 0.5], [0.5, 1.0]])
+    a = np.linalg.det(BQ)
+    b = -(AQ[0, 0] * BQ[1, 1] + AQ[1, 1] * BQ[0, 0] - 2 * AQ[0, 1] * BQ[0, 1])
+    c = np.linalg.det(AQ)
+    disc = math.sqrt(b * b - 4 * a * c)
+    roots = sorted([(-b - disc) / (2 * a), (-b + disc) / (2 * a)])
+    eps, Phi = sla.eigh(AQ, BQ)
+    assert np.allclose(eps, roots, rtol=1e-14)
+    assert np.allclose(Phi.T @ BQ @ Phi, np.eye(2), atol=1e-14)
+
+
+# ---------------------------------------------------------------- full loop
+
+def _interval(intervals, key):
+    iv = intervals[key]
+    return iv["lmin"], iv["lmax"], iv["M"]
+
+
+def test_feast_v0_matches_closed_form(intervals):
+    """cfg 10x10x20 at V = 0: the M eigenvalues equal the tensor-product closed
+    form to 1e-12 relative; the count equals the inertia count."""
+    wl = workloads.WORKLOADS["q1_10x10x20_fp64"]
+    op = wl.operator(0, zero_potential=True)
+    lmin, lmax, M = _interval(intervals, "q1_10x10x20/v0")
+    res = oracle.feast(op, lmin, lmax, wl.M0, wl.Ne, workloads.random_Y(op.N, wl.M0, 1000), tol=wl.tol)
+    cf = oracle.closed_form_eigenvalues_v0(10, 10, 20)
+    assert res.converged and res.m_found == M
+    assert np.allclose(res.lam[:M], cf[:M], rtol=1e-12, atol=0)
+    assert res.resid[:M].max() < 1e-12
+    assert oracle.inertia_count(op, lmax) - oracle.inertia_count(op, lmin) == M
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_feast_matches_dense_pencil(intervals, seed):
+    """cfg 10x10x20 with a Gaussian potential: eigenvalues vs the dense LAPACK
+    pencil to 1e-12; X B-orthonormal (Eq. 9 / Sec. III.A); residual <= 1e-10;
+    the trace change falls loop over loop (Table II behaviour)."""
+    wl = workloads.WORKLOADS["q1_10x10x20_fp64"]
+    op = wl.operator(seed)
+    lmin, lmax, M = _interval(intervals, f"q1_10x10x20/seed{seed}")
+    res = oracle.feast(op, lmin, lmax, wl.M0, wl.Ne, workloads.random_Y(op.N, wl.M0, 1000 + seed), tol=wl.tol)
+    lam = oracle.dense_generalized_eigh(op)[0]
+    assert res.m_found == M and res.converged
+    assert np.allclose(res.lam[:M], lam[:M], rtol=1e-12, atol=0)
+    B = oracle.assemble(op.B27, 10, 10, 20)
+    X = res.X[:, :M]
+    assert np.abs(X.T @ (B @ X) - np.eye(M)).max() < 1e-12
+    assert res.resid[:M].max() < 1e-10
+    ch = res.rel_change_history
+    assert all(b < a for a, b in zip(ch, ch[1:])) or ch[-1] < 1e-13
+    # Courant-Fischer: Ritz values of any subspace are >= the true ones
+    assert np.all(res.lam[:M] >= lam[:M] - 1e-12 * np.abs(lam[:M]))
+
+
+def test_inertia_count_matches_dense_eigenvalues():
+    op = workloads.q1_operator(4, 5, 6, workloads.gaussian_potential(5, 2, 4, 5, 6))
+    lam = oracle.dense_generalized_eigh(op)[0]
+    for sigma in (lam[0] - 1.0, 0.5 * (lam[3] + lam[4]), 0.5 * (lam[40] + lam[41]), lam[-1] + 1):
+        assert oracle.inertia_count(op, sigma) == int((lam < sigma).sum())
+
+
+def test_k_copies_give_k_fold_multiplicity():
+    """Sec. IV.B, k(N, M): block-diagonal copies make every eigenvalue k-fold
+    and FEAST finds k M pairs in the unchanged interval."""
+    blk = workloads.q1_operator(4, 4, 5, workloads.gaussian_potential(3, 9, 4, 4, 5))
+    lam1 = oracle.dense_generalized_eigh(blk)[0]
+    M = 6
+    lmin, lmax = lam1[0] - 0.5, 0.5 * (lam1[M - 1] + lam1[M])
+    k = 2
+    rep = workloads.replicate_z(blk, k)
+    res = oracle.feast(rep, lmin, lmax, 16, 8, workloads.random_Y(rep.N, 16, 77), tol=1e-12)
+    assert res.m_found == k * M
+    got = np.sort(res.lam[:k * M]).reshape(M, k)
+    assert np.allclose(got, np.repeat(lam1[:M, None], k, axis=1), rtol=1e-11, atol=0)
+
+
+def test_bq_not_spd_when_m0_too_large():
+    """Sec. III.B (ii): far more vectors than eigenvalues in a narrow interval
+    drive B_Q's smallest eigenvalue below the 1e-14 ratio."""
+    op = workloads.q1_operator(5, 5, 6)
+    lam = oracle.closed_form_eigenvalues_v0(5, 5, 6)
+    lmin, lmax = lam[0] - 0.1, 0.5 * (lam[0] + lam[1])
+    with pytest.raises(oracle.BQNotSPD):
+        oracle.feast(op, lmin, lmax, 60, 8, workloads.random_Y(op.N, 60, 1), tol=1e-12)
+
+
+# ---------------------------------------------------------------- planted mistakes
+
+def test_pins_catch_planted_mistakes(monkeypatch):
+    """Plant plausible mistakes in the oracle (on the CPU) and check that a pin
+    fails for each: a dropped 1/2 in Eq. 15, a wrong contour centre in Eq. 14,
+    a dropped factor r, the imaginary instead of the real part.  (Reflecting
+    the nodes to the lower half circle is not a mistake for real symmetric A:
+    G(conj Z) = conj G(Z) leaves the real part of Eq. 15 unchanged.)"""
+    op, A, B = _tiny()
+    lam, X = oracle.dense_generalized_eigh(op)
+    lmin, lmax = lam[2] - 0.3, 0.5 * (lam[7] + lam[8])
+    rhs = np.random.default_rng(5).standard_normal((op.N, 4))
+    f = oracle.filter_value(lam, lmin, lmax, 8)
+    Qref = X @ (f[:, None] * (X.T @ rhs))
+    import oracle.feast_oracle as fo
+
+    def err_with(patched_contour=None, part="real", scale=2.0):
+        orig = fo.contour_points
+
+        def contour(lmin_, lmax_, Ne_):
+            x, w, th, Z, r = orig(lmin_, lmax_, Ne_)
+            if patched_contour:
+                return patched_contour(x, w, th, Z, r)
+            return x, w, th, Z, r
+        monkeypatch.setattr(fo, "contour_points", contour)
+        try:
+            Q, _ = fo.quadrature_subspace(A, B, rhs, lmin, lmax, 8, op.n, op.nz)
+        finally:
+            monkeypatch.setattr(fo, "contour_points", orig)
+        return np.abs(Q - Qref).max() / np.abs(Qref).max()
+
+    assert err_with() < 1e-12
+    # dropped 1/2: weights doubled
+    assert err_with(lambda x, w, th, Z, r: (x, 2 * w, th, Z, r)) > 1e-3
+    # centre taken as (lmax - lmin)/2 instead of (lmax + lmin)/2 in Eq. 14
+    assert err_with(lambda x, w, th, Z, r: (x, w, th, Z - (lmax + lmin) / 2 + r, r)) > 1e-3
+    # factor r dropped from Eq. 15
+    assert err_with(lambda x, w, th, Z, r: (x, w, th, Z, 1.0)) > 1e-3
+    # rotated phase (e^{i theta} -> i e^{i theta} picks the imaginary part)
+    assert err_with(lambda x, w, th, Z, r: (x, w, th + math.pi / 2, Z, r)) > 1e-3
