@@ -1,0 +1,218 @@
+/*
+ * feast.h -- C-ABI of the GB300 FEAST eigensolver library (libfeast_gb300.so).
+ *
+ * FEAST (Polizzi, arXiv:0901.2665) finds every eigenpair (lambda, x) of the
+ * generalized problem A x = lambda B x with lambda inside [lmin, lmax], for
+ * real symmetric A and symmetric positive definite B (Sec. III.A, Eq. 2).
+ * Each refinement loop (Fig. 2, steps 2-6):
+ *   - solves the Ne complex shifted systems (Z_e B - A) Q_e = B Y with M0
+ *     right-hand sides at the Gauss-Legendre nodes Z_e of the upper half
+ *     circle around the interval (Eqs. 13-14);
+ *   - accumulates Q = -sum_e (w_e/2) Re{ r e^{i theta_e} Q_e } (Eq. 15);
+ *   - runs Rayleigh-Ritz: A_Q = Q^T A Q, B_Q = Q^T B Q, A_Q Phi = eps B_Q Phi,
+ *     X = Q Phi (Eqs. 6-9);
+ *   - stops on the relative change of the in-interval trace, else Y = X and
+ *     the next right-hand side is B X (Sec. III.B (i)).
+ *
+ * Operators are 27-point layered stencils (see feast_operator).  The linear
+ * systems are block tridiagonal over the z-layers and are solved by an
+ * unpivoted block elimination whose diagonal blocks are inverted explicitly;
+ * the inverses are computed once per node and reused by every loop
+ * (Sec. V, parallelism level (ii)).
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are column-major; N x M0 blocks have leading dimension N.
+ *   - Complex arrays are interleaved (re, im) doubles.
+ *   - Pointers may be host or device memory unless stated otherwise; the
+ *     library inspects each pointer (cudaPointerGetAttributes) and copies host
+ *     data through its own device workspace.  Step-level entry points take
+ *     DEVICE pointers only.
+ *   - The caller owns every buffer it passes; the handle owns its workspace
+ *     and releases it in feast_destroy.
+ *   - All device work is ordered on the stream given to feast_init.  Entry
+ *     points that return host-visible results synchronise that stream.
+ *   - Errors are returned as feast_status; no exception crosses the ABI.
+ *     feast_last_error() gives a message for the last failing call.
+ *   - A handle must not be used by two host threads at once.
+ */
+#ifndef FEAST_GB300_H
+#define FEAST_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct feast_handle feast_handle;
+
+typedef enum {
+  FEAST_OK = 0,
+  FEAST_ERR_ARG = 1,             /* invalid argument (sizes, interval, pointers) */
+  FEAST_ERR_BQ_NOT_SPD = 2,      /* B_Q = Q^T B Q not positive definite: M0 too large
+                                    for the interval (Sec. III.B (ii)) */
+  FEAST_ERR_NO_CONVERGENCE = 3,  /* trace test not met within max_loops; outputs hold
+                                    the last loop's pairs */
+  FEAST_ERR_M0_TOO_SMALL = 4,    /* every Ritz value fell inside the interval: Fig. 2
+                                    step 1 needs M0 > M; outputs hold the last loop */
+  FEAST_ERR_PIVOT = 5,           /* zero or non-finite pivot in a block inversion */
+  FEAST_ERR_OOM = 6,             /* device workspace allocation failed */
+  FEAST_ERR_CUDA = 7,            /* CUDA runtime error */
+  FEAST_ERR_TIMEOUT = 8,         /* a bounded device wait gave up */
+  FEAST_ERR_JACOBI = 9           /* reduced eigensolve did not converge */
+} feast_status;
+
+enum { FEAST_PREC_FP64 = 0, FEAST_PREC_MIXED = 1 };
+
+/*
+ * Layered 27-point operator on an nx x ny x nz interior grid.
+ * Node id i = ix + nx*(iy + ny*iz); layer iz holds the n = nx*ny unknowns
+ * [iz*n, (iz+1)*n).  A27 and B27 are [27][N] arrays of row-wise stencil
+ * coefficients: slot s = (dz+1)*9 + (dy+1)*3 + (dx+1) couples row i to column
+ * i + dx + nx*(dy + ny*dz) and must be 0 where that neighbour is outside the
+ * grid.  A must be symmetric and B symmetric positive definite (Eq. 2); the
+ * library relies on the symmetry and does not check it.
+ */
+typedef struct {
+  int nx, ny, nz;
+  const double* A27;
+  const double* B27;
+} feast_operator;
+
+typedef struct {
+  int max_loops;      /* refinement loop cap (default 20) */
+  int precision;      /* FEAST_PREC_FP64 (default) or FEAST_PREC_MIXED */
+  double ir_tol;      /* MIXED: relative residual target of each node solve (1e-12) */
+  int ir_max;         /* MIXED: cap on refinement steps per node solve (default 30) */
+  uint64_t seed;      /* start block when Y0 == NULL: Y(row, col) = uniform [-1, 1)
+                         from SplitMix64 output col*N + row of this seed */
+} feast_options;
+
+/* Per-solve diagnostics, valid after feast_solve (also after a failing one). */
+typedef struct {
+  int loops;
+  int m_found;
+  double trace[64];         /* in-interval trace after each loop (first 64 loops) */
+  double rel_change[64];    /* relative trace change; rel_change[0] = -1 */
+  double resid_max;         /* max over in-interval pairs, ||Ax-lBx||_1/(||A||_1 ||x||_1) */
+  double resid_paper_max;   /* max over in-interval pairs, ||Ax-lBx||_1/||Ax||_1 (Table I) */
+  double t_factor_ms;       /* device time of the node factorisations */
+  double t_solve_ms;        /* device time of all node solves (incl. refinement) */
+  double t_rr_ms;           /* device time of Rayleigh-Ritz (Gram, eigensolve, X = Q Phi) */
+  double t_total_ms;        /* wall time of the call */
+  int ir_steps_max;         /* MIXED: most refinement steps taken by one node solve */
+  double ir_resid_max;      /* MIXED: worst final relative residual of a node solve */
+  long long factor_flops;   /* algorithmic flops of the factorisation (8 n^3 per layer per node) */
+} feast_info;
+
+/* Fills *opt with the defaults listed above. */
+void feast_default_options(feast_options* opt);
+
+/*
+ * Creates a handle bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  opt may be NULL for
+ * the defaults.  Errors: FEAST_ERR_ARG, FEAST_ERR_CUDA.
+ */
+feast_status feast_init(feast_handle** h, const feast_options* opt, void* cuda_stream);
+
+/* Releases the handle and every device buffer it owns.  NULL is a no-op. */
+feast_status feast_destroy(feast_handle* h);
+
+/* Message of the last failing call on h ("" if none); valid until the next call. */
+const char* feast_last_error(const feast_handle* h);
+
+/* Copies the diagnostics of the last feast_solve into *info. */
+feast_status feast_get_info(const feast_handle* h, feast_info* info);
+
+/*
+ * The eigensolver (Fig. 2).  Finds the eigenpairs of (op->A27, op->B27) in the
+ * closed interval [lmin, lmax] with a subspace of M0 columns and Ne contour
+ * nodes; stops when the in-interval count is unchanged and the relative trace
+ * change is <= tol (loop 1 never stops).
+ *   Y0      : N x M0 start block, or NULL for the seeded random block
+ *             (a previous X gives a warm start: the right-hand side is B*Y0).
+ *   lambda  : out, M0 Ritz values, ascending, the m_found in-interval values first.
+ *   X       : out, N x M0 Ritz vectors (B-orthonormal), columns aligned with lambda.
+ *   resid   : out (may be NULL), M0 residuals ||A x - l B x||_1 / (||A||_1 ||x||_1).
+ *   m_found : out, number of Ritz values inside [lmin, lmax].
+ *   loops   : out, refinement loops run.
+ * Requirements: nx, ny, nz >= 1; 1 <= M0 <= min(N, 128); 1 <= Ne <= 64; lmin < lmax.
+ * Returns FEAST_OK, or one of the codes above; on FEAST_ERR_NO_CONVERGENCE and
+ * FEAST_ERR_M0_TOO_SMALL the outputs are filled.  Synchronises the stream.
+ */
+feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin, double lmax,
+                         int M0, int Ne, double tol, const double* Y0,
+                         double* lambda, double* X, double* resid, int* m_found, int* loops);
+
+/* ---------------------------------------------------------------------------
+ * Step-level entry points (DEVICE pointers only; ordered on the handle's
+ * stream; they do not synchronise unless stated).
+ * ------------------------------------------------------------------------- */
+
+/*
+ * Gauss-Legendre nodes and the contour (Fig. 2 caption; Eqs. 13-14), on the
+ * host: x[e], w[e] (ordered as the paper's Ne = 8 table: x_1 > 0,
+ * x_2 = -x_1, ...), theta[e] = -(pi/2)(x_e - 1), Z_e = (lmax+lmin)/2 + r e^{i theta_e}
+ * returned as Zre/Zim.  Any output pointer may be NULL.  Host memory.
+ */
+feast_status feast_contour(double lmin, double lmax, int Ne, double* x, double* w,
+                           double* theta, double* Zre, double* Zim);
+
+/*
+ * Y = C X for the 27-point operator C (a [27][N] coefficient array, device)
+ * on the nx x ny x nz grid; X and Y are N x k column-major device arrays.
+ * Used for A Q, B Q and B Y (Fig. 2 steps 2, 3, 6).
+ */
+feast_status feast_stencil_apply(feast_handle* h, int nx, int ny, int nz, const double* C27,
+                                 const double* X, double* Y, int k);
+
+/*
+ * Node solve (Fig. 2 step 2): Qe = (Z B - A)^{-1} RHS for one complex shift
+ * Z = Zre + i Zim with Zim > 0.  RHS: N x k real, Qe: N x k complex
+ * (interleaved), device.  precision selects the FP64 or the mixed
+ * (complex64 tensor-core factors + FP64 refinement) path.  Synchronises.
+ */
+feast_status feast_node_solve(feast_handle* h, const feast_operator* op, double Zre, double Zim,
+                              const double* RHS, double* Qe, int k, int precision);
+
+/*
+ * Step 2 in full: Q = -sum_e (w_e/2) Re{ r e^{i theta_e} (Z_e B - A)^{-1} RHS }
+ * (Eq. 15) for the Ne nodes of [lmin, lmax].  RHS, Q: N x k real, device.
+ * Synchronises.
+ */
+feast_status feast_quadrature(feast_handle* h, const feast_operator* op, double lmin, double lmax,
+                              int Ne, const double* RHS, double* Q, int k, int precision);
+
+/*
+ * Reduced eigensolve (Fig. 2 step 4; Eqs. 6, 8): A_Q Phi = eps B_Q Phi for
+ * symmetric M0 x M0 A_Q and s.p.d. B_Q (column-major, device), M0 <= 128.
+ * eps ascending (device, M0), Phi B_Q-orthonormal (device, M0 x M0).
+ * Returns FEAST_ERR_BQ_NOT_SPD when B_Q's eigenvalue ratio is <= 1e-14.
+ * Synchronises.
+ */
+feast_status feast_reduced_eig(feast_handle* h, const double* AQ, const double* BQ, int M0,
+                               double* eps, double* Phi);
+
+/*
+ * Rayleigh-Ritz (Fig. 2 steps 3-5; Eqs. 6-9): from Q (N x M0, device) forms
+ * A_Q, B_Q, solves the reduced problem and writes eps (M0, ascending) and
+ * X = Q Phi (N x M0), device.  AQ/BQ (M0 x M0, device) receive the reduced
+ * matrices when non-NULL.  Synchronises.
+ */
+feast_status feast_rayleigh_ritz(feast_handle* h, const feast_operator* op, const double* Q, int M0,
+                                 double* eps, double* X, double* AQ, double* BQ);
+
+/*
+ * Residuals (Table I caption): per column m of X (N x k, device),
+ * resid[m] = ||A x_m - l_m B x_m||_1 / (||A||_1 ||x_m||_1) and
+ * resid_paper[m] = ||A x_m - l_m B x_m||_1 / ||A x_m||_1 (device, k each;
+ * either may be NULL).  Synchronises.
+ */
+feast_status feast_residuals(feast_handle* h, const feast_operator* op, const double* lambda,
+                             const double* X, int k, double* resid, double* resid_paper);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEAST_GB300_H */

@@ -1,0 +1,225 @@
+"""Python binding of the GB300 FEAST library (libfeast_gb300.so).
+
+Argument marshalling only: every step of the eigensolver runs in the CUDA
+kernels behind the C-ABI declared in include/feast.h.  Functions keep the C
+names.  Buffers may be torch tensors (CUDA or CPU) or numpy arrays; CUDA
+tensors are passed as device pointers, everything else as host pointers (the
+library copies host data through its own device workspace).
+
+Importing this package loads the shared library and raises ImportError when it
+has not been built (``python -m paper_0901_2665_gb300.build``); there is no
+fallback implementation.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfeast_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_0901_2665_gb300.build`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+FEAST_OK = 0
+FEAST_ERR_ARG = 1
+FEAST_ERR_BQ_NOT_SPD = 2
+FEAST_ERR_NO_CONVERGENCE = 3
+FEAST_ERR_M0_TOO_SMALL = 4
+FEAST_ERR_PIVOT = 5
+FEAST_ERR_OOM = 6
+FEAST_ERR_CUDA = 7
+FEAST_ERR_TIMEOUT = 8
+FEAST_ERR_JACOBI = 9
+STATUS_NAMES = {v: k for k, v in globals().items() if k.startswith("FEAST_ERR_") or k == "FEAST_OK"}
+
+FEAST_PREC_FP64 = 0
+FEAST_PREC_MIXED = 1
+
+EXPORTED = [
+    "feast_default_options", "feast_init", "feast_destroy", "feast_last_error", "feast_get_info",
+    "feast_solve", "feast_contour", "feast_stencil_apply", "feast_node_solve", "feast_quadrature",
+    "feast_reduced_eig", "feast_rayleigh_ritz", "feast_residuals",
+]
+
+
+class feast_operator(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("A27", ctypes.c_void_p), ("B27", ctypes.c_void_p)]
+
+
+class feast_options(ctypes.Structure):
+    _fields_ = [("max_loops", ctypes.c_int), ("precision", ctypes.c_int), ("ir_tol", ctypes.c_double),
+                ("ir_max", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class feast_info(ctypes.Structure):
+    _fields_ = [("loops", ctypes.c_int), ("m_found", ctypes.c_int),
+                ("trace", ctypes.c_double * 64), ("rel_change", ctypes.c_double * 64),
+                ("resid_max", ctypes.c_double), ("resid_paper_max", ctypes.c_double),
+                ("t_factor_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
+                ("t_rr_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double),
+                ("ir_steps_max", ctypes.c_int), ("ir_resid_max", ctypes.c_double),
+                ("factor_flops", ctypes.c_longlong)]
+
+
+_vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+_lib.feast_default_options.argtypes = [ctypes.POINTER(feast_options)]
+_lib.feast_default_options.restype = None
+_lib.feast_init.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(feast_options), _vp]
+_lib.feast_destroy.argtypes = [_vp]
+_lib.feast_last_error.argtypes = [_vp]
+_lib.feast_last_error.restype = ctypes.c_char_p
+_lib.feast_get_info.argtypes = [_vp, ctypes.POINTER(feast_info)]
+_lib.feast_solve.argtypes = [_vp, ctypes.POINTER(feast_operator), _d, _d, _i, _i, _d, _vp, _vp, _vp, _vp,
+                             ctypes.POINTER(_i), ctypes.POINTER(_i)]
+_lib.feast_contour.argtypes = [_d, _d, _i, _vp, _vp, _vp, _vp, _vp]
+_lib.feast_stencil_apply.argtypes = [_vp, _i, _i, _i, _vp, _vp, _vp, _i]
+_lib.feast_node_solve.argtypes = [_vp, ctypes.POINTER(feast_operator), _d, _d, _vp, _vp, _i, _i]
+_lib.feast_quadrature.argtypes = [_vp, ctypes.POINTER(feast_operator), _d, _d, _i, _vp, _vp, _i, _i]
+_lib.feast_reduced_eig.argtypes = [_vp, _vp, _vp, _i, _vp, _vp]
+_lib.feast_rayleigh_ritz.argtypes = [_vp, ctypes.POINTER(feast_operator), _vp, _i, _vp, _vp, _vp, _vp]
+_lib.feast_residuals.argtypes = [_vp, ctypes.POINTER(feast_operator), _vp, _vp, _i, _vp, _vp]
+for _f in EXPORTED:
+    if _f not in ("feast_default_options", "feast_last_error"):
+        getattr(_lib, _f).restype = ctypes.c_int
+
+
+class FeastError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(buf):
+    """Address of a torch tensor / numpy array (None -> NULL)."""
+    if buf is None:
+        return None
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return buf.data_ptr()
+    if isinstance(buf, np.ndarray):
+        if not (buf.flags["C_CONTIGUOUS"] or buf.flags["F_CONTIGUOUS"]):
+            raise ValueError("array must be contiguous")
+        return buf.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # pragma: no cover - torch is optional for the binding
+        pass
+    return None
+
+
+def default_options() -> feast_options:
+    o = feast_options()
+    _lib.feast_default_options(ctypes.byref(o))
+    return o
+
+
+def make_operator(nx, ny, nz, A27, B27):
+    """feast_operator over two [27][N] float64 buffers (kept alive by the caller)."""
+    return feast_operator(nx, ny, nz, _ptr(A27), _ptr(B27))
+
+
+def feast_contour(lmin: float, lmax: float, Ne: int):
+    arrs = [np.zeros(Ne) for _ in range(5)]
+    st = _lib.feast_contour(lmin, lmax, Ne, *[a.ctypes.data for a in arrs])
+    if st != FEAST_OK:
+        raise FeastError(st, "feast_contour")
+    x, w, theta, zr, zi = arrs
+    return x, w, theta, zr + 1j * zi
+
+
+@dataclasses.dataclass
+class SolveResult:
+    status: int
+    m_found: int
+    loops: int
+    info: feast_info
+
+
+class Handle:
+    """Owns one feast_handle (feast_init / feast_destroy)."""
+
+    def __init__(self, precision: int = FEAST_PREC_FP64, max_loops: int = 20, ir_tol: float = 1e-12,
+                 ir_max: int = 30, seed: int = 1000, stream=None):
+        opt = default_options()
+        opt.precision, opt.max_loops, opt.ir_tol, opt.ir_max, opt.seed = precision, max_loops, ir_tol, ir_max, seed
+        self._h = _vp()
+        st = _lib.feast_init(ctypes.byref(self._h), ctypes.byref(opt), stream if stream is not None else _current_stream())
+        if st != FEAST_OK:
+            raise FeastError(st, "feast_init failed")
+
+    def close(self):
+        if self._h:
+            _lib.feast_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return _lib.feast_last_error(self._h).decode()
+
+    def _check(self, st, what, allow=()):
+        if st != FEAST_OK and st not in allow:
+            raise FeastError(st, f"{what}: {self.last_error()}")
+        return st
+
+    def info(self) -> feast_info:
+        inf = feast_info()
+        self._check(_lib.feast_get_info(self._h, ctypes.byref(inf)), "feast_get_info")
+        return inf
+
+    def feast_solve(self, op: feast_operator, lmin, lmax, M0, Ne, tol, Y0, lam, X, resid=None,
+                    allow=(FEAST_ERR_NO_CONVERGENCE, FEAST_ERR_M0_TOO_SMALL)) -> SolveResult:
+        m, loops = ctypes.c_int(0), ctypes.c_int(0)
+        st = _lib.feast_solve(self._h, ctypes.byref(op), float(lmin), float(lmax), int(M0), int(Ne), float(tol),
+                              _ptr(Y0), _ptr(lam), _ptr(X), _ptr(resid), ctypes.byref(m), ctypes.byref(loops))
+        self._check(st, "feast_solve", allow)
+        return SolveResult(st, m.value, loops.value, self.info())
+
+    def feast_stencil_apply(self, nx, ny, nz, C27, X, Y, k):
+        self._check(_lib.feast_stencil_apply(self._h, nx, ny, nz, _ptr(C27), _ptr(X), _ptr(Y), int(k)),
+                    "feast_stencil_apply")
+
+    def feast_node_solve(self, op, Z: complex, RHS, Qe, k, precision=FEAST_PREC_FP64):
+        self._check(_lib.feast_node_solve(self._h, ctypes.byref(op), Z.real, Z.imag, _ptr(RHS), _ptr(Qe), int(k),
+                                          int(precision)), "feast_node_solve")
+        return self.info()
+
+    def feast_quadrature(self, op, lmin, lmax, Ne, RHS, Q, k, precision=FEAST_PREC_FP64):
+        self._check(_lib.feast_quadrature(self._h, ctypes.byref(op), float(lmin), float(lmax), int(Ne), _ptr(RHS),
+                                          _ptr(Q), int(k), int(precision)), "feast_quadrature")
+        return self.info()
+
+    def feast_reduced_eig(self, AQ, BQ, M0, eps, Phi, allow=()):
+        return self._check(_lib.feast_reduced_eig(self._h, _ptr(AQ), _ptr(BQ), int(M0), _ptr(eps), _ptr(Phi)),
+                           "feast_reduced_eig", allow)
+
+    def feast_rayleigh_ritz(self, op, Q, M0, eps, X, AQ=None, BQ=None):
+        self._check(_lib.feast_rayleigh_ritz(self._h, ctypes.byref(op), _ptr(Q), int(M0), _ptr(eps), _ptr(X),
+                                             _ptr(AQ), _ptr(BQ)), "feast_rayleigh_ritz")
+
+    def feast_residuals(self, op, lam, X, k, resid, resid_paper=None):
+        self._check(_lib.feast_residuals(self._h, ctypes.byref(op), _ptr(lam), _ptr(X), int(k), _ptr(resid),
+                                         _ptr(resid_paper)), "feast_residuals")
+
+
+def library_path() -> str:
+    return LIB_PATH

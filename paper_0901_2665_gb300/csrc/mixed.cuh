@@ -1,0 +1,28 @@
+// Mixed-precision node factor-and-solve: complex64 block inverses computed and
+// applied on the tcgen05 tensor cores, FP64-residual iterative refinement of
+// every node solution (internal interface).
+#pragma once
+
+#include "common.cuh"
+
+namespace feast {
+
+struct MixedSolveStats {
+  int steps_max = 0;        // most refinement steps taken by one node solve
+  double resid_max = 0.0;   // worst final relative residual
+};
+
+struct MixedWork {
+  void* bufs[16] = {};
+  size_t sizes[16] = {};
+  void release();
+};
+
+// Both return nullptr on success, else a static error message.
+const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
+                         MixedWork& w, int* status);
+const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
+                        MixedWork& w, const double* RHS, cplx* G, int k, double ir_tol, int ir_max,
+                        MixedSolveStats* stats, int* status);
+
+}  // namespace feast

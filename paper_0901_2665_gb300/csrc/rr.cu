@@ -1,0 +1,424 @@
+// Rayleigh-Ritz in FP64 (Fig. 2 steps 3-5; Eqs. 6-9) and the residuals of
+// Table I.
+#include "kernels.cuh"
+
+namespace feast {
+
+namespace {
+
+// ---------------------------------------------------------------- Gram
+constexpr int kGramTile = 64;
+constexpr int kGramRows = 4096;   // rows per partial sum (split-K chunk)
+
+// partial[chunk][a + b*k1] = sum_{r in chunk} X[r, a] Y[r, b]
+__global__ void __launch_bounds__(256) k_gram_partial(long long N, int k1, int k2, const double* __restrict__ X,
+                                                      const double* __restrict__ Y, double* __restrict__ partial) {
+  constexpr int BK = 16;
+  __shared__ double Xs[BK][kGramTile + 1];
+  __shared__ double Ys[BK][kGramTile + 1];
+  const int a0 = blockIdx.x * kGramTile, b0 = blockIdx.y * kGramTile;
+  const long long r0 = (long long)blockIdx.z * kGramRows;
+  const long long r1 = min(N, r0 + kGramRows);
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  double acc[4][4] = {};
+  for (long long rb = r0; rb < r1; rb += BK) {
+    for (int t = tid; t < BK * kGramTile; t += 256) {
+      const int rr = t % BK, c = t / BK;
+      const long long r = rb + rr;
+      Xs[rr][c] = (r < r1 && a0 + c < k1) ? X[(long long)(a0 + c) * N + r] : 0.0;
+      Ys[rr][c] = (r < r1 && b0 + c < k2) ? Y[(long long)(b0 + c) * N + r] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < BK; ++rr) {
+      double xa[4], yb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xa[i] = Xs[rr][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) yb[j] = Ys[rr][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(xa[i], yb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* P = partial + (long long)blockIdx.z * k1 * k2;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int a = a0 + ty + 16 * i;
+    if (a >= k1) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = b0 + tx + 16 * j;
+      if (b < k2) P[a + (long long)b * k1] = acc[i][j];
+    }
+  }
+}
+
+// out = sum over chunks in chunk order (deterministic)
+__global__ void k_gram_reduce(int nchunks, int total, const double* __restrict__ partial, double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s += partial[(long long)c * total + t];
+  out[t] = s;
+}
+
+// ---------------------------------------------------------------- tall GEMM
+// C[r, c] = sum_j Q[r, j] P[j, c]; 64 rows x 64 cols per CTA.
+__global__ void __launch_bounds__(256) k_dgemm_tall(long long N, int m, int k, const double* __restrict__ Q,
+                                                    const double* __restrict__ P, double* __restrict__ C) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ double Qs[BK][BM + 1];
+  __shared__ double Ps[BK][BN + 1];
+  const long long r0 = (long long)blockIdx.x * BM;
+  const int c0 = blockIdx.y * BN;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  double acc[4][4] = {};
+  for (int kb = 0; kb < m; kb += BK) {
+    for (int t = tid; t < BK * BM; t += 256) {
+      const int row = t % BM, kk = t / BM;
+      const long long r = r0 + row;
+      Qs[kk][row] = (r < N && kb + kk < m) ? Q[(long long)(kb + kk) * N + r] : 0.0;
+    }
+    for (int t = tid; t < BK * BN; t += 256) {
+      const int kk = t % BK, col = t / BK;
+      Ps[kk][col] = (kb + kk < m && c0 + col < k) ? P[(long long)(c0 + col) * m + kb + kk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double q[4], p[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) q[i] = Qs[kk][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) p[j] = Ps[kk][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(q[i], p[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long long r = r0 + tx + 16 * i;
+    if (r >= N) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + ty + 16 * j;
+      if (c < k) C[(long long)c * N + r] = acc[i][j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Jacobi
+// Cyclic two-sided Jacobi (Golub & Van Loan, sym.schur2 rotations) with the
+// round-robin parallel ordering: in each step the m' = m + (m odd) indices are
+// split into m'/2 disjoint pairs, m'-1 steps make a sweep that meets every
+// pair once.  The matrix lives in shared memory (ld m+1); the accumulated
+// rotations go to V (global, col-major, ld m).  Returns the sweeps used, or
+// -1 when the sweep cap is hit.
+__device__ int jacobi_block(double* As, int m, double* V, double* cs, int* pq, int* flag, double abs_floor,
+                             int max_sweeps) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int ld = m + 1;
+  const int mp = m + (m & 1);
+  const int npairs = mp / 2;
+  double fro = 0.0;
+  // scale of the matrix for the absolute threshold
+  if (tid == 0) {
+    double s = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) s += As[i * ld + j] * As[i * ld + j];
+    cs[2 * npairs] = sqrt(s);
+  }
+  __syncthreads();
+  fro = cs[2 * npairs];
+  // A rotation is skipped when |a_pq| <= 1e-15 sqrt(|a_pp a_qq|) (the
+  // relative criterion that keeps small eigenvalues of a positive definite
+  // matrix accurate to their own scale) or |a_pq| <= abs_floor * ||A||_F.
+  const double abs_tol = abs_floor * fro;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) *flag = 0;
+    __syncthreads();
+    for (int step = 0; step < mp - 1; ++step) {
+      // pairs of this step and their rotations
+      for (int k = tid; k < npairs; k += nth) {
+        int p, q;
+        if (k == 0) {
+          p = mp - 1;
+          q = step;
+        } else {
+          p = (step + k) % (mp - 1);
+          q = (step - k + (mp - 1)) % (mp - 1);
+        }
+        if (p > q) { const int t = p; p = q; q = t; }
+        double c = 1.0, s = 0.0;
+        if (q < m) {
+          const double apq = As[p * ld + q];
+          const double app = As[p * ld + p], aqq = As[q * ld + q];
+          if (fabs(apq) > 1e-15 * sqrt(fabs(app)) * sqrt(fabs(aqq)) && fabs(apq) > abs_tol &&
+              fabs(apq) > 1e-300) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau))
+                                          : -1.0 / (-tau + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+            *flag = 1;
+          }
+        }
+        pq[2 * k] = p;
+        pq[2 * k + 1] = q;
+        cs[2 * k] = c;
+        cs[2 * k + 1] = s;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int t = tid; t < npairs * m; t += nth) {
+        const int k = t / m, j = t % m;
+        const int p = pq[2 * k], q = pq[2 * k + 1];
+        const double s = cs[2 * k + 1];
+        if (q >= m || s == 0.0) continue;
+        const double c = cs[2 * k];
+        const double ap = As[p * ld + j], aq = As[q * ld + j];
+        As[p * ld + j] = c * ap - s * aq;
+        As[q * ld + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int t = tid; t < npairs * m; t += nth) {
+        const int k = t / m, i = t % m;
+        const int p = pq[2 * k], q = pq[2 * k + 1];
+        const double s = cs[2 * k + 1];
+        if (q >= m || s == 0.0) continue;
+        const double c = cs[2 * k];
+        const double ap = As[i * ld + p], aq = As[i * ld + q];
+        As[i * ld + p] = c * ap - s * aq;
+        As[i * ld + q] = s * ap + c * aq;
+        const double vp = V[(long long)p * m + i], vq = V[(long long)q * m + i];
+        V[(long long)p * m + i] = c * vp - s * vq;
+        V[(long long)q * m + i] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+    const int any = *flag;
+    __syncthreads();
+    if (!any) return sweep + 1;
+  }
+  return -1;
+}
+
+// Two-stage reduced eigensolve (one CTA):
+//   B_Q = U diag(d) U^T           (Jacobi)
+//   C   = D^{-1/2} U^T A_Q U D^{-1/2}
+//   C   = W diag(eps) W^T          (Jacobi)
+//   Phi = U D^{-1/2} W, eps ascending.  Phi^T B_Q Phi = I.
+// work: U (m*m), W (m*m), T (m*m) doubles.
+__global__ void __launch_bounds__(1024) k_reduced_eig(int m, const double* __restrict__ AQ,
+                                                      const double* __restrict__ BQ, double* __restrict__ eps,
+                                                      double* __restrict__ Phi, double* __restrict__ work,
+                                                      int* status) {
+  extern __shared__ double smem[];
+  const int ld = m + 1;
+  double* As = smem;                       // m*(m+1)
+  double* cs = As + m * ld;                // 2*(m/2+1) + 1
+  double* dsc = cs + 2 * (m / 2 + 2);      // m: D^{-1/2}
+  double* ev = dsc + m;                    // m: eigenvalues of C
+  int* pq = (int*)(ev + m);                // 2*(m/2+1)
+  int* flag = pq + 2 * (m / 2 + 2);
+  double* U = work;
+  double* W = work + (long long)m * m;
+  double* T = work + 2LL * m * m;
+  const int tid = threadIdx.x, nth = blockDim.x;
+
+  // ---- stage 1: B_Q
+  for (int t = tid; t < m * m; t += nth) {
+    const int i = t % m, j = t / m;   // column-major input
+    As[i * ld + j] = 0.5 * (BQ[i + (long long)j * m] + BQ[j + (long long)i * m]);
+    U[t] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // Stage 1 uses the purely relative criterion.  B_Q that is singular to
+  // working precision keeps producing rounding-level off-diagonal entries in
+  // its null directions and exhausts the sweep cap; that case is reported as
+  // "not s.p.d." below through its diagonal ratio, any other cap-out as a
+  // Jacobi failure.
+  const int sw = jacobi_block(As, m, U, cs, pq, flag, 0.0, 40);
+  __shared__ double dminmax[2];
+  if (tid == 0) {
+    double dmin = As[0], dmax = As[0];
+    for (int i = 1; i < m; ++i) {
+      dmin = fmin(dmin, As[i * ld + i]);
+      dmax = fmax(dmax, As[i * ld + i]);
+    }
+    dminmax[0] = dmin;
+    dminmax[1] = dmax;
+  }
+  __syncthreads();
+  if (!(dminmax[0] > 1e-14 * dminmax[1])) {
+    if (tid == 0) atomicExch(status, (int)DEV_BQ_NOT_SPD);
+    return;
+  }
+  if (sw < 0) {
+    if (tid == 0) atomicExch(status, (int)DEV_JACOBI);
+    return;
+  }
+  for (int i = tid; i < m; i += nth) dsc[i] = 1.0 / sqrt(As[i * ld + i]);
+  __syncthreads();
+
+  // ---- C = D^{-1/2} U^T A_Q U D^{-1/2}
+  for (int t = tid; t < m * m; t += nth) {
+    const int i = t % m, j = t / m;
+    As[i * ld + j] = 0.5 * (AQ[i + (long long)j * m] + AQ[j + (long long)i * m]);
+  }
+  __syncthreads();
+  // T = A_Q U   (T col-major)
+  for (int t = tid; t < m * m; t += nth) {
+    const int i = t % m, j = t / m;
+    double s = 0.0;
+    for (int l = 0; l < m; ++l) s = fma(As[i * ld + l], U[(long long)j * m + l], s);
+    T[t] = s;
+  }
+  __syncthreads();
+  // As = D^{-1/2} U^T T D^{-1/2}
+  for (int t = tid; t < m * m; t += nth) {
+    const int i = t % m, j = t / m;
+    double s = 0.0;
+    for (int l = 0; l < m; ++l) s = fma(U[(long long)i * m + l], T[(long long)j * m + l], s);
+    As[i * ld + j] = s * dsc[i] * dsc[j];
+  }
+  __syncthreads();
+  for (int t = tid; t < m * m; t += nth) {
+    const int i = t % m, j = t / m;
+    if (i < j) {
+      const double v = 0.5 * (As[i * ld + j] + As[j * ld + i]);
+      As[i * ld + j] = v;
+      As[j * ld + i] = v;
+    }
+    W[t] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+
+  // ---- stage 2
+  // Stage 2: the Ritz values are wanted to absolute accuracy ~eps ||C||, so
+  // rotations below 2 eps ||C||_F are skipped (this also bounds the sweeps
+  // when C has eigenvalues near zero).
+  const int sw2 = jacobi_block(As, m, W, cs, pq, flag, 2.0 * 2.220446049250313e-16, 40);
+  if (sw2 < 0) {
+    if (tid == 0) atomicExch(status, (int)DEV_JACOBI);
+    return;
+  }
+  for (int i = tid; i < m; i += nth) ev[i] = As[i * ld + i];
+  __syncthreads();
+  // Phi = U D^{-1/2} W, columns placed at their ascending rank
+  for (int t = tid; t < m * m; t += nth) {
+    const int i = t % m, j = t / m;
+    const double ej = ev[j];
+    int rank = 0;
+    for (int l = 0; l < m; ++l) rank += (ev[l] < ej) || (ev[l] == ej && l < j);
+    double s = 0.0;
+    for (int l = 0; l < m; ++l) s = fma(U[(long long)l * m + i] * dsc[l], W[(long long)j * m + l], s);
+    Phi[i + (long long)rank * m] = s;
+    if (i == 0) eps[rank] = ej;
+  }
+}
+
+// ---------------------------------------------------------------- residuals
+__global__ void __launch_bounds__(256) k_residual_norms(long long N, const double* __restrict__ AX,
+                                                        const double* __restrict__ BX,
+                                                        const double* __restrict__ lambda,
+                                                        const double* __restrict__ X, double* __restrict__ out) {
+  const int j = blockIdx.x;
+  const double l = lambda[j];
+  const double* ax = AX + (long long)j * N;
+  const double* bx = BX + (long long)j * N;
+  const double* x = X + (long long)j * N;
+  double r = 0.0, xn = 0.0, an = 0.0;
+  for (long long i = threadIdx.x; i < N; i += blockDim.x) {
+    r += fabs(ax[i] - l * bx[i]);
+    xn += fabs(x[i]);
+    an += fabs(ax[i]);
+  }
+  __shared__ double red[3][256];
+  red[0][threadIdx.x] = r;
+  red[1][threadIdx.x] = xn;
+  red[2][threadIdx.x] = an;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) out[3 * j + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_residual_finish(int k, const double* __restrict__ norms, const double* __restrict__ normA,
+                                  double* __restrict__ resid, double* __restrict__ resid_paper) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  if (resid) resid[j] = norms[3 * j] / (normA[0] * norms[3 * j + 1]);
+  if (resid_paper) resid_paper[j] = norms[3 * j] / norms[3 * j + 2];
+}
+
+__global__ void k_permute_columns(long long N, int k, const int* __restrict__ perm, const double* __restrict__ src,
+                                  double* __restrict__ dst) {
+  const long long total = N * k;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t % N, j = t / N;
+    dst[t] = src[(long long)perm[j] * N + r];
+  }
+}
+
+}  // namespace
+
+long long gram_partial_elems(long long N, int k1, int k2) {
+  return (long long)cdiv(N, kGramRows) * k1 * k2;
+}
+
+void gram(cudaStream_t s, long long N, int k1, int k2, const double* X, const double* Y, double* partial,
+          double* out) {
+  const int nchunks = cdiv(N, kGramRows);
+  dim3 grid(cdiv(k1, kGramTile), cdiv(k2, kGramTile), nchunks);
+  k_gram_partial<<<grid, 256, 0, s>>>(N, k1, k2, X, Y, partial);
+  const int total = k1 * k2;
+  k_gram_reduce<<<cdiv(total, 256), 256, 0, s>>>(nchunks, total, partial, out);
+}
+
+void dgemm_tall(cudaStream_t s, long long N, int m, int k, const double* Q, const double* P, double* C) {
+  dim3 grid(cdiv(N, 64), cdiv(k, 64));
+  k_dgemm_tall<<<grid, 256, 0, s>>>(N, m, k, Q, P, C);
+}
+
+void reduced_eig(cudaStream_t s, int m, const double* AQ, const double* BQ, double* eps, double* Phi,
+                 double* work, int* status) {
+  const size_t smem = sizeof(double) * ((size_t)m * (m + 1) + 2 * (m / 2 + 2) + 2 * m) +
+                      sizeof(int) * (2 * (m / 2 + 2) + 1);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_reduced_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  k_reduced_eig<<<1, 1024, smem, s>>>(m, AQ, BQ, eps, Phi, work, status);
+}
+
+void residual_norms(cudaStream_t s, long long N, int k, const double* AX, const double* BX,
+                    const double* lambda, const double* X, double* out) {
+  k_residual_norms<<<k, 256, 0, s>>>(N, AX, BX, lambda, X, out);
+}
+
+void residual_finish(cudaStream_t s, int k, const double* norms, const double* normA, double* resid,
+                     double* resid_paper) {
+  k_residual_finish<<<cdiv(k, 128), 128, 0, s>>>(k, norms, normA, resid, resid_paper);
+}
+
+void permute_columns(cudaStream_t s, long long N, int k, const int* perm, const double* src, double* dst) {
+  long long total = N * k;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_permute_columns<<<blocks, 256, 0, s>>>(N, k, perm, src, dst);
+}
+
+}  // namespace feast
