@@ -9,12 +9,14 @@ namespace feast {
 
 struct MixedSolveStats {
   int steps_max = 0;        // most refinement steps taken by one node solve
-  double resid_max = 0.0;   // worst final relative residual
+  double resid_max = 0.0;   // worst final relative residual ||R||_F / ||RHS||_F
 };
 
 struct MixedWork {
   void* bufs[16] = {};
   size_t sizes[16] = {};
+  int nz_factored = 0, ne_factored = 0;   // shape of the factors held
+  int bemb_k = 0;                         // right-hand sides the RHS operand was zeroed for
   void release();
 };
 

@@ -1,0 +1,257 @@
+// tcgen05 TF32 GEMM for sm_103a: D (128 x BN per CTA, fp32 in TMEM) =
+// sum_k A[m, k] B[n, k] with A and B K-major fp32 operands loaded by TMA into
+// 128-byte-swizzled shared memory, one elected thread issuing
+// tcgen05.mma.kind::tf32 (M = 128, N = BN, K = 8 per instruction), and a
+// caller-supplied epilogue that reads the accumulator back with tcgen05.ld.
+//
+// Warp roles (192 threads): warp 0 = TMA producer, warp 1 = TMEM owner and
+// MMA issuer, warps 2-5 = epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
+// Every mbarrier wait is bounded; on expiry the kernel records DEV_TIMEOUT in
+// the status word, stops issuing work and still releases its TMEM.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace feast {
+namespace tc {
+
+constexpr int kStages = 4;
+constexpr int kBlockM = 128;
+constexpr int kBlockK = 32;                      // fp32 elements per 128-byte swizzle row
+constexpr int kATileBytes = kBlockM * kBlockK * 4;   // 16 KB
+constexpr int kThreads = 192;
+constexpr long long kWaitLimit = 1LL << 26;      // polls before a wait gives up (~1 s)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false (and DEV_TIMEOUT recorded) when the limit is reached or
+// another role of the CTA already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, volatile int* abort_flag) {
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 1023) == 1023 && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  atomicExch(status, (int)DEV_TIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart (stride byte offset), descriptor
+// version 1; the leading byte offset is unused for this layout.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>(1u) << 16;
+  d |= static_cast<uint64_t>(1024u >> 4) << 32;
+  d |= static_cast<uint64_t>(1u) << 46;
+  d |= static_cast<uint64_t>(2u) << 61;
+  return d;
+}
+
+// Instruction descriptor for kind::tf32: fp32 accumulator, TF32 A and B,
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 16 consecutive fp32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Round an fp32 value to TF32 (10 explicit mantissa bits, nearest).
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Geometry of a batched launch: grid (n tiles, m tiles, batch).  The A tile
+// of CTA (tn, tm, e) starts at row a_row0 + e*a_batch + tm*128 of A's tensor
+// map, the B tile at row b_row0 + e*b_batch + tn*BN; nk K-blocks of 32.
+struct Geom {
+  int a_row0, a_batch;
+  int b_row0, b_batch;
+  int nk;
+};
+
+template <int BN>
+struct Smem {
+  static constexpr int kBTileBytes = BN * kBlockK * 4;
+  static constexpr int kStageBytes = kATileBytes + kBTileBytes;
+  static constexpr int kTmemCols = BN < 32 ? 32 : BN;
+  static constexpr size_t kBytes = 1024 /*align slack*/ + (size_t)kStages * kStageBytes + 256;
+};
+
+// Epilogue contract: epi(e, tm, tn, row, lane_taddr, BN) with row in [0, 128)
+// the accumulator row of this thread and lane_taddr the TMEM address of its
+// lane at column 0.
+template <int BN, class Epi>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Geom geo, Epi epi,
+              int* status) {
+  using S = Smem<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + kStages * kATileBytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * S::kStageBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* tfull = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tfull + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int e = blockIdx.z, tm = blockIdx.y, tn = blockIdx.x;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(tfull, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, S::kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const int ay = geo.a_row0 + e * geo.a_batch + tm * kBlockM;
+      const int by = geo.b_row0 + e * geo.b_batch + tn * BN;
+      int issued = 0;
+      for (int kb = 0; kb < geo.nk; ++kb) {
+        const int s = kb % kStages;
+        const uint32_t ph = (kb / kStages) & 1;
+        if (kb >= kStages && !mbar_wait(&empty[s], ph ^ 1, status, abort_flag)) break;
+        mbar_arrive_expect_tx(&full[s], S::kStageBytes);
+        tma_load_2d(sA + s * kATileBytes, &tmA, &full[s], kb * kBlockK, ay);
+        tma_load_2d(sB + s * S::kBTileBytes, &tmB, &full[s], kb * kBlockK, by);
+        issued = kb + 1;
+      }
+      if (*abort_flag) {
+        // drain: wait (bounded) for the last load issued into every stage
+        for (int kb = issued - kStages < 0 ? 0 : issued - kStages; kb < issued; ++kb) {
+          for (long long it = 0; it < kWaitLimit; ++it)
+            if (mbar_try_wait(&full[kb % kStages], (kb / kStages) & 1)) break;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32(kBlockM, BN);
+      for (int kb = 0; kb < geo.nk; ++kb) {
+        const int s = kb % kStages;
+        const uint32_t ph = (kb / kStages) & 1;
+        if (!mbar_wait(&full[s], ph, status, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sA + s * kATileBytes);
+        const uint32_t b0 = smem_u32(sB + s * S::kBTileBytes);
+#pragma unroll
+        for (int kk = 0; kk < kBlockK / 8; ++kk)
+          mma_tf32(tmem, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc, (kb | kk) != 0);
+        mma_commit(&empty[s]);
+      }
+      // always signal: the epilogue (and the TMEM release) wait for every
+      // issued MMA to finish, also on the abort path
+      mma_commit(tfull);
+    }
+  } else {
+    const int q = warp % 4;
+    const int row = q * 32 + lane;
+    const bool ok = mbar_wait(tfull, 0, status, abort_flag);
+    tc_fence_after();
+    if (ok && !*abort_flag) epi(e, tm, tn, row, tmem + (static_cast<uint32_t>(q * 32) << 16));
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, S::kTmemCols);
+  }
+}
+
+}  // namespace tc
+}  // namespace feast

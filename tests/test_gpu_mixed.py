@@ -1,0 +1,85 @@
+"""Parity of the mixed-precision path (complex64 tensor-core factors and
+solves, FP64 iterative refinement) with the CPU oracle.
+
+The refinement stops when ||R||_F <= 1e-12 ||RHS||_F for every node, so the
+node solutions must satisfy that bound when their residual is recomputed by
+the oracle's own sparse product, and agree with the oracle's FP64 solution to
+within the forward error that bound allows (condition number of Z_e B - A up
+to ~1e4 here: 1e-8 relative).  Eigenpairs must meet the same gates as the FP64
+path: eigenvalues within 1e-10 relative, residuals <= 1e-10.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from test_gpu_parity import GRIDS, _compare_feast, back, cm, dev_op
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def F():
+    import paper_0901_2665_gb300 as mod
+    return mod
+
+
+@pytest.mark.parametrize("nx,ny,nz,G,seed", GRIDS)
+@pytest.mark.parametrize("k", [5, 24])
+def test_node_solve_mixed_matches_oracle(nx, ny, nz, G, seed, k):
+    op = workloads.q1_operator(nx, ny, nz, workloads.gaussian_potential(G, seed, nx, ny, nz))
+    lam = oracle.closed_form_eigenvalues_v0(nx, ny, nz)
+    lmin, lmax = lam[0] - 3.0, lam[min(12, len(lam) - 1)]
+    _, _, _, Z, _ = oracle.contour_points(lmin, lmax, 8)
+    RHS = np.random.default_rng(seed + 11).standard_normal((op.N, k))
+    A = oracle.assemble(op.A27, nx, ny, nz)
+    B = oracle.assemble(op.B27, nx, ny, nz)
+    dop, keep = dev_op(op)
+    h = F().Handle(precision=F().FEAST_PREC_MIXED)
+    for z in (Z[0], Z[7]):
+        Qe = torch.zeros((k, op.N), dtype=torch.complex128, device="cuda")
+        info = h.feast_node_solve(dop, complex(z), cm(RHS), Qe, k, precision=F().FEAST_PREC_MIXED)
+        got = back(Qe)
+        M = (z * B - A).astype(np.complex128)
+        res = np.linalg.norm(M @ got - RHS) / np.linalg.norm(RHS)
+        assert res <= 1e-12, res
+        assert info.ir_resid_max <= 1e-12 and info.ir_steps_max >= 1
+        ref = oracle.block_tridiag_factor(M, op.n, nz).solve(RHS.astype(np.complex128))
+        assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_quadrature_mixed_matches_oracle():
+    nx, ny, nz, G, seed = GRIDS[0]
+    op = workloads.q1_operator(nx, ny, nz, workloads.gaussian_potential(G, seed, nx, ny, nz))
+    lam = oracle.closed_form_eigenvalues_v0(nx, ny, nz)
+    lmin, lmax = lam[0] - 3.0, 0.5 * (lam[9] + lam[10])
+    k = 16
+    RHS = np.random.default_rng(seed + 2).standard_normal((op.N, k))
+    A = oracle.assemble(op.A27, nx, ny, nz)
+    B = oracle.assemble(op.B27, nx, ny, nz)
+    dop, keep = dev_op(op)
+    Q = torch.zeros((k, op.N), dtype=torch.float64, device="cuda")
+    F().Handle().feast_quadrature(dop, lmin, lmax, 8, cm(RHS), Q, k, precision=F().FEAST_PREC_MIXED)
+    ref, _ = oracle.quadrature_subspace(A, B, RHS, lmin, lmax, 8, op.n, nz)
+    assert np.abs(back(Q) - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("key,seed,zero", [("q1_10x10x20/v0", 0, True)] +
+                         [(f"q1_10x10x20/seed{s}", s, False) for s in range(5)])
+def test_feast_solve_mixed_matches_oracle(intervals, key, seed, zero):
+    wl = workloads.WORKLOADS["q1_10x10x20_fp64"]
+    op = wl.operator(seed, zero_potential=zero)
+    iv = intervals[key]
+    Y = workloads.random_Y(op.N, wl.M0, 1000 + seed)
+    ref = oracle.feast(op, iv["lmin"], iv["lmax"], wl.M0, wl.Ne, Y, tol=wl.tol)
+    dop, keep = dev_op(op)
+    lam = torch.zeros(wl.M0, dtype=torch.float64, device="cuda")
+    X = torch.zeros((wl.M0, op.N), dtype=torch.float64, device="cuda")
+    resid = torch.zeros(wl.M0, dtype=torch.float64, device="cuda")
+    h = F().Handle(precision=F().FEAST_PREC_MIXED)
+    r = h.feast_solve(dop, iv["lmin"], iv["lmax"], wl.M0, wl.Ne, wl.tol, cm(Y), lam, X, resid, allow=())
+    _compare_feast(lam.cpu().numpy(), back(X), r.m_found, r.loops, ref, op, iv["M"])
+    assert resid.cpu().numpy()[:iv["M"]].max() <= 1e-10
+    assert r.info.ir_resid_max <= 1e-12
