@@ -86,6 +86,7 @@ typedef struct {
   int ir_max;         /* MIXED: cap on refinement steps per node solve (default 30) */
   uint64_t seed;      /* start block when Y0 == NULL: Y(row, col) = uniform [-1, 1)
                          from SplitMix64 output col*N + row of this seed */
+  int profile;        /* 1: time the main kernel classes with CUDA events (feast_info.kernel_ms) */
 } feast_options;
 
 /* Per-solve diagnostics, valid after feast_solve (also after a failing one). */
@@ -103,6 +104,16 @@ typedef struct {
   int ir_steps_max;         /* MIXED: most refinement steps taken by one node solve */
   double ir_resid_max;      /* MIXED: worst final relative residual of a node solve */
   long long factor_flops;   /* algorithmic flops of the factorisation (8 n^3 per layer per node) */
+  /* kernel accounting of the call: launches of the library's kernels, and
+     with options.profile the summed device time and launch count per class:
+     0 sweep-update GEMM, 1 block-solve GEMM, 2 panel inversion, 3 panel
+     product/packing, 4 Schur complements, 5 solve couplings, 6 FP64
+     refinement residual, 7 FP64-path factor/solve kernels */
+  long long gpu_launches;
+  double kernel_ms[8];
+  long long kernel_launches[8];
+  double kernel_flops[8];   /* algorithmic flops of each class (complex FMA = 8 real flops;
+                               a TF32 product counts once) */
 } feast_info;
 
 /* Fills *opt with the defaults listed above. */

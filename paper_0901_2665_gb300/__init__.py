@@ -56,7 +56,7 @@ class feast_operator(ctypes.Structure):
 
 class feast_options(ctypes.Structure):
     _fields_ = [("max_loops", ctypes.c_int), ("precision", ctypes.c_int), ("ir_tol", ctypes.c_double),
-                ("ir_max", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("ir_max", ctypes.c_int), ("seed", ctypes.c_uint64), ("profile", ctypes.c_int)]
 
 
 class feast_info(ctypes.Structure):
@@ -66,7 +66,13 @@ class feast_info(ctypes.Structure):
                 ("t_factor_ms", ctypes.c_double), ("t_solve_ms", ctypes.c_double),
                 ("t_rr_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double),
                 ("ir_steps_max", ctypes.c_int), ("ir_resid_max", ctypes.c_double),
-                ("factor_flops", ctypes.c_longlong)]
+                ("factor_flops", ctypes.c_longlong), ("gpu_launches", ctypes.c_longlong),
+                ("kernel_ms", ctypes.c_double * 8), ("kernel_launches", ctypes.c_longlong * 8),
+                ("kernel_flops", ctypes.c_double * 8)]
+
+
+KERNEL_CLASSES = ["sweep_gemm", "solve_gemm", "panel_inverse", "panel_product", "schur", "solve_coupling",
+                  "fp64_residual", "fp64_path"]
 
 
 _vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
@@ -154,9 +160,10 @@ class Handle:
     """Owns one feast_handle (feast_init / feast_destroy)."""
 
     def __init__(self, precision: int = FEAST_PREC_FP64, max_loops: int = 20, ir_tol: float = 1e-12,
-                 ir_max: int = 30, seed: int = 1000, stream=None):
+                 ir_max: int = 30, seed: int = 1000, stream=None, profile: bool = False):
         opt = default_options()
         opt.precision, opt.max_loops, opt.ir_tol, opt.ir_max, opt.seed = precision, max_loops, ir_tol, ir_max, seed
+        opt.profile = 1 if profile else 0
         self._h = _vp()
         st = _lib.feast_init(ctypes.byref(self._h), ctypes.byref(opt), stream if stream is not None else _current_stream())
         if st != FEAST_OK:

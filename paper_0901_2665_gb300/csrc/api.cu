@@ -15,6 +15,7 @@
 #include "../../include/feast.h"
 #include "kernels.cuh"
 #include "mixed.cuh"
+#include "prof.cuh"
 
 using namespace feast;
 
@@ -326,6 +327,7 @@ void feast_default_options(feast_options* opt) {
   opt->ir_tol = 1e-12;
   opt->ir_max = 30;
   opt->seed = 1000;
+  opt->profile = 0;
 }
 
 feast_status feast_init(feast_handle** out, const feast_options* opt, void* cuda_stream) {
@@ -340,6 +342,7 @@ feast_status feast_init(feast_handle** out, const feast_options* opt, void* cuda
     if (h->opt.precision != FEAST_PREC_FP64 && h->opt.precision != FEAST_PREC_MIXED)
       fail(FEAST_ERR_ARG, "unknown precision");
     ck(cudaGetDevice(&h->device), "cudaGetDevice");
+    if (h->opt.profile) prof::set_enabled(true);
     for (auto& e : h->ev) ck(cudaEventCreate(&e), "event");
     reset_status(h);
   });
@@ -480,6 +483,9 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
   feast_status st = guarded(h, [&] {
     auto t_wall0 = std::chrono::steady_clock::now();
     h->info = feast_info{};
+    prof::set_enabled(h->opt.profile != 0);
+    prof::collect(nullptr, nullptr, nullptr);   // drop records of earlier calls
+    const long long launches0 = prof::launches();
     if (!(lmin < lmax) || !std::isfinite(lmin) || !std::isfinite(lmax)) fail(FEAST_ERR_ARG, "need lmin < lmax");
     if (Ne < 1 || Ne > 64) fail(FEAST_ERR_ARG, "Ne must be in [1, 64]");
     if (!lambda || !X || !m_found || !loops) fail(FEAST_ERR_ARG, "output pointer is NULL");
@@ -607,6 +613,8 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
       h->info.resid_max = std::max(h->info.resid_max, r1[j]);
       h->info.resid_paper_max = std::max(h->info.resid_paper_max, rp[j]);
     }
+    h->info.gpu_launches = prof::launches() - launches0;
+    prof::collect(h->info.kernel_ms, h->info.kernel_launches, h->info.kernel_flops);
     h->info.t_total_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_wall0).count();
     if (count >= M0) final_status = FEAST_ERR_M0_TOO_SMALL;

@@ -14,6 +14,7 @@
 //   forward   g_1 = b_1,  g_i = b_i + C_i (S'_{i-1} g_{i-1})
 //   backward  x_nb = -S'_nb g_nb,  x_i = -S'_i (g_i - C_{i+1}^T x_{i+1})
 #include "kernels.cuh"
+#include "prof.cuh"
 
 namespace feast {
 
@@ -295,6 +296,7 @@ void zgemm_sym(cudaStream_t s, int n, int k, int Ne, double alpha, const cplx* S
                long long ldx, long long sX, cplx* C, long long ldc, long long sC) {
   dim3 grid(cdiv(k, 32), cdiv(n, 64), Ne);
   k_zgemm_sym<<<grid, 256, 0, s>>>(n, k, alpha, S, sS, X, ldx, sX, C, ldc, sC);
+  prof::count_launch();
 }
 
 void factor_fp64(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
@@ -302,7 +304,10 @@ void factor_fp64(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A2
   const int n = g.n(), nb = g.nz;
   const long long nn = (long long)n * n;
   const long long sF = (long long)nb * nn;  // node stride of the factor array
+  prof::begin(s, prof::FP64_SOLVE);
+  prof::add_work(prof::FP64_SOLVE, 8.0 * n * (double)n * n * nb * Ne);
   for (int i = 0; i < nb; ++i) {
+    prof::count_launch((i > 0 ? 2 : 1) + 3 * cdiv(n, kPanel64));
     cplx* Si = w.F + (long long)i * nn;
     if (i > 0) {
       const cplx* Sprev = w.F + (long long)(i - 1) * nn;
@@ -316,6 +321,7 @@ void factor_fp64(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A2
       k_sweep_update<<<dim3(cdiv(n, 64), cdiv(n, 64), Ne), 256, 0, s>>>(Si, sF, n, k0, bw, w.T, w.L, w.Pinv);
     }
   }
+  prof::end(s, prof::FP64_SOLVE);
 }
 
 void solve_fp64(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "mixed.cuh"
+#include "prof.cuh"
 #include "tc_gemm.cuh"
 
 namespace feast {
@@ -29,7 +30,7 @@ namespace feast {
 namespace {
 
 constexpr int kPanel = 64;   // sweep panel width (complex columns)
-constexpr int kRowsPerPanelCta = 128;
+constexpr int kRowsPerPanelCta = 32;
 
 struct f2 {
   float x, y;
@@ -40,20 +41,6 @@ __device__ __forceinline__ void f2fma(f2& acc, f2 a, f2 b) {
   acc.x = fmaf(-a.y, b.y, acc.x);
   acc.y = fmaf(a.x, b.y, acc.y);
   acc.y = fmaf(a.y, b.x, acc.y);
-}
-__device__ __forceinline__ f2 f2inv(f2 a) {
-  if (fabsf(a.x) >= fabsf(a.y)) {
-    float r = a.y / a.x, d = a.x + a.y * r;
-    return f2{1.0f / d, -r / d};
-  }
-  float r = a.x / a.y, d = a.x * r + a.y;
-  return f2{r / d, -1.0f / d};
-}
-
-// coefficient of M_e = Z_e B - A at stencil slot s of grid row `row`
-__device__ __forceinline__ f2 mcoef(const double* A27, const double* B27, long long N, int s, long long row, cplx z) {
-  const double a = A27[(long long)s * N + row], b = B27[(long long)s * N + row];
-  return f2{(float)(z.re * b - a), (float)(z.im * b)};
 }
 
 // ------------------------------------------------------------------ layout
@@ -68,25 +55,47 @@ struct Dims {
   int ldB;       // floats per embedded RHS row
 };
 
+// Cf[e][s][i] = (Z_e B - A)[i, i + off(s)] in complex fp32, 0 outside the grid:
+// the coefficients of every node matrix, computed once per factorisation.
+__global__ void k_mx_coef(Dims d, const cplx* __restrict__ Z, const double* __restrict__ A27,
+                          const double* __restrict__ B27, f2* __restrict__ Cf) {
+  const int e = blockIdx.y;
+  const cplx z = Z[e];
+  const long long total = 27LL * d.N;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(t / d.N);
+    const long long i = t % d.N;
+    const int ix = (int)(i % d.nx), iy = (int)((i / d.nx) % d.ny), iz = (int)(i / d.n);
+    const int dx = slot_dx(s), dy = slot_dy(s), dz = slot_dz(s);
+    const bool ok = ix + dx >= 0 && ix + dx < d.nx && iy + dy >= 0 && iy + dy < d.ny && iz + dz >= 0 &&
+                    iz + dz < d.nz;
+    const double a = ok ? A27[t] : 0.0, b = ok ? B27[t] : 0.0;
+    Cf[(long long)e * total + t] = ok ? f2{(float)(z.re * b - a), (float)(z.im * b)} : f2{0.f, 0.f};
+  }
+}
+
+__device__ __forceinline__ f2 cf_at(const Dims& d, const f2* Cf, int e, int s, long long row) {
+  return Cf[((long long)e * 27 + s) * d.N + row];
+}
+
 // ------------------------------------------------------------------ Schur
-// T1[a, q] = sum_b S'[a, b] C[q, b] (row-split, fp32)
-__global__ void __launch_bounds__(256) k_mx_schur1(Dims d, int layer, const cplx* __restrict__ Z,
-                                                   const double* __restrict__ A27, const double* __restrict__ B27,
+// The fp32 working copies of S_i / S'_i live in a two-layer ping-pong buffer
+// F[e][layer & 1]: the recursion only ever needs the previous layer.
+// T1[a, q] = sum_b S'[a, b] C[q, b] (row-split, fp32), C = dz = -1 slots of layer `layer`
+__global__ void __launch_bounds__(256) k_mx_schur1(Dims d, int layer, const f2* __restrict__ Cf,
                                                    const float* __restrict__ F, float* __restrict__ T1) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int a = blockIdx.y, e = blockIdx.z;
   if (q >= d.n) return;
   const long long rowq = (long long)layer * d.n + q;
-  const int qx = q % d.nx, qy = q / d.nx;
-  const cplx z = Z[e];
-  const float* S = F + (((long long)e * d.nz + layer - 1) * d.n + a) * d.ldF;
+  const float* S = F + (((long long)e * 2 + ((layer - 1) & 1)) * d.n + a) * d.ldF;
   f2 acc{0.f, 0.f};
 #pragma unroll
   for (int t = 0; t < 9; ++t) {
-    const int dx = t % 3 - 1, dy = t / 3 - 1;
-    if (qx + dx < 0 || qx + dx >= d.nx || qy + dy < 0 || qy + dy >= d.ny) continue;
-    const int b = q + dx + d.nx * dy;
-    f2fma(acc, f2{S[b], S[d.n + b]}, mcoef(A27, B27, d.N, t, rowq, z));
+    const int b = q + (t % 3 - 1) + d.nx * (t / 3 - 1);
+    const f2 c = cf_at(d, Cf, e, t, rowq);
+    if (c.x != 0.f || c.y != 0.f) f2fma(acc, f2{S[b], S[d.n + b]}, c);
   }
   float* out = T1 + ((long long)e * d.n + a) * d.ldF;
   out[q] = acc.x;
@@ -94,214 +103,265 @@ __global__ void __launch_bounds__(256) k_mx_schur1(Dims d, int layer, const cplx
 }
 
 // S_i[p, q] = D_i[p, q] + sum_a C[p, a] T1[a, q] -> F (layer i)
-__global__ void __launch_bounds__(256) k_mx_schur2(Dims d, int layer, const cplx* __restrict__ Z,
-                                                   const double* __restrict__ A27, const double* __restrict__ B27,
+__global__ void __launch_bounds__(256) k_mx_schur2(Dims d, int layer, const f2* __restrict__ Cf,
                                                    const float* __restrict__ T1, float* __restrict__ F) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y, e = blockIdx.z;
   if (q >= d.n) return;
   const long long rowp = (long long)layer * d.n + p;
   const int px = p % d.nx, py = p / d.nx;
-  const cplx z = Z[e];
   f2 acc{0.f, 0.f};
   const int ddx = (q % d.nx) - px, ddy = (q / d.nx) - py;
-  if (ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1) acc = mcoef(A27, B27, d.N, 9 + (ddy + 1) * 3 + (ddx + 1), rowp, z);
+  if (ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1) acc = cf_at(d, Cf, e, 9 + (ddy + 1) * 3 + (ddx + 1), rowp);
   if (layer > 0) {
     const float* T = T1 + (long long)e * d.n * d.ldF;
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
-      const int dx = t % 3 - 1, dy = t / 3 - 1;
-      if (px + dx < 0 || px + dx >= d.nx || py + dy < 0 || py + dy >= d.ny) continue;
-      const float* Trow = T + (long long)(p + dx + d.nx * dy) * d.ldF;
-      f2fma(acc, mcoef(A27, B27, d.N, t, rowp, z), f2{Trow[q], Trow[d.n + q]});
+      const f2 c = cf_at(d, Cf, e, t, rowp);
+      if (c.x == 0.f && c.y == 0.f) continue;
+      const float* Trow = T + (long long)(p + (t % 3 - 1) + d.nx * (t / 3 - 1)) * d.ldF;
+      f2fma(acc, c, f2{Trow[q], Trow[d.n + q]});
     }
   }
-  float* out = F + (((long long)e * d.nz + layer) * d.n + p) * d.ldF;
+  float* out = F + (((long long)e * 2 + (layer & 1)) * d.n + p) * d.ldF;
   out[q] = acc.x;
   out[d.n + q] = acc.y;
 }
 
 // ------------------------------------------------------------------ panel
-// For panel K = [k0, k0+bw) of node e: Pinv = S[K,K]^{-1} (fp32 unpivoted
-// sweep, redundantly per CTA), then for this CTA's 128 rows i:
-//   T[i, :] = S[i, K] Pinv,  L[i, :] = S[i, K]
-// and the GEMM operands Aop = [Tr | Ti] (row i) and Bop (embedded L, rows in
-// blocks of 64 complex columns: 64 rows [Lr, -Li] then 64 rows [Li, Lr]),
-// rounded to TF32.  Chunk 0 also stores Pinv.
-__global__ void __launch_bounds__(256) k_mx_panel(Dims d, int layer, int k0, int bw, const float* __restrict__ F,
-                                                  float* __restrict__ Aop, float* __restrict__ Bop,
-                                                  f2* __restrict__ Tc, f2* __restrict__ PinvOut, int* status) {
-  extern __shared__ f2 psm[];
-  f2* P = psm;                               // 64 x 65
-  f2* Ls = psm + kPanel * (kPanel + 1);      // 128 x 65
-  f2* fac = Ls + kRowsPerPanelCta * (kPanel + 1);   // 64
-  __shared__ f2 piv_inv;
+constexpr int kPinvThreads = 512;
+
+// 1/a for complex fp32 with scaling (reciprocal instructions only).
+__device__ __forceinline__ f2 f2inv_fast(f2 a) {
+  const float rs = __frcp_rn(fmaxf(fabsf(a.x), fabsf(a.y)));
+  const float x = a.x * rs, y = a.y * rs;
+  const float dinv = __frcp_rn(x * x + y * y);
+  return f2{x * dinv * rs, -y * dinv * rs};
+}
+
+// Pinv = S[K,K]^{-1} for panel K = [k0, k0+bw) of every node (one CTA per
+// node): unpivoted sweep of the 64 x 64 diagonal block in fp32, padded with
+// the identity when bw < 64.  The block stays in registers (thread t owns
+// rows 2(t/16)..+1, columns 4(t%16)..+3); the owners of pivot row and column
+// kk publish them to a double-buffered shared copy, one barrier per pivot.
+__global__ void __launch_bounds__(kPinvThreads) k_mx_pinv(Dims d, int layer, int k0, int bw,
+                                                          const float* __restrict__ F, f2* __restrict__ PinvOut,
+                                                          int* status) {
+  __shared__ f2 colbuf[2][kPanel];
+  __shared__ f2 rowbuf[2][kPanel];
   __shared__ int bad;
-  const int e = blockIdx.y;
-  const int r0 = blockIdx.x * kRowsPerPanelCta;
-  const int tid = threadIdx.x, nth = blockDim.x;
+  const int e = blockIdx.x;
+  const int tid = threadIdx.x;
   const int n = d.n;
-  const float* Fl = F + ((long long)e * d.nz + layer) * n * d.ldF;
+  const float* Fl = F + ((long long)e * 2 + (layer & 1)) * n * d.ldF;
   if (tid == 0) bad = 0;
-  for (int t = tid; t < kPanel * kPanel; t += nth) {
-    const int i = t / kPanel, j = t % kPanel;
-    f2 v{(i == j) ? 1.f : 0.f, 0.f};
-    if (i < bw && j < bw) {
-      const float* row = Fl + (long long)(k0 + i) * d.ldF;
-      v = f2{row[k0 + j], row[n + k0 + j]};
+  const int rb = tid / 16, cb = tid % 16;
+  const int i0 = 2 * rb, j0 = 4 * cb;
+  f2 v[2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = i0 + a, j = j0 + b;
+      f2 x{(i == j) ? 1.f : 0.f, 0.f};
+      if (i < bw && j < bw) {
+        const float* row = Fl + (long long)(k0 + i) * d.ldF;
+        x = f2{row[k0 + j], row[n + k0 + j]};
+      }
+      v[a][b] = x;
     }
-    P[i * (kPanel + 1) + j] = v;
-  }
-  for (int t = tid; t < kRowsPerPanelCta * kPanel; t += nth) {
-    const int r = t / kPanel, m = t % kPanel;
-    const int i = r0 + r;
-    f2 v{0.f, 0.f};
-    if (i < n && m < bw) {
-      const float* row = Fl + (long long)i * d.ldF;
-      v = f2{row[k0 + m], row[n + k0 + m]};
-    }
-    Ls[r * (kPanel + 1) + m] = v;
-  }
-  __syncthreads();
-  // unpivoted sweep of P: after all pivots P = -P0^{-1}
   for (int kk = 0; kk < kPanel; ++kk) {
-    if (tid == 0) {
-      const f2 dv = P[kk * (kPanel + 1) + kk];
-      const float mag = fabsf(dv.x) + fabsf(dv.y);
-      if (!(mag > 0.f) || !isfinite(mag)) bad = 1;
-      piv_inv = (mag > 0.f) ? f2inv(dv) : f2{0.f, 0.f};
+    f2* cbuf = colbuf[kk & 1];
+    f2* rbuf = rowbuf[kk & 1];
+    // publish pivot column / row (static register indices: no local memory)
+    if (cb == kk / 4) {
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (b == kk % 4) cbuf[i0 + a] = v[a][b];
+    }
+    if (rb == kk / 2) {
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (a == kk % 2) rbuf[j0 + b] = v[a][b];
     }
     __syncthreads();
-    const f2 inv = piv_inv;
-    for (int i = tid; i < kPanel; i += nth) fac[i] = f2mul(P[i * (kPanel + 1) + kk], inv);
-    __syncthreads();
-    for (int t = tid; t < kPanel * kPanel; t += nth) {
-      const int i = t / kPanel, j = t % kPanel;
-      if (i == kk || j == kk) continue;
-      f2 v = P[i * (kPanel + 1) + j];
-      const f2 u = f2mul(fac[i], P[kk * (kPanel + 1) + j]);
-      v.x -= u.x;
-      v.y -= u.y;
-      P[i * (kPanel + 1) + j] = v;
-    }
-    __syncthreads();
-    for (int t = tid; t < kPanel; t += nth) {
-      if (t != kk) {
-        P[t * (kPanel + 1) + kk] = fac[t];
-        P[kk * (kPanel + 1) + t] = f2mul(P[kk * (kPanel + 1) + t], inv);
+    const f2 piv = rbuf[kk];
+    const float mag = fabsf(piv.x) + fabsf(piv.y);
+    const bool good = mag > 0.f && isfinite(mag);
+    if (tid == 0 && !good) bad = 1;
+    const f2 inv = good ? f2inv_fast(piv) : f2{0.f, 0.f};
+    f2 fac[2], rw[4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) fac[a] = f2mul(cbuf[i0 + a], inv);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) rw[b] = rbuf[j0 + b];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = i0 + a, j = j0 + b;
+        const f2 u = f2mul(fac[a], rw[b]);
+        const f2 upd{v[a][b].x - u.x, v[a][b].y - u.y};
+        const f2 rowv = f2mul(rw[b], inv);
+        v[a][b] = (i != kk) ? ((j != kk) ? upd : fac[a]) : ((j != kk) ? rowv : f2{-inv.x, -inv.y});
       }
-    }
-    if (tid == 0) P[kk * (kPanel + 1) + kk] = f2{-inv.x, -inv.y};
-    __syncthreads();
   }
-  // Pinv = -P
-  if (blockIdx.x == 0)
-    for (int t = tid; t < kPanel * kPanel; t += nth) {
-      const f2 v = P[(t / kPanel) * (kPanel + 1) + t % kPanel];
-      PinvOut[(long long)e * kPanel * kPanel + t] = f2{-v.x, -v.y};
-    }
-  // T = L Pinv for the 128 rows; one (row, 8-column group) per thread-iteration
-  for (int t = tid; t < kRowsPerPanelCta * (kPanel / 8); t += nth) {
-    const int r = t / (kPanel / 8), cg = (t % (kPanel / 8)) * 8;
-    const int i = r0 + r;
-    f2 acc[8];
+  // v holds -P^{-1}
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = f2{0.f, 0.f};
-    for (int m = 0; m < kPanel; ++m) {
-      const f2 l = Ls[r * (kPanel + 1) + m];
+  for (int a = 0; a < 2; ++a)
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const f2 pv = P[m * (kPanel + 1) + cg + c];
-        f2fma(acc[c], l, f2{-pv.x, -pv.y});
-      }
-    }
-    if (i < n) {
-      float* arow = Aop + ((long long)e * n + i) * (2 * kPanel);
-      f2* trow = Tc + ((long long)e * n + i) * kPanel;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        arow[cg + c] = tc::to_tf32(acc[c].x);
-        arow[kPanel + cg + c] = tc::to_tf32(acc[c].y);
-        trow[cg + c] = acc[c];
-      }
-      // embedded L rows for complex column j = i
-      const long long brow = ((long long)e * d.nblk64 + i / 64) * 128 + (i % 64);
-      float* bre = Bop + brow * (2 * kPanel);
-      float* bim = Bop + (brow + 64) * (2 * kPanel);
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const f2 l = Ls[r * (kPanel + 1) + cg + c];
-        bre[cg + c] = tc::to_tf32(l.x);
-        bre[kPanel + cg + c] = tc::to_tf32(-l.y);
-        bim[cg + c] = tc::to_tf32(l.y);
-        bim[kPanel + cg + c] = tc::to_tf32(l.x);
-      }
-    }
-  }
+    for (int b = 0; b < 4; ++b)
+      PinvOut[(long long)e * kPanel * kPanel + (i0 + a) * kPanel + j0 + b] = f2{-v[a][b].x, -v[a][b].y};
   if (tid == 0 && bad) atomicExch(status, (int)DEV_PIVOT);
 }
 
+// For panel K and this CTA's 32 rows i:  T[i, :] = S[i, K] Pinv  and
+// L[i, :] = S[i, K], written as the TF32-rounded GEMM operands
+// Aop = [Tr | Ti] (row i) and Bop (embedded L, rows in blocks of 64 complex
+// columns: 64 rows [Lr, -Li] then 64 rows [Li, Lr]), and in fp32 as Tc.
+__global__ void __launch_bounds__(256) k_mx_panel_T(Dims d, int layer, int k0, int bw, const float* __restrict__ F,
+                                                    const f2* __restrict__ PinvIn, float* __restrict__ Aop,
+                                                    float* __restrict__ Bop, f2* __restrict__ Tc) {
+  __shared__ f2 Ps[kPanel][kPanel + 1];
+  __shared__ f2 Ls[kRowsPerPanelCta][kPanel + 1];
+  const int e = blockIdx.y;
+  const int r0 = blockIdx.x * kRowsPerPanelCta;
+  const int tid = threadIdx.x;
+  const int n = d.n;
+  const float* Fl = F + ((long long)e * 2 + (layer & 1)) * n * d.ldF;
+  const f2* Pin = PinvIn + (long long)e * kPanel * kPanel;
+  for (int t = tid; t < kPanel * kPanel; t += 256) Ps[t / kPanel][t % kPanel] = Pin[t];
+  for (int t = tid; t < kRowsPerPanelCta * kPanel; t += 256) {
+    const int r = t / kPanel, m = t % kPanel;
+    const int i = r0 + r;
+    f2 x{0.f, 0.f};
+    if (i < n && m < bw) {
+      const float* row = Fl + (long long)i * d.ldF;
+      x = f2{row[k0 + m], row[n + k0 + m]};
+    }
+    Ls[r][m] = x;
+  }
+  __syncthreads();
+  const int r = tid / 8, c0 = (tid % 8) * 8;
+  const int i = r0 + r;
+  f2 acc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc[c] = f2{0.f, 0.f};
+#pragma unroll 4
+  for (int m = 0; m < kPanel; ++m) {
+    const f2 l = Ls[r][m];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) f2fma(acc[c], l, Ps[m][c0 + c]);
+  }
+  if (i >= n) return;
+  float* arow = Aop + ((long long)e * n + i) * (2 * kPanel);
+  f2* trow = Tc + ((long long)e * n + i) * kPanel;
+  const long long brow = ((long long)e * d.nblk64 + i / 64) * 128 + (i % 64);
+  float* bre = Bop + brow * (2 * kPanel);
+  float* bim = Bop + (brow + 64) * (2 * kPanel);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    arow[c0 + c] = tc::to_tf32(acc[c].x);
+    arow[kPanel + c0 + c] = tc::to_tf32(acc[c].y);
+    trow[c0 + c] = acc[c];
+    const f2 l = Ls[r][c0 + c];
+    bre[c0 + c] = tc::to_tf32(l.x);
+    bre[kPanel + c0 + c] = tc::to_tf32(-l.y);
+    bim[c0 + c] = tc::to_tf32(l.y);
+    bim[kPanel + c0 + c] = tc::to_tf32(l.x);
+  }
+}
+
 // ------------------------------------------------------------------ epilogues
-// Sweep trailing update on tile (rows tm*128.., complex columns tn*64..).
+constexpr int kStageLd = tc::kBlockM + 1;   // staging row stride (floats): conflict-free both ways
+
+// Sweep trailing update on tile (rows tm*128.., complex columns tn*64..):
+//   i, j outside K:  S[i, j] -= acc[i, j]
+//   i in K, j not:   S[i, j]  = T[j, i - k0]
+//   j in K, i not:   S[i, j]  = T[i, j - k0]
+//   both in K:       S[i, j]  = -Pinv[i - k0, j - k0]
+// The last panel writes every entry of the finished S'_i, so it also stores
+// the TF32-rounded (nearest) copy that the block solves read.
+// The accumulator goes through shared memory (one half, real or imaginary,
+// at a time) so that the read-modify-write of S is coalesced along rows.
 struct SweepEpi {
-  float* F;        // row-split storage of the layer being swept, node stride sF floats
+  float* F;        // row-split fp32 working copy of the layer being swept, node stride sF floats
   long long sF;
-  int ldF, n, k0, bw, last;
+  float* Fr;       // last panel only: TF32-rounded copy of the finished S' (solve operand), node stride sFr
+  long long sFr;
+  int ldF, n, k0, bw;
   const f2* Tc;    // n x 64 per node
   const f2* Pinv;  // 64 x 64 per node
-  __device__ void operator()(int e, int tm, int tn, int row, uint32_t taddr) const {
-    const int i = tm * tc::kBlockM + row;
-    float* Frow = F + e * sF + (long long)i * ldF;
+  __device__ void operator()(int e, int tm, int tn, int row, uint32_t taddr, int ept, uint8_t* stage) const {
+    float* Sg = reinterpret_cast<float*>(stage);   // 64 columns x kStageLd
+    float* Fe = F + e * sF;
     const f2* T = Tc + (long long)e * n * kPanel;
     const f2* Pi = Pinv + (long long)e * kPanel * kPanel;
-    const bool inI = i >= k0 && i < k0 + bw;
 #pragma unroll 1
-    for (int c0 = 0; c0 < 64; c0 += 16) {
-      float re[16], im[16];
-      tc::tmem_ld16(taddr + c0, re);
-      tc::tmem_ld16(taddr + 64 + c0, im);
-      if (i >= n) continue;
+    for (int half = 0; half < 2; ++half) {
+#pragma unroll 1
+      for (int c0 = 0; c0 < 64; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(taddr + half * 64 + c0, v);
 #pragma unroll
-      for (int t = 0; t < 16; ++t) {
-        const int j = tn * 64 + c0 + t;
-        if (j >= n) continue;
-        const bool inJ = j >= k0 && j < k0 + bw;
-        float vr, vi;
-        if (!inI && !inJ) {
-          vr = Frow[j] - re[t];
-          vi = Frow[n + j] - im[t];
-        } else if (inI && !inJ) {
-          const f2 v = T[(long long)j * kPanel + (i - k0)];
-          vr = v.x;
-          vi = v.y;
-        } else if (!inI && inJ) {
-          const f2 v = T[(long long)i * kPanel + (j - k0)];
-          vr = v.x;
-          vi = v.y;
-        } else {
-          const f2 v = Pi[(i - k0) * kPanel + (j - k0)];
-          vr = -v.x;
-          vi = -v.y;
-        }
-        if (last) {
-          vr = tc::to_tf32(vr);
-          vi = tc::to_tf32(vi);
-        }
-        Frow[j] = vr;
-        Frow[n + j] = vi;
+        for (int t = 0; t < 16; ++t) Sg[(c0 + t) * kStageLd + row] = v[t];
       }
+      tc::epilogue_sync();
+      const int cc = ept % 64;
+      const int j = tn * 64 + cc;
+      const bool inJ = j >= k0 && j < k0 + bw;
+      const bool jok = j < n;
+      // rows ept/64, +2, +4, ...: 16 independent loads in flight per thread
+#pragma unroll 1
+      for (int base = ept / 64; base < tc::kBlockM; base += 32) {
+        float cur[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int i = tm * tc::kBlockM + base + 2 * u;
+          const bool inI = i >= k0 && i < k0 + bw;
+          cur[u] = (jok && i < n && !inI && !inJ) ? Fe[(long long)i * ldF + half * n + j] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int rr = base + 2 * u;
+          const int i = tm * tc::kBlockM + rr;
+          if (!jok || i >= n) continue;
+          const bool inI = i >= k0 && i < k0 + bw;
+          float val;
+          if (!inI && !inJ) {
+            val = cur[u] - Sg[cc * kStageLd + rr];
+          } else if (inI && !inJ) {
+            const f2 t2 = T[(long long)j * kPanel + (i - k0)];
+            val = half ? t2.y : t2.x;
+          } else if (!inI && inJ) {
+            const f2 t2 = T[(long long)i * kPanel + (j - k0)];
+            val = half ? t2.y : t2.x;
+          } else {
+            const f2 p2 = Pi[(i - k0) * kPanel + (j - k0)];
+            val = -(half ? p2.y : p2.x);
+          }
+          Fe[(long long)i * ldF + half * n + j] = val;
+          if (Fr) Fr[e * sFr + (long long)i * ldF + half * n + j] = tc::to_tf32(val);
+        }
+      }
+      tc::epilogue_sync();
     }
   }
 };
 
-// Solve product: out[m*ldo + p] = alpha * (S' g)[p, m] (complex64).
+// Solve product: out[m*ldo + p] = alpha * (S' g)[p, m] (complex64); lanes are
+// consecutive rows p, so the stores of a warp are contiguous.
 template <int CB>
 struct SolveEpi {
   f2* out;
   long long sOut, ldo;
   int n, k;
   float alpha;
-  __device__ void operator()(int e, int tm, int tn, int row, uint32_t taddr) const {
+  __device__ void operator()(int e, int tm, int tn, int row, uint32_t taddr, int, uint8_t*) const {
     const int p = tm * tc::kBlockM + row;
     f2* o = out + e * sOut;
 #pragma unroll 1
@@ -332,74 +392,52 @@ __device__ __forceinline__ void write_emb(const Dims& d, float* Bemb, int e, int
   im_row[d.n + p] = tc::to_tf32(g.x);
 }
 
-// forward: g_i = R_i + C_i t (t = S'_{i-1} g_{i-1}; absent for layer 0)
-// R is the real RHS (Rreal) or the complex64 residual of node e (Rc).
-__global__ void __launch_bounds__(256) k_mx_couple_fwd(Dims d, int layer, const cplx* __restrict__ Z,
-                                                       const double* __restrict__ A27, const double* __restrict__ B27,
+// forward: g_i = R_i + C_i t (t = S'_{i-1} g_{i-1}; absent for layer 0); one
+// thread per (row p, column m).  R is the real RHS (Rreal) or the complex64
+// residual of node e (Rc).
+__global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, int layer, const f2* __restrict__ Cf,
                                                        const double* __restrict__ Rreal, const f2* __restrict__ Rc,
                                                        const f2* __restrict__ Tout, f2* __restrict__ Gc,
                                                        float* __restrict__ Bemb) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int e = blockIdx.z;
+  const int m = blockIdx.y, e = blockIdx.z;
   if (p >= d.n) return;
   const long long row = (long long)layer * d.n + p;
-  const int px = p % d.nx, py = p / d.nx;
-  const cplx z = Z[e];
-  f2 c[9];
-  int off[9];
-#pragma unroll
-  for (int t = 0; t < 9; ++t) {
-    const int dx = t % 3 - 1, dy = t / 3 - 1;
-    const bool ok = layer > 0 && px + dx >= 0 && px + dx < d.nx && py + dy >= 0 && py + dy < d.ny;
-    c[t] = ok ? mcoef(A27, B27, d.N, t, row, z) : f2{0.f, 0.f};
-    off[t] = ok ? p + dx + d.nx * dy : p;
-  }
   const long long sG = d.N * d.k;
-  const f2* T = Tout + (long long)e * d.n * d.k;
-  const int m0 = blockIdx.y * 16, m1 = min(d.k, m0 + 16);
-  for (int m = m0; m < m1; ++m) {
-    f2 g = Rc ? Rc[e * sG + (long long)m * d.N + row] : f2{(float)Rreal[(long long)m * d.N + row], 0.f};
-    if (layer > 0) {
+  f2 g = Rc ? Rc[e * sG + (long long)m * d.N + row] : f2{(float)Rreal[(long long)m * d.N + row], 0.f};
+  if (layer > 0) {
+    const f2* T = Tout + ((long long)e * d.k + m) * d.n;
 #pragma unroll
-      for (int t = 0; t < 9; ++t) f2fma(g, c[t], T[(long long)m * d.n + off[t]]);
+    for (int t = 0; t < 9; ++t) {
+      const f2 c = cf_at(d, Cf, e, t, row);
+      if (c.x != 0.f || c.y != 0.f) f2fma(g, c, T[p + (t % 3 - 1) + d.nx * (t / 3 - 1)]);
     }
-    Gc[e * sG + (long long)m * d.N + row] = g;
-    write_emb(d, Bemb, e, p, m, g);
   }
+  Gc[e * sG + (long long)m * d.N + row] = g;
+  write_emb(d, Bemb, e, p, m, g);
 }
 
 // backward: s_i = g_i - U_i x_{i+1} (U_i = M[i, i+1], empty on the top layer)
-__global__ void __launch_bounds__(256) k_mx_couple_bwd(Dims d, int layer, const cplx* __restrict__ Z,
-                                                       const double* __restrict__ A27, const double* __restrict__ B27,
+__global__ void __launch_bounds__(128) k_mx_couple_bwd(Dims d, int layer, const f2* __restrict__ Cf,
                                                        const f2* __restrict__ Gc, float* __restrict__ Bemb) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int e = blockIdx.z;
+  const int m = blockIdx.y, e = blockIdx.z;
   if (p >= d.n) return;
   const long long row = (long long)layer * d.n + p;
-  const int px = p % d.nx, py = p / d.nx;
-  const bool has_next = layer + 1 < d.nz;
-  const cplx z = Z[e];
-  f2 c[9];
-  long long off[9];
-#pragma unroll
-  for (int t = 0; t < 9; ++t) {
-    const int dx = t % 3 - 1, dy = t / 3 - 1;
-    const bool ok = has_next && px + dx >= 0 && px + dx < d.nx && py + dy >= 0 && py + dy < d.ny;
-    c[t] = ok ? mcoef(A27, B27, d.N, 18 + t, row, z) : f2{0.f, 0.f};
-    off[t] = ok ? (long long)d.n + dx + d.nx * dy : 0;
-  }
   const long long sG = d.N * d.k;
-  const int m0 = blockIdx.y * 16, m1 = min(d.k, m0 + 16);
-  for (int m = m0; m < m1; ++m) {
-    const f2* col = Gc + e * sG + (long long)m * d.N + row;
-    f2 s = col[0];
-    f2 u{0.f, 0.f};
+  const f2* col = Gc + e * sG + (long long)m * d.N + row;
+  f2 sv = col[0];
+  if (layer + 1 < d.nz) {
 #pragma unroll
-    for (int t = 0; t < 9; ++t) f2fma(u, c[t], col[off[t]]);
-    s.x -= u.x;
-    s.y -= u.y;
-    write_emb(d, Bemb, e, p, m, s);
+    for (int t = 0; t < 9; ++t) {
+      const f2 c = cf_at(d, Cf, e, 18 + t, row);
+      if (c.x == 0.f && c.y == 0.f) continue;
+      const f2 x = col[d.n + (t % 3 - 1) + d.nx * (t / 3 - 1)];
+      sv.x -= c.x * x.x - c.y * x.y;
+      sv.y -= c.x * x.y + c.y * x.x;
+    }
   }
+  write_emb(d, Bemb, e, p, m, sv);
 }
 
 // ------------------------------------------------------------------ refinement
@@ -422,68 +460,88 @@ __global__ void k_mx_accumulate(long long total, int first, const f2* __restrict
   }
 }
 
-constexpr int kResBlock = 256;
-constexpr int kResCols = 16;
+constexpr int kResRows = 128;      // grid rows per block
+constexpr int kResThreads = 256;   // two columns in flight per row
+constexpr size_t kResSmem = sizeof(cplx) * 27 * kResRows;
 
-// R_e = RHS - (Z_e B - A) Q_e in FP64; stores R as complex64 and per-block
-// partial sums of |R|^2 (and |RHS|^2 for node 0).
-__global__ void __launch_bounds__(kResBlock) k_mx_residual(Dims d, const cplx* __restrict__ Z,
-                                                           const double* __restrict__ A27,
-                                                           const double* __restrict__ B27,
-                                                           const double* __restrict__ RHS,
-                                                           const cplx* __restrict__ Q, f2* __restrict__ Rc,
-                                                           double* __restrict__ partial, const int* __restrict__ active) {
-  const int e = blockIdx.z;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// R_e = RHS - (Z_e B - A) Q_e in FP64 (108 FP64 FMAs per complex entry, the
+// only FP64 arithmetic of the kernel): the block's 128 rows keep their 27
+// complex coefficients in shared memory while the threads sweep the columns.
+// Stores R as complex64 and per-block partial sums of |R|^2 and |RHS|^2.
+__global__ void __launch_bounds__(kResThreads) k_mx_residual(Dims d, const cplx* __restrict__ Z,
+                                                             const double* __restrict__ A27,
+                                                             const double* __restrict__ B27,
+                                                             const double* __restrict__ RHS,
+                                                             const cplx* __restrict__ Q, f2* __restrict__ Rc,
+                                                             double* __restrict__ partial,
+                                                             const int* __restrict__ active) {
+  extern __shared__ cplx rsm[];
+  __shared__ double red[2][kResThreads];
+  const int e = blockIdx.y;
+  const int tid = threadIdx.x;
+  if (!active[e]) return;   // block-uniform; the norm kernel ignores inactive nodes
+  const long long i0 = (long long)blockIdx.x * kResRows;
+  const cplx z = Z[e];
+  for (int t = tid; t < 27 * kResRows; t += kResThreads) {
+    const int s = t / kResRows, r = t % kResRows;
+    const long long i = i0 + r;
+    cplx c{0.0, 0.0};
+    if (i < d.N) {
+      const int ix = (int)(i % d.nx), iy = (int)((i / d.nx) % d.ny), iz = (int)(i / d.n);
+      const int dx = slot_dx(s), dy = slot_dy(s), dz = slot_dz(s);
+      if (ix + dx >= 0 && ix + dx < d.nx && iy + dy >= 0 && iy + dy < d.ny && iz + dz >= 0 && iz + dz < d.nz) {
+        const double a = A27[(long long)s * d.N + i], b = B27[(long long)s * d.N + i];
+        c = cplx{z.re * b - a, z.im * b};
+      }
+    }
+    rsm[t] = c;
+  }
+  __syncthreads();
+  const int r = tid % kResRows;
+  const long long i = i0 + r;
   double rr = 0.0, bb = 0.0;
-  if (active[e] && i < d.N) {
+  if (i < d.N) {
     const int ix = (int)(i % d.nx), iy = (int)((i / d.nx) % d.ny), iz = (int)(i / d.n);
-    const cplx z = Z[e];
-    cplx c[27];
-    long long off[27];
+    int off[27];
 #pragma unroll
     for (int s = 0; s < 27; ++s) {
       const int dx = slot_dx(s), dy = slot_dy(s), dz = slot_dz(s);
       const bool ok = ix + dx >= 0 && ix + dx < d.nx && iy + dy >= 0 && iy + dy < d.ny && iz + dz >= 0 &&
                       iz + dz < d.nz;
-      const double a = ok ? A27[(long long)s * d.N + i] : 0.0;
-      const double b = ok ? B27[(long long)s * d.N + i] : 0.0;
-      c[s] = cplx{z.re * b - a, z.im * b};
-      off[s] = ok ? (long long)dx + (long long)d.nx * (dy + (long long)d.ny * dz) : 0;
+      off[s] = ok ? dx + d.nx * (dy + d.ny * dz) : 0;
     }
     const long long sG = d.N * d.k;
-    const int m0 = blockIdx.y * kResCols, m1 = min(d.k, m0 + kResCols);
-    for (int m = m0; m < m1; ++m) {
+    for (int m = tid / kResRows; m < d.k; m += kResThreads / kResRows) {
       const cplx* q = Q + e * sG + (long long)m * d.N + i;
       const double b = RHS[(long long)m * d.N + i];
-      cplx acc = cplx{b, 0.0};
+      double are = b, aim = 0.0;
 #pragma unroll
       for (int s = 0; s < 27; ++s) {
+        const cplx c = rsm[s * kResRows + r];
         const cplx v = q[off[s]];
-        acc.re -= c[s].re * v.re - c[s].im * v.im;
-        acc.im -= c[s].re * v.im + c[s].im * v.re;
+        are = fma(-c.re, v.re, are);
+        are = fma(c.im, v.im, are);
+        aim = fma(-c.re, v.im, aim);
+        aim = fma(-c.im, v.re, aim);
       }
-      Rc[e * sG + (long long)m * d.N + i] = f2{(float)acc.re, (float)acc.im};
-      rr += acc.re * acc.re + acc.im * acc.im;
+      Rc[e * sG + (long long)m * d.N + i] = f2{(float)are, (float)aim};
+      rr += are * are + aim * aim;
       bb += b * b;
     }
   }
-  __shared__ double red[2][kResBlock];
-  red[0][threadIdx.x] = rr;
-  red[1][threadIdx.x] = bb;
+  red[0][tid] = rr;
+  red[1][tid] = bb;
   __syncthreads();
-  for (int w = kResBlock / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      red[0][threadIdx.x] += red[0][threadIdx.x + w];
-      red[1][threadIdx.x] += red[1][threadIdx.x + w];
+  for (int w = kResThreads / 2; w > 0; w >>= 1) {
+    if (tid < w) {
+      red[0][tid] += red[0][tid + w];
+      red[1][tid] += red[1][tid + w];
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    const long long nblk = (long long)gridDim.x * gridDim.y;
-    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-    partial[(long long)e * nblk * 2 + 2 * b] = red[0][0];
-    partial[(long long)e * nblk * 2 + 2 * b + 1] = red[1][0];
+  if (tid == 0) {
+    partial[((long long)e * gridDim.x + blockIdx.x) * 2] = red[0][0];
+    partial[((long long)e * gridDim.x + blockIdx.x) * 2 + 1] = red[1][0];
   }
 }
 
@@ -543,21 +601,22 @@ bool make_map(CUtensorMap* map, const float* base, long long inner, long long ro
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, class Epi>
+template <int BN, int STAGES, class Epi>
 cudaError_t launch_tc(cudaStream_t s, dim3 grid, const CUtensorMap& a, const CUtensorMap& b, tc::Geom geo,
                       const Epi& epi, int* status) {
-  constexpr size_t smem = tc::Smem<BN>::kBytes;
+  constexpr size_t smem = tc::Smem<BN, STAGES>::kBytes;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc::k_tc_gemm<BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(tc::k_tc_gemm<BN, STAGES, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  tc::k_tc_gemm<BN, Epi><<<grid, tc::kThreads, smem, s>>>(a, b, geo, epi, status);
+  tc::k_tc_gemm<BN, STAGES, Epi><<<grid, tc::kThreads, smem, s>>>(a, b, geo, epi, status);
   return cudaGetLastError();
 }
 
-enum Buf { B_F = 0, B_T1, B_AOP, B_BOP, B_TC, B_PINV, B_GC, B_RC, B_BEMB, B_TOUT, B_PART, B_REL, B_ACTIVE, B_COUNT };
+enum Buf { B_F = 0, B_T1, B_AOP, B_BOP, B_TC, B_PINV, B_GC, B_RC, B_BEMB, B_TOUT, B_PART, B_REL, B_ACTIVE, B_CF, B_FW, B_COUNT };
 
 bool ensure(MixedWork& w, int idx, size_t bytes, cudaStream_t s, bool zero = false) {
   if (w.sizes[idx] >= bytes && w.bufs[idx]) {
@@ -615,38 +674,55 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
   if (!encode_fn()) return "cuTensorMapEncodeTiled is not available from the driver";
   const size_t fbytes = sizeof(float) * (size_t)Ne * d.nz * d.n * d.ldF;
   if (!ensure(w, B_F, fbytes, s)) return "out of device memory (mixed factors)";
+  if (!ensure(w, B_FW, sizeof(float) * (size_t)Ne * 2 * d.n * d.ldF, s)) return "out of device memory (working layers)";
   if (!ensure(w, B_T1, sizeof(float) * (size_t)Ne * d.n * d.ldF, s)) return "out of device memory (schur scratch)";
   if (!ensure(w, B_AOP, sizeof(float) * (size_t)Ne * d.n * 2 * kPanel, s, true)) return "out of device memory";
   if (!ensure(w, B_BOP, sizeof(float) * (size_t)Ne * d.nblk64 * 128 * 2 * kPanel, s, true)) return "out of device memory";
   if (!ensure(w, B_TC, sizeof(f2) * (size_t)Ne * d.n * kPanel, s)) return "out of device memory";
   if (!ensure(w, B_PINV, sizeof(f2) * (size_t)Ne * kPanel * kPanel, s)) return "out of device memory";
+  if (!ensure(w, B_CF, sizeof(f2) * (size_t)Ne * 27 * d.N, s)) return "out of device memory (coefficients)";
   // The row-split padding [2n, ldF) is never read (the tensor maps stop at 2n).
-  float* F = buf<float>(w, B_F);
+  float* Fr = buf<float>(w, B_F);    // TF32-rounded S'_i of every layer (solve operand)
+  float* F = buf<float>(w, B_FW);    // fp32 working layers (ping-pong)
   float* Aop = buf<float>(w, B_AOP);
   float* Bop = buf<float>(w, B_BOP);
+  f2* Cf = buf<f2>(w, B_CF);
+  k_mx_coef<<<dim3((unsigned)std::min<long long>(4096, (27 * d.N + 255) / 256), Ne), 256, 0, s>>>(d, Z, A27, B27, Cf);
+  prof::count_launch();
   CUtensorMap tmA, tmB;
   if (!make_map(&tmA, Aop, 2 * kPanel, (long long)Ne * d.n, 2 * kPanel, 128)) return "tensor map (Aop) rejected";
   if (!make_map(&tmB, Bop, 2 * kPanel, (long long)Ne * d.nblk64 * 128, 2 * kPanel, 128))
     return "tensor map (Bop) rejected";
-  const size_t panel_smem = sizeof(f2) * ((size_t)kPanel * (kPanel + 1) + (size_t)kRowsPerPanelCta * (kPanel + 1) + kPanel);
-  static bool panel_attr = false;
-  if (!panel_attr) {
-    cudaFuncSetAttribute(k_mx_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem);
-    panel_attr = true;
-  }
-  const long long sF = (long long)d.nz * d.n * d.ldF;
+  const long long sF = 2LL * d.n * d.ldF;
+  const long long sFr = (long long)d.nz * d.n * d.ldF;
   for (int layer = 0; layer < d.nz; ++layer) {
+    prof::begin(s, prof::SCHUR);
+    prof::add_work(prof::SCHUR, (layer > 0 ? 144.0 : 0.0) * d.n * (double)d.n * Ne);
     if (layer > 0)
-      k_mx_schur1<<<dim3(cdiv(d.n, 256), d.n, Ne), 256, 0, s>>>(d, layer, Z, A27, B27, F, buf<float>(w, B_T1));
-    k_mx_schur2<<<dim3(cdiv(d.n, 256), d.n, Ne), 256, 0, s>>>(d, layer, Z, A27, B27, buf<float>(w, B_T1), F);
+      k_mx_schur1<<<dim3(cdiv(d.n, 256), d.n, Ne), 256, 0, s>>>(d, layer, Cf, F, buf<float>(w, B_T1));
+    k_mx_schur2<<<dim3(cdiv(d.n, 256), d.n, Ne), 256, 0, s>>>(d, layer, Cf, buf<float>(w, B_T1), F);
+    prof::end(s, prof::SCHUR);
+    prof::count_launch(layer > 0 ? 2 : 1);
     for (int k0 = 0; k0 < d.n; k0 += kPanel) {
       const int bw = d.n - k0 < kPanel ? d.n - k0 : kPanel;
-      k_mx_panel<<<dim3(cdiv(d.n, kRowsPerPanelCta), Ne), 256, panel_smem, s>>>(
-          d, layer, k0, bw, F, Aop, Bop, buf<f2>(w, B_TC), buf<f2>(w, B_PINV), status);
-      SweepEpi epi{F + (long long)layer * d.n * d.ldF, sF, d.ldF, d.n, k0, bw, k0 + kPanel >= d.n,
-                   buf<f2>(w, B_TC), buf<f2>(w, B_PINV)};
+      prof::begin(s, prof::PINV);
+      prof::add_work(prof::PINV, 8.0 * kPanel * kPanel * kPanel * Ne);
+      k_mx_pinv<<<Ne, kPinvThreads, 0, s>>>(d, layer, k0, bw, F, buf<f2>(w, B_PINV), status);
+      prof::end(s, prof::PINV);
+      prof::begin(s, prof::PANEL_T);
+      prof::add_work(prof::PANEL_T, 8.0 * d.n * kPanel * kPanel * Ne);
+      k_mx_panel_T<<<dim3(cdiv(d.n, kRowsPerPanelCta), Ne), 256, 0, s>>>(d, layer, k0, bw, F, buf<f2>(w, B_PINV), Aop,
+                                                                       Bop, buf<f2>(w, B_TC));
+      prof::end(s, prof::PANEL_T);
+      prof::count_launch(3);
+      const bool last = k0 + kPanel >= d.n;
+      SweepEpi epi{F + (long long)(layer & 1) * d.n * d.ldF, sF, last ? Fr + (long long)layer * d.n * d.ldF : nullptr,
+                   sFr, d.ldF, d.n, k0, bw, buf<f2>(w, B_TC), buf<f2>(w, B_PINV)};
       tc::Geom geo{0, d.n, 0, d.nblk64 * 128, (2 * kPanel) / tc::kBlockK};
-      cudaError_t err = launch_tc<128>(s, dim3(d.nblk64, cdiv(d.n, 128), Ne), tmA, tmB, geo, epi, status);
+      prof::begin(s, prof::SWEEP_GEMM);
+      prof::add_work(prof::SWEEP_GEMM, 8.0 * d.n * (double)d.n * bw * Ne);
+      cudaError_t err = launch_tc<128, 2>(s, dim3(d.nblk64, cdiv(d.n, 128), Ne), tmA, tmB, geo, epi, status);
+      prof::end(s, prof::SWEEP_GEMM);
       if (err != cudaSuccess) return "tcgen05 sweep-update launch failed";
     }
   }
@@ -669,23 +745,31 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
   if (!make_map(&tmB, Bemb, 2 * d.n, (long long)d.Ne * d.nblkCB * 2 * CB, d.ldB, 2 * CB))
     return "tensor map (rhs) rejected";
   const int nk = (2 * d.n + tc::kBlockK - 1) / tc::kBlockK;
-  const dim3 cgrid(cdiv(d.n, 256), cdiv(d.k, 16), d.Ne);
+  const f2* Cf = buf<f2>(w, B_CF);
+  const dim3 cgrid(cdiv(d.n, 128), d.k, d.Ne);
   const dim3 ggrid(d.nblkCB, cdiv(d.n, 128), d.Ne);
   // forward sweep
-  k_mx_couple_fwd<<<cgrid, 256, 0, s>>>(d, 0, Z, A27, B27, Rreal, Rc, Tout, Gc, Bemb);
+  k_mx_couple_fwd<<<cgrid, 128, 0, s>>>(d, 0, Cf, Rreal, Rc, Tout, Gc, Bemb);
   for (int i = 1; i < d.nz; ++i) {
     SolveEpi<CB> epi{Tout, (long long)d.n * d.k, d.n, d.n, d.k, 1.0f};
     tc::Geom geo{(i - 1) * d.n, d.nz * d.n, 0, d.nblkCB * 2 * CB, nk};
-    if (launch_tc<2 * CB>(s, ggrid, tmF, tmB, geo, epi, status) != cudaSuccess) return "tcgen05 solve launch failed";
-    k_mx_couple_fwd<<<cgrid, 256, 0, s>>>(d, i, Z, A27, B27, Rreal, Rc, Tout, Gc, Bemb);
+    prof::begin(s, prof::SOLVE_GEMM);
+    prof::add_work(prof::SOLVE_GEMM, 8.0 * d.n * (double)d.n * d.k * d.Ne);
+    if (launch_tc<2 * CB, 4>(s, ggrid, tmF, tmB, geo, epi, status) != cudaSuccess) return "tcgen05 solve launch failed";
+    prof::end(s, prof::SOLVE_GEMM);
+    k_mx_couple_fwd<<<cgrid, 128, 0, s>>>(d, i, Cf, Rreal, Rc, Tout, Gc, Bemb);
   }
   // backward sweep: x_i overwrites g_i
   for (int i = d.nz - 1; i >= 0; --i) {
-    k_mx_couple_bwd<<<cgrid, 256, 0, s>>>(d, i, Z, A27, B27, Gc, Bemb);
+    k_mx_couple_bwd<<<cgrid, 128, 0, s>>>(d, i, Cf, Gc, Bemb);
     SolveEpi<CB> epi{Gc + (long long)i * d.n, d.N * d.k, d.N, d.n, d.k, -1.0f};
     tc::Geom geo{i * d.n, d.nz * d.n, 0, d.nblkCB * 2 * CB, nk};
-    if (launch_tc<2 * CB>(s, ggrid, tmF, tmB, geo, epi, status) != cudaSuccess) return "tcgen05 solve launch failed";
+    prof::begin(s, prof::SOLVE_GEMM);
+    prof::add_work(prof::SOLVE_GEMM, 8.0 * d.n * (double)d.n * d.k * d.Ne);
+    if (launch_tc<2 * CB, 4>(s, ggrid, tmF, tmB, geo, epi, status) != cudaSuccess) return "tcgen05 solve launch failed";
+    prof::end(s, prof::SOLVE_GEMM);
   }
+  prof::count_launch(4 * d.nz - 2 + 2);
   return nullptr;
 }
 
@@ -715,8 +799,13 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
   const bool shape_changed = w.sizes[B_BEMB] != bemb || w.bemb_k != k;
   if (!ensure(w, B_BEMB, bemb, s, shape_changed)) return "out of device memory";
   w.bemb_k = k;
-  const dim3 rgrid(cdiv(d.N, kResBlock), cdiv(k, kResCols), Ne);
-  const long long nblk = (long long)rgrid.x * rgrid.y;
+  const dim3 rgrid(cdiv(d.N, kResRows), Ne);
+  const long long nblk = rgrid.x;
+  static bool res_attr = false;
+  if (!res_attr) {
+    cudaFuncSetAttribute(k_mx_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResSmem);
+    res_attr = true;
+  }
   if (!ensure(w, B_PART, sizeof(double) * 2 * (size_t)Ne * nblk, s)) return "out of device memory";
   if (!ensure(w, B_REL, sizeof(double) * Ne, s)) return "out of device memory";
   if (!ensure(w, B_ACTIVE, sizeof(int) * Ne, s)) return "out of device memory";
@@ -727,10 +816,19 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
   // first solve: Q_e = M~^{-1} RHS
   if (const char* m = solve_once(s, d, Z, A27, B27, w, RHS, nullptr, status)) return m;
   k_mx_accumulate<<<dim3(acc_blocks, Ne), 256, 0, s>>>(sG, 1, buf<f2>(w, B_GC), G, buf<int>(w, B_ACTIVE));
+  prof::count_launch();
   int steps = 0;
   for (;;) {
-    k_mx_residual<<<rgrid, kResBlock, 0, s>>>(d, Z, A27, B27, RHS, G, buf<f2>(w, B_RC), buf<double>(w, B_PART),
-                                              buf<int>(w, B_ACTIVE));
+    prof::begin(s, prof::RESIDUAL);
+    {
+      int nact = 0;
+      for (int e = 0; e < Ne; ++e) nact += active[e];
+      prof::add_work(prof::RESIDUAL, 216.0 * (double)d.N * k * nact);   // 108 FP64 FMAs per complex entry
+    }
+    k_mx_residual<<<rgrid, kResThreads, kResSmem, s>>>(d, Z, A27, B27, RHS, G, buf<f2>(w, B_RC),
+                                                       buf<double>(w, B_PART), buf<int>(w, B_ACTIVE));
+    prof::end(s, prof::RESIDUAL);
+    prof::count_launch(2);
     k_mx_resnorm<<<Ne, 256, 0, s>>>(Ne, nblk, buf<double>(w, B_PART), buf<double>(w, B_REL), buf<int>(w, B_ACTIVE));
     int st = 0;
     cudaMemcpyAsync(rel.data(), w.bufs[B_REL], sizeof(double) * Ne, cudaMemcpyDeviceToHost, s);
@@ -750,6 +848,7 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
     cudaMemcpyAsync(w.bufs[B_ACTIVE], active.data(), sizeof(int) * Ne, cudaMemcpyHostToDevice, s);
     if (const char* m = solve_once(s, d, Z, A27, B27, w, nullptr, buf<f2>(w, B_RC), status)) return m;
     k_mx_accumulate<<<dim3(acc_blocks, Ne), 256, 0, s>>>(sG, 0, buf<f2>(w, B_GC), G, buf<int>(w, B_ACTIVE));
+    prof::count_launch();
     ++steps;
   }
   if (stats) {

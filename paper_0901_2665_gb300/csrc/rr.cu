@@ -1,6 +1,7 @@
 // Rayleigh-Ritz in FP64 (Fig. 2 steps 3-5; Eqs. 6-9) and the residuals of
 // Table I.
 #include "kernels.cuh"
+#include "prof.cuh"
 
 namespace feast {
 
@@ -383,13 +384,16 @@ void gram(cudaStream_t s, long long N, int k1, int k2, const double* X, const do
   const int nchunks = cdiv(N, kGramRows);
   dim3 grid(cdiv(k1, kGramTile), cdiv(k2, kGramTile), nchunks);
   k_gram_partial<<<grid, 256, 0, s>>>(N, k1, k2, X, Y, partial);
+  prof::count_launch();
   const int total = k1 * k2;
   k_gram_reduce<<<cdiv(total, 256), 256, 0, s>>>(nchunks, total, partial, out);
+  prof::count_launch();
 }
 
 void dgemm_tall(cudaStream_t s, long long N, int m, int k, const double* Q, const double* P, double* C) {
   dim3 grid(cdiv(N, 64), cdiv(k, 64));
   k_dgemm_tall<<<grid, 256, 0, s>>>(N, m, k, Q, P, C);
+  prof::count_launch();
 }
 
 void reduced_eig(cudaStream_t s, int m, const double* AQ, const double* BQ, double* eps, double* Phi,
@@ -402,16 +406,19 @@ void reduced_eig(cudaStream_t s, int m, const double* AQ, const double* BQ, doub
     attr_set = true;
   }
   k_reduced_eig<<<1, 1024, smem, s>>>(m, AQ, BQ, eps, Phi, work, status);
+  prof::count_launch();
 }
 
 void residual_norms(cudaStream_t s, long long N, int k, const double* AX, const double* BX,
                     const double* lambda, const double* X, double* out) {
   k_residual_norms<<<k, 256, 0, s>>>(N, AX, BX, lambda, X, out);
+  prof::count_launch();
 }
 
 void residual_finish(cudaStream_t s, int k, const double* norms, const double* normA, double* resid,
                      double* resid_paper) {
   k_residual_finish<<<cdiv(k, 128), 128, 0, s>>>(k, norms, normA, resid, resid_paper);
+  prof::count_launch();
 }
 
 void permute_columns(cudaStream_t s, long long N, int k, const int* perm, const double* src, double* dst) {
@@ -419,6 +426,7 @@ void permute_columns(cudaStream_t s, long long N, int k, const int* perm, const 
   int blocks = (int)((total + 255) / 256);
   if (blocks > 152 * 32) blocks = 152 * 32;
   k_permute_columns<<<blocks, 256, 0, s>>>(N, k, perm, src, dst);
+  prof::count_launch();
 }
 
 }  // namespace feast

@@ -1,6 +1,7 @@
 // 27-point stencil products, layer couplings of the node systems and the
 // quadrature sum (Fig. 2 steps 2, 3, 6; Eq. 15).
 #include "kernels.cuh"
+#include "prof.cuh"
 
 namespace feast {
 
@@ -194,16 +195,19 @@ void stencil_apply(cudaStream_t s, Grid g, const double* C27, const double* X, l
   if (g.N() == 0 || k == 0) return;
   dim3 grid(cdiv(g.N(), 256), cdiv(k, kColsPerThread));
   k_stencil_apply<<<grid, 256, 0, s>>>(g, C27, X, ldx, Y, ldy, k);
+  prof::count_launch();
 }
 
 void random_block(cudaStream_t s, long long N, int k, uint64_t seed, double* Y) {
   long long total = N * k;
   if (total == 0) return;
   k_random_block<<<grid1d(total, 256), 256, 0, s>>>(total, seed, Y);
+  prof::count_launch();
 }
 
 void stencil_norm1(cudaStream_t s, Grid g, const double* A27, double* out) {
   k_stencil_norm1<<<1, 256, 0, s>>>(g, A27, out);
+  prof::count_launch();
 }
 
 void couple_forward(cudaStream_t s, Grid g, int layer, int Ne, const cplx* Z, const double* A27,
@@ -211,12 +215,14 @@ void couple_forward(cudaStream_t s, Grid g, int layer, int Ne, const cplx* Z, co
                     long long sG, int k) {
   dim3 grid(cdiv(g.n(), 256), cdiv(k, kColsPerThread), Ne);
   k_couple_forward<<<grid, 256, 0, s>>>(g, layer, Z, A27, B27, RHS, Tmp, sT, G, sG, k);
+  prof::count_launch();
 }
 
 void couple_backward(cudaStream_t s, Grid g, int layer, int Ne, const cplx* Z, const double* A27,
                      const double* B27, const cplx* G, long long sG, cplx* Tmp, long long sT, int k) {
   dim3 grid(cdiv(g.n(), 256), cdiv(k, kColsPerThread), Ne);
   k_couple_backward<<<grid, 256, 0, s>>>(g, layer, Z, A27, B27, G, sG, Tmp, sT, k);
+  prof::count_launch();
 }
 
 void quadrature_sum(cudaStream_t s, long long N, int k, int Ne, const cplx* coef, const cplx* G,
@@ -224,6 +230,7 @@ void quadrature_sum(cudaStream_t s, long long N, int k, int Ne, const cplx* coef
   long long total = N * k;
   if (total == 0) return;
   k_quadrature_sum<<<grid1d(total, 256), 256, 0, s>>>(N, k, Ne, coef, G, sG, Q);
+  prof::count_launch();
 }
 
 void rhs_to_complex(cudaStream_t s, long long rows, int k, int Ne, const double* RHS, long long ldr,
@@ -232,6 +239,7 @@ void rhs_to_complex(cudaStream_t s, long long rows, int k, int Ne, const double*
   if (total == 0) return;
   dim3 grid(grid1d(total, 256), Ne);
   k_rhs_to_complex<<<grid, 256, 0, s>>>(rows, k, RHS, ldr, G, ldg, sG);
+  prof::count_launch();
 }
 
 }  // namespace feast

@@ -19,7 +19,6 @@
 namespace feast {
 namespace tc {
 
-constexpr int kStages = 4;
 constexpr int kBlockM = 128;
 constexpr int kBlockK = 32;                      // fp32 elements per 128-byte swizzle row
 constexpr int kATileBytes = kBlockM * kBlockK * 4;   // 16 KB
@@ -153,22 +152,29 @@ struct Geom {
   int nk;
 };
 
-template <int BN>
+template <int BN, int STAGES>
 struct Smem {
   static constexpr int kBTileBytes = BN * kBlockK * 4;
   static constexpr int kStageBytes = kATileBytes + kBTileBytes;
   static constexpr int kTmemCols = BN < 32 ? 32 : BN;
-  static constexpr size_t kBytes = 1024 /*align slack*/ + (size_t)kStages * kStageBytes + 256;
+  static constexpr size_t kPipeBytes = (size_t)STAGES * kStageBytes;
+  static constexpr size_t kBytes = 1024 /*align slack*/ + kPipeBytes + 256;
 };
 
-// Epilogue contract: epi(e, tm, tn, row, lane_taddr, BN) with row in [0, 128)
-// the accumulator row of this thread and lane_taddr the TMEM address of its
-// lane at column 0.
-template <int BN, class Epi>
-__global__ void __launch_bounds__(kThreads, 1)
+// Named barrier of the 128 epilogue threads (warps 2-5).
+__device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Epilogue contract: epi(e, tm, tn, row, lane_taddr, ept, stage) with row in
+// [0, 128) the accumulator row (TMEM lane) of this thread, lane_taddr the TMEM
+// address of that lane at column 0, ept in [0, 128) the thread's index in the
+// epilogue group and stage the pipeline shared memory (Smem::kPipeBytes),
+// free for reuse once the accumulator is complete.
+template <int BN, int STAGES, class Epi>
+__global__ void __launch_bounds__(kThreads)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Geom geo, Epi epi,
               int* status) {
-  using S = Smem<BN>;
+  using S = Smem<BN, STAGES>;
+  constexpr int kStages = STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -241,9 +247,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     const int q = warp % 4;
     const int row = q * 32 + lane;
-    const bool ok = mbar_wait(tfull, 0, status, abort_flag);
+    mbar_wait(tfull, 0, status, abort_flag);
     tc_fence_after();
-    if (ok && !*abort_flag) epi(e, tm, tn, row, tmem + (static_cast<uint32_t>(q * 32) << 16));
+    // one decision for the whole epilogue group: a thread that gave up set
+    // the flag before this barrier, so all 128 threads read the same value
+    epilogue_sync();
+    if (!*abort_flag)
+      epi(e, tm, tn, row, tmem + (static_cast<uint32_t>(q * 32) << 16), static_cast<int>(threadIdx.x) - 64, smem);
   }
   tc_fence_before();
   __syncthreads();
