@@ -222,6 +222,36 @@ feast_status feast_rayleigh_ritz(feast_handle* h, const feast_operator* op, cons
 feast_status feast_residuals(feast_handle* h, const feast_operator* op, const double* lambda,
                              const double* X, int k, double* resid, double* resid_paper);
 
+/*
+ * Allocation-free reduced eigensolve.  The paper has no counterpart: this is
+ * a library convenience.  It computes exactly what feast_reduced_eig computes
+ * (same kernel), for callers that cannot call cudaMalloc: code that must keep
+ * every device byte under its own allocator or a budget fixed at start-up
+ * (a framework memory pool, a co-scheduled process with a hard memory cap),
+ * and paths where an allocation's implicit synchronisation or its failure in
+ * the middle of work is not acceptable.  It needs no handle.
+ *
+ * AQ, BQ (M0 x M0, column-major), eps (M0) and Phi (M0 x M0) are DEVICE
+ * pointers owned by the caller; 1 <= M0 <= 128.  The work space (3 * 128 * 128
+ * doubles plus a status word, about 385 KB) is a fixed device array inside the
+ * library that every GPU which loads the library holds until the process
+ * exits.  Nothing is allocated or freed per call.
+ *
+ * The first call on a device, with that device current, looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  Work is ordered on cuda_stream (NULL = legacy
+ * default stream) and the call synchronises that stream to read the status.
+ * Every call shares the one array, which keeps the last call's contents (the
+ * status word is cleared at the start of each call): calls whose work overlaps
+ * on the GPU, from two streams or two host threads, race on it.
+ *
+ * Returns FEAST_ERR_ARG for M0 outside [1, 128] or a NULL pointer (nothing is
+ * launched), FEAST_ERR_BQ_NOT_SPD, FEAST_ERR_JACOBI or FEAST_ERR_CUDA as
+ * feast_reduced_eig does, else FEAST_OK.
+ */
+feast_status feast_reduced_eig_noalloc(const double* AQ, const double* BQ, int M0, double* eps, double* Phi,
+                                       void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

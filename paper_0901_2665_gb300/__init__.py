@@ -45,7 +45,7 @@ FEAST_PREC_MIXED = 1
 EXPORTED = [
     "feast_default_options", "feast_init", "feast_destroy", "feast_last_error", "feast_get_info",
     "feast_solve", "feast_contour", "feast_stencil_apply", "feast_node_solve", "feast_quadrature",
-    "feast_reduced_eig", "feast_rayleigh_ritz", "feast_residuals",
+    "feast_reduced_eig", "feast_rayleigh_ritz", "feast_residuals", "feast_reduced_eig_noalloc",
 ]
 
 
@@ -92,6 +92,7 @@ _lib.feast_quadrature.argtypes = [_vp, ctypes.POINTER(feast_operator), _d, _d, _
 _lib.feast_reduced_eig.argtypes = [_vp, _vp, _vp, _i, _vp, _vp]
 _lib.feast_rayleigh_ritz.argtypes = [_vp, ctypes.POINTER(feast_operator), _vp, _i, _vp, _vp, _vp, _vp]
 _lib.feast_residuals.argtypes = [_vp, ctypes.POINTER(feast_operator), _vp, _vp, _i, _vp, _vp]
+_lib.feast_reduced_eig_noalloc.argtypes = [_vp, _vp, _i, _vp, _vp, _vp]
 for _f in EXPORTED:
     if _f not in ("feast_default_options", "feast_last_error"):
         getattr(_lib, _f).restype = ctypes.c_int
@@ -226,6 +227,13 @@ class Handle:
     def feast_residuals(self, op, lam, X, k, resid, resid_paper=None):
         self._check(_lib.feast_residuals(self._h, ctypes.byref(op), _ptr(lam), _ptr(X), int(k), _ptr(resid),
                                          _ptr(resid_paper)), "feast_residuals")
+
+
+def feast_reduced_eig_noalloc(AQ, BQ, M0, eps, Phi, stream=None) -> int:
+    """Allocation-free reduced eigensolve (no handle; device buffers).  Returns
+    the feast_status code (FEAST_OK, FEAST_ERR_ARG, FEAST_ERR_BQ_NOT_SPD, ...)."""
+    return _lib.feast_reduced_eig_noalloc(_ptr(AQ), _ptr(BQ), int(M0), _ptr(eps), _ptr(Phi),
+                                          stream if stream is not None else _current_stream())
 
 
 def library_path() -> str:

@@ -430,3 +430,70 @@ void permute_columns(cudaStream_t s, long long N, int k, const int* perm, const 
 }
 
 }  // namespace feast
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the reduced eigensolve (declared in feast.h).
+// Its scratch (three M0 x M0 work matrices and the device status word) is
+// a file-scope device array that every GPU loading this library holds until
+// the process exits; nothing is allocated per call.
+#include <mutex>
+
+#include "../../include/feast.h"
+
+namespace {
+
+constexpr int kNoAllocMaxM0 = 128;
+constexpr int kNoAllocWork = 3 * kNoAllocMaxM0 * kNoAllocMaxM0;   // doubles of eigensolve work space
+constexpr int kNoAllocDoubles = kNoAllocWork + 32;                // + the status word (and padding)
+
+__device__ __align__(256) double g_reduced_eig_scratch[kNoAllocDoubles];
+
+std::mutex g_noalloc_mutex;
+double* g_noalloc_base[256] = {};   // device address of the array, per device ordinal
+
+}  // namespace
+
+extern "C" feast_status feast_reduced_eig_noalloc(const double* AQ, const double* BQ, int M0, double* eps,
+                                                  double* Phi, void* cuda_stream) {
+  if (M0 < 1 || M0 > kNoAllocMaxM0 || !AQ || !BQ || !eps || !Phi) return FEAST_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    cudaGetLastError();
+    return FEAST_ERR_CUDA;
+  }
+  double* base = nullptr;
+  {
+    // set-up, once per device and with that device current: the host-side
+    // name of the array is not a device address, so ask the runtime for it
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_base[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_reduced_eig_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return FEAST_ERR_CUDA;
+      }
+      g_noalloc_base[dev] = static_cast<double*>(p);
+    }
+    base = g_noalloc_base[dev];
+  }
+  int* status = reinterpret_cast<int*>(base + kNoAllocWork);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  // the array keeps the previous call's contents: the status word must start at 0
+  if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) {
+    cudaGetLastError();
+    return FEAST_ERR_CUDA;
+  }
+  feast::reduced_eig(s, M0, AQ, BQ, eps, Phi, base, status);
+  int st = 0;
+  if (cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return FEAST_ERR_CUDA;
+  }
+  switch (st) {
+    case feast::DEV_OK: return FEAST_OK;
+    case feast::DEV_BQ_NOT_SPD: return FEAST_ERR_BQ_NOT_SPD;
+    case feast::DEV_JACOBI: return FEAST_ERR_JACOBI;
+    default: return FEAST_ERR_CUDA;
+  }
+}
