@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--layers", type=int, default=400,
+                    help="z-layers of the workload (400; fewer only to bound a profiler capture)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--sample-layers", type=int, default=8, help=argparse.SUPPRESS)
     ap.add_argument("--loops", type=int, default=4, help=argparse.SUPPRESS)
@@ -265,6 +267,15 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     wl = workloads.WORKLOADS[WORKLOAD]
     iv = load_interval()
+    if args.layers != wl.nz:
+        # reduced layer count (profiling only): same grid family and potential
+        # law; interval from the V = 0 tensor-product spectrum, M not certified
+        wl = workloads.Workload(wl.name, wl.nx, wl.ny, args.layers, wl.gaussians, wl.M, wl.M0)
+        h0 = 1.0 / (wl.nx + 1)
+        mu = lambda m: (6 / h0 ** 2) * (1 - np.cos(np.arange(1, m + 1) * np.pi / (m + 1))) / (  # noqa: E731
+            2 + np.cos(np.arange(1, m + 1) * np.pi / (m + 1)))
+        lam0 = np.sort((0.5 * (mu(wl.nx)[:, None, None] + mu(wl.ny)[None, :, None] + mu(wl.nz)[None, None, :])).ravel())
+        iv = {"lmin": float(lam0[0] - 4.0), "lmax": float(0.5 * (lam0[89] + lam0[90])), "M": -1}
     op = wl.operator(0)
     N, n, nb, M0, Ne, M = op.N, op.n, op.nz, wl.M0, wl.Ne, iv["M"]
     A = torch.from_numpy(op.A27).to(dev)
@@ -279,7 +290,7 @@ def run_ours(args):
 
     def step():
         r = h.feast_solve(dop, iv["lmin"], iv["lmax"], M0, Ne, wl.tol, None, lam, X, resid, allow=())
-        ok = (r.m_found == M and r.info.resid_max <= 1e-10)
+        ok = ((r.m_found == M or M < 0) and r.info.resid_max <= 1e-10)
         return r, ok
 
     for _ in range(args.warmup):

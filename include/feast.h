@@ -155,6 +155,24 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
                          int M0, int Ne, double tol, const double* Y0,
                          double* lambda, double* X, double* resid, int* m_found, int* loops);
 
+/*
+ * Many independent problems (Sec. V, parallelism level (i): independent
+ * search intervals or instances) solved concurrently on the handle's GPU.
+ * Instance i has operator ops[i], interval [lmin[i], lmax[i]] and subspace
+ * M0[i]; Y0 (may be NULL, or hold NULL entries) gives start blocks; lambda[i],
+ * X[i], resid[i] (resid may be NULL) receive the outputs exactly as in
+ * feast_solve, as do m_found[i] and loops[i]; statuses[i] receives the
+ * instance's feast_status.  Host or device pointers as in feast_solve.
+ * Worker threads, each with its own stream and workspace, take the instances
+ * largest first; `workers` bounds their number (0 = as many as the device
+ * memory allows, at most 8).  Returns FEAST_OK when every instance
+ * succeeded, else the status of the first failing instance.  Synchronises.
+ */
+feast_status feast_solve_batched(feast_handle* h, int count, const feast_operator* ops, const double* lmin,
+                                 const double* lmax, const int* M0, int Ne, double tol, const double* const* Y0,
+                                 double* const* lambda, double* const* X, double* const* resid, int* m_found,
+                                 int* loops, feast_status* statuses, int workers);
+
 /* ---------------------------------------------------------------------------
  * Step-level entry points (DEVICE pointers only; ordered on the handle's
  * stream; they do not synchronise unless stated).

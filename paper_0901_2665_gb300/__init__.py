@@ -46,6 +46,7 @@ EXPORTED = [
     "feast_default_options", "feast_init", "feast_destroy", "feast_last_error", "feast_get_info",
     "feast_solve", "feast_contour", "feast_stencil_apply", "feast_node_solve", "feast_quadrature",
     "feast_reduced_eig", "feast_rayleigh_ritz", "feast_residuals", "feast_reduced_eig_noalloc",
+    "feast_solve_batched",
 ]
 
 
@@ -93,6 +94,8 @@ _lib.feast_reduced_eig.argtypes = [_vp, _vp, _vp, _i, _vp, _vp]
 _lib.feast_rayleigh_ritz.argtypes = [_vp, ctypes.POINTER(feast_operator), _vp, _i, _vp, _vp, _vp, _vp]
 _lib.feast_residuals.argtypes = [_vp, ctypes.POINTER(feast_operator), _vp, _vp, _i, _vp, _vp]
 _lib.feast_reduced_eig_noalloc.argtypes = [_vp, _vp, _i, _vp, _vp, _vp]
+_lib.feast_solve_batched.argtypes = [_vp, _i, ctypes.POINTER(feast_operator), _vp, _vp, _vp, _i, _d, _vp, _vp, _vp,
+                                     _vp, _vp, _vp, _vp, _i]
 for _f in EXPORTED:
     if _f not in ("feast_default_options", "feast_last_error"):
         getattr(_lib, _f).restype = ctypes.c_int
@@ -201,6 +204,28 @@ class Handle:
                               _ptr(Y0), _ptr(lam), _ptr(X), _ptr(resid), ctypes.byref(m), ctypes.byref(loops))
         self._check(st, "feast_solve", allow)
         return SolveResult(st, m.value, loops.value, self.info())
+
+    def feast_solve_batched(self, ops, lmin, lmax, M0, Ne, tol, Y0, lam, X, resid=None, workers=0, raise_on_error=True):
+        """ops: list of feast_operator; lmin/lmax/M0: per-instance sequences;
+        Y0, lam, X, resid: per-instance buffers (Y0 / resid may be None).
+        Returns (status, m_found, loops, statuses) as numpy arrays."""
+        cnt = len(ops)
+        op_arr = (feast_operator * cnt)(*ops)
+        lo = np.ascontiguousarray(lmin, dtype=np.float64)
+        hi = np.ascontiguousarray(lmax, dtype=np.float64)
+        m0 = np.ascontiguousarray(M0, dtype=np.int32)
+        P = ctypes.c_void_p * cnt
+        y_arr = P(*[_ptr(y) for y in Y0]) if Y0 is not None else None
+        r_arr = P(*[_ptr(r) for r in resid]) if resid is not None else None
+        mf = np.zeros(cnt, dtype=np.int32)
+        lp = np.zeros(cnt, dtype=np.int32)
+        sts = np.zeros(cnt, dtype=np.int32)
+        st = _lib.feast_solve_batched(self._h, cnt, op_arr, lo.ctypes.data, hi.ctypes.data, m0.ctypes.data, int(Ne),
+                                      float(tol), y_arr, P(*[_ptr(x) for x in lam]), P(*[_ptr(x) for x in X]), r_arr,
+                                      mf.ctypes.data, lp.ctypes.data, sts.ctypes.data, int(workers))
+        if raise_on_error:
+            self._check(st, "feast_solve_batched")
+        return st, mf, lp, sts
 
     def feast_stencil_apply(self, nx, ny, nz, C27, X, Y, k):
         self._check(_lib.feast_stencil_apply(self._h, nx, ny, nz, _ptr(C27), _ptr(X), _ptr(Y), int(k)),

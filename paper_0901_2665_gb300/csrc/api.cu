@@ -3,12 +3,14 @@
 // kernels; the host computes only the quadrature nodes, the in-interval count
 // and the trace test on M0 scalars per loop.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -483,8 +485,12 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
   feast_status st = guarded(h, [&] {
     auto t_wall0 = std::chrono::steady_clock::now();
     h->info = feast_info{};
-    prof::set_enabled(h->opt.profile != 0);
-    prof::collect(nullptr, nullptr, nullptr);   // drop records of earlier calls
+    if (h->opt.profile) {
+      prof::set_enabled(true);
+      prof::collect(nullptr, nullptr, nullptr);   // drop records of earlier calls
+    } else {
+      prof::set_enabled(false);
+    }
     const long long launches0 = prof::launches();
     if (!(lmin < lmax) || !std::isfinite(lmin) || !std::isfinite(lmax)) fail(FEAST_ERR_ARG, "need lmin < lmax");
     if (Ne < 1 || Ne > 64) fail(FEAST_ERR_ARG, "Ne must be in [1, 64]");
@@ -614,7 +620,7 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
       h->info.resid_paper_max = std::max(h->info.resid_paper_max, rp[j]);
     }
     h->info.gpu_launches = prof::launches() - launches0;
-    prof::collect(h->info.kernel_ms, h->info.kernel_launches, h->info.kernel_flops);
+    if (h->opt.profile) prof::collect(h->info.kernel_ms, h->info.kernel_launches, h->info.kernel_flops);
     h->info.t_total_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_wall0).count();
     if (count >= M0) final_status = FEAST_ERR_M0_TOO_SMALL;
@@ -626,6 +632,84 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
   else if (final_status == FEAST_ERR_NO_CONVERGENCE)
     h->err = "trace test not met within max_loops";
   return final_status;
+}
+
+// Device bytes one instance needs (mixed or FP64 path), for the worker count.
+static double instance_bytes(const feast_operator& op, int M0, int Ne, int precision) {
+  const double N = (double)op.nx * op.ny * op.nz, n = (double)op.nx * op.ny;
+  const double ldF = std::ceil(2.0 * n / 32.0) * 32.0;
+  const double blk = 8.0 * N * M0;
+  double b = 16.0 * N * M0 * Ne + 12.0 * blk + 2.0 * 27.0 * N * 8.0;
+  if (precision == FEAST_PREC_MIXED)
+    b += 4.0 * Ne * op.nz * n * ldF + 8.0 * Ne * 27.0 * N + 2.0 * 8.0 * N * M0 * Ne + 4.0 * Ne * 3.0 * n * ldF;
+  else
+    b += 16.0 * Ne * op.nz * n * n + 16.0 * Ne * n * n;
+  return b * 1.05 + 64.0 * 1024 * 1024;
+}
+
+feast_status feast_solve_batched(feast_handle* h, int count, const feast_operator* ops, const double* lmin,
+                                 const double* lmax, const int* M0, int Ne, double tol, const double* const* Y0,
+                                 double* const* lambda, double* const* X, double* const* resid, int* m_found,
+                                 int* loops, feast_status* statuses, int workers) {
+  if (!h) return FEAST_ERR_ARG;
+  if (count < 0 || (count > 0 && (!ops || !lmin || !lmax || !M0 || !lambda || !X || !m_found || !loops || !statuses)))
+    return FEAST_ERR_ARG;
+  if (count == 0) return FEAST_OK;
+  // largest instances first
+  std::vector<int> order(count);
+  std::vector<double> bytes(count);
+  for (int i = 0; i < count; ++i) {
+    order[i] = i;
+    bytes[i] = instance_bytes(ops[i], M0[i], Ne, h->opt.precision);
+  }
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return bytes[a] > bytes[b]; });
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    h->err = "cudaMemGetInfo failed";
+    return FEAST_ERR_CUDA;
+  }
+  int K = workers > 0 ? workers : (int)std::floor(0.85 * (double)free_b / bytes[order[0]]);
+  K = std::max(1, std::min({K, 8, count}));
+  feast_options opt = h->opt;
+  opt.profile = 0;
+  const int device = h->device;
+  std::atomic<int> next{0};
+  std::vector<std::thread> pool;
+  std::vector<std::string> errs(count);
+  for (int wkr = 0; wkr < K; ++wkr) {
+    pool.emplace_back([&, wkr] {
+      cudaSetDevice(device);
+      cudaStream_t st = nullptr;
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        for (int j; (j = next.fetch_add(1)) < count;) statuses[order[j]] = FEAST_ERR_CUDA;
+        return;
+      }
+      feast_handle* sub = nullptr;
+      if (feast_init(&sub, &opt, st) != FEAST_OK) {
+        for (int j; (j = next.fetch_add(1)) < count;) statuses[order[j]] = FEAST_ERR_CUDA;
+        cudaStreamDestroy(st);
+        return;
+      }
+      for (int j; (j = next.fetch_add(1)) < count;) {
+        const int i = order[j];
+        statuses[i] = feast_solve(sub, &ops[i], lmin[i], lmax[i], M0[i], Ne, tol, Y0 ? Y0[i] : nullptr, lambda[i],
+                                  X[i], resid ? resid[i] : nullptr, &m_found[i], &loops[i]);
+        if (statuses[i] != FEAST_OK) errs[i] = sub->err;
+      }
+      feast_destroy(sub);
+      cudaStreamDestroy(st);
+    });
+  }
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < count; ++i)
+    if (statuses[i] != FEAST_OK) {
+      h->err = "instance " + std::to_string(i) + ": " + errs[i];
+      return statuses[i];
+    }
+  h->err.clear();
+  return FEAST_OK;
 }
 
 }  // extern "C"

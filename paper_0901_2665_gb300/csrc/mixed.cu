@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "mixed.cuh"
@@ -129,7 +130,6 @@ __global__ void __launch_bounds__(256) k_mx_schur2(Dims d, int layer, const f2* 
 }
 
 // ------------------------------------------------------------------ panel
-constexpr int kPinvThreads = 512;
 
 // 1/a for complex fp32 with scaling (reciprocal instructions only).
 __device__ __forceinline__ f2 f2inv_fast(f2 a) {
@@ -140,82 +140,138 @@ __device__ __forceinline__ f2 f2inv_fast(f2 a) {
 }
 
 // Pinv = S[K,K]^{-1} for panel K = [k0, k0+bw) of every node (one CTA per
-// node): unpivoted sweep of the 64 x 64 diagonal block in fp32, padded with
-// the identity when bw < 64.  The block stays in registers (thread t owns
-// rows 2(t/16)..+1, columns 4(t%16)..+3); the owners of pivot row and column
-// kk publish them to a double-buffered shared copy, one barrier per pivot.
+// node, 256 threads): block sweep of the 64 x 64 diagonal block (fp32,
+// padded with the identity when bw < 64) in four 16-wide sub-panels.  For
+// each sub-panel J, one warp sweeps the 16 x 16 block P[J,J] in registers
+// (shuffles, no block barrier) giving D = P[J,J]^{-1}; then the CTA forms
+// T = P[:,J] D and applies the block sweep to the 64 x 64 block:
+//   i, j outside J: P[i,j] -= T[i,:] P[J,j];  i outside, j in J: P[i,j] = T[i,j];
+//   i in J, j outside: P[i,j] = T[j,i] (symmetry);  both in J: P[i,j] = -D.
+// After the four sub-panels P = -S[K,K]^{-1}.
+constexpr int kPinvThreads = 256;
+constexpr int kSub = 16;
+
 __global__ void __launch_bounds__(kPinvThreads) k_mx_pinv(Dims d, int layer, int k0, int bw,
                                                           const float* __restrict__ F, f2* __restrict__ PinvOut,
                                                           int* status) {
-  __shared__ f2 colbuf[2][kPanel];
-  __shared__ f2 rowbuf[2][kPanel];
+  __shared__ f2 P[kPanel][kPanel + 1];
+  __shared__ f2 Dn[kSub][kSub + 1];
+  __shared__ f2 T[kPanel][kSub + 1];
   __shared__ int bad;
   const int e = blockIdx.x;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
   const int n = d.n;
   const float* Fl = F + ((long long)e * 2 + (layer & 1)) * n * d.ldF;
   if (tid == 0) bad = 0;
-  const int rb = tid / 16, cb = tid % 16;
-  const int i0 = 2 * rb, j0 = 4 * cb;
-  f2 v[2][4];
+  for (int t = tid; t < kPanel * kPanel; t += kPinvThreads) {
+    const int i = t / kPanel, j = t % kPanel;
+    f2 x{(i == j) ? 1.f : 0.f, 0.f};
+    if (i < bw && j < bw) {
+      const float* row = Fl + (long long)(k0 + i) * d.ldF;
+      x = f2{row[k0 + j], row[n + k0 + j]};
+    }
+    P[i][j] = x;
+  }
+  __syncthreads();
+  for (int sb = 0; sb < kPanel / kSub; ++sb) {
+    const int J0 = sb * kSub;
+    // ---- A: warp 0 sweeps P[J,J]; lane l holds row l/2, columns 8(l%2)..+7
+    if (warp == 0) {
+      const int r = lane >> 1, c0 = (lane & 1) * 8;
+      f2 v[8];
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+      for (int t = 0; t < 8; ++t) v[t] = P[J0 + r][J0 + c0 + t];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int i = i0 + a, j = j0 + b;
-      f2 x{(i == j) ? 1.f : 0.f, 0.f};
-      if (i < bw && j < bw) {
-        const float* row = Fl + (long long)(k0 + i) * d.ldF;
-        x = f2{row[k0 + j], row[n + k0 + j]};
+      for (int k = 0; k < kSub; ++k) {
+        // pivot row k (my 8 columns), pivot column k (my row), pivot value
+        f2 rowk[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          rowk[t].x = __shfl_sync(0xffffffffu, v[t].x, 2 * k + (lane & 1));
+          rowk[t].y = __shfl_sync(0xffffffffu, v[t].y, 2 * k + (lane & 1));
+        }
+        f2 colk, piv;
+        colk.x = __shfl_sync(0xffffffffu, v[k % 8].x, 2 * r + k / 8);
+        colk.y = __shfl_sync(0xffffffffu, v[k % 8].y, 2 * r + k / 8);
+        piv.x = __shfl_sync(0xffffffffu, v[k % 8].x, 2 * k + k / 8);
+        piv.y = __shfl_sync(0xffffffffu, v[k % 8].y, 2 * k + k / 8);
+        const float mag = fabsf(piv.x) + fabsf(piv.y);
+        const bool good = mag > 0.f && isfinite(mag);
+        if (lane == 0 && !good) bad = 1;
+        const f2 inv = good ? f2inv_fast(piv) : f2{0.f, 0.f};
+        const f2 fac = f2mul(colk, inv);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int j = c0 + t;
+          const f2 u = f2mul(fac, rowk[t]);
+          const f2 upd{v[t].x - u.x, v[t].y - u.y};
+          const f2 rowv = f2mul(rowk[t], inv);
+          v[t] = (r != k) ? ((j != k) ? upd : fac) : ((j != k) ? rowv : f2{-inv.x, -inv.y});
+        }
       }
-      v[a][b] = x;
-    }
-  for (int kk = 0; kk < kPanel; ++kk) {
-    f2* cbuf = colbuf[kk & 1];
-    f2* rbuf = rowbuf[kk & 1];
-    // publish pivot column / row (static register indices: no local memory)
-    if (cb == kk / 4) {
 #pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-          if (b == kk % 4) cbuf[i0 + a] = v[a][b];
-    }
-    if (rb == kk / 2) {
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-          if (a == kk % 2) rbuf[j0 + b] = v[a][b];
+      for (int t = 0; t < 8; ++t) Dn[r][c0 + t] = f2{-v[t].x, -v[t].y};   // D = P[J,J]^{-1}
     }
     __syncthreads();
-    const f2 piv = rbuf[kk];
-    const float mag = fabsf(piv.x) + fabsf(piv.y);
-    const bool good = mag > 0.f && isfinite(mag);
-    if (tid == 0 && !good) bad = 1;
-    const f2 inv = good ? f2inv_fast(piv) : f2{0.f, 0.f};
-    f2 fac[2], rw[4];
+    // ---- B: T = P[:, J] D (64 x 16), thread -> row tid/4, columns 4(tid%4)..+3
+    {
+      const int i = tid / 4, q0 = (tid % 4) * 4;
+      f2 acc[4] = {f2{0.f, 0.f}, f2{0.f, 0.f}, f2{0.f, 0.f}, f2{0.f, 0.f}};
 #pragma unroll
-    for (int a = 0; a < 2; ++a) fac[a] = f2mul(cbuf[i0 + a], inv);
+      for (int m = 0; m < kSub; ++m) {
+        const f2 pim = P[i][J0 + m];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) rw[b] = rbuf[j0 + b];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int i = i0 + a, j = j0 + b;
-        const f2 u = f2mul(fac[a], rw[b]);
-        const f2 upd{v[a][b].x - u.x, v[a][b].y - u.y};
-        const f2 rowv = f2mul(rw[b], inv);
-        v[a][b] = (i != kk) ? ((j != kk) ? upd : fac[a]) : ((j != kk) ? rowv : f2{-inv.x, -inv.y});
+        for (int q = 0; q < 4; ++q) f2fma(acc[q], pim, Dn[m][q0 + q]);
       }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) T[i][q0 + q] = acc[q];
+    }
+    __syncthreads();
+    // ---- C: the block sweep of the 64 x 64 block; thread -> column j = tid % 64
+    // and rows 16 (tid / 64) .. +15, so a warp reads 32 consecutive entries of
+    // a row (no bank conflicts) and broadcasts T[i, m]
+    {
+      const int j = tid % kPanel, i0 = (tid / kPanel) * 16;
+      const bool inJ = j >= J0 && j < J0 + kSub;
+      f2 out[16];
+#pragma unroll
+      for (int a = 0; a < 16; ++a) out[a] = P[i0 + a][j];
+      if (!inJ) {
+#pragma unroll 4
+        for (int m = 0; m < kSub; ++m) {
+          const f2 pj = P[J0 + m][j];
+#pragma unroll
+          for (int a = 0; a < 16; ++a) {
+            const f2 u = f2mul(T[i0 + a][m], pj);
+            out[a].x -= u.x;
+            out[a].y -= u.y;
+          }
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 16; ++a) {
+        const int i = i0 + a;
+        const bool inI = i >= J0 && i < J0 + kSub;
+        if (!inI && inJ) {
+          out[a] = T[i][j - J0];
+        } else if (inI && !inJ) {
+          out[a] = T[j][i - J0];
+        } else if (inI && inJ) {
+          const f2 dv = Dn[i - J0][j - J0];
+          out[a] = f2{-dv.x, -dv.y};
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int a = 0; a < 16; ++a) P[i0 + a][j] = out[a];
+    }
+    __syncthreads();
   }
-  // v holds -P^{-1}
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-      PinvOut[(long long)e * kPanel * kPanel + (i0 + a) * kPanel + j0 + b] = f2{-v[a][b].x, -v[a][b].y};
+  // P holds -S[K,K]^{-1}
+  for (int t = tid; t < kPanel * kPanel; t += kPinvThreads) {
+    const f2 v = P[t / kPanel][t % kPanel];
+    PinvOut[(long long)e * kPanel * kPanel + t] = f2{-v.x, -v.y};
+  }
   if (tid == 0 && bad) atomicExch(status, (int)DEV_PIVOT);
 }
 
@@ -246,33 +302,35 @@ __global__ void __launch_bounds__(256) k_mx_panel_T(Dims d, int layer, int k0, i
     Ls[r][m] = x;
   }
   __syncthreads();
-  const int r = tid / 8, c0 = (tid % 8) * 8;
-  const int i = r0 + r;
+  // thread -> column c, rows r0 + rq + 4q (q < 8): the Pinv loads of a warp are
+  // 32 consecutive entries, the L loads a broadcast
+  const int c = tid % kPanel, rq = tid / kPanel;
   f2 acc[8];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) acc[c] = f2{0.f, 0.f};
+  for (int q = 0; q < 8; ++q) acc[q] = f2{0.f, 0.f};
 #pragma unroll 4
   for (int m = 0; m < kPanel; ++m) {
-    const f2 l = Ls[r][m];
+    const f2 pv = Ps[m][c];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) f2fma(acc[c], l, Ps[m][c0 + c]);
+    for (int q = 0; q < 8; ++q) f2fma(acc[q], Ls[rq + 4 * q][m], pv);
   }
-  if (i >= n) return;
-  float* arow = Aop + ((long long)e * n + i) * (2 * kPanel);
-  f2* trow = Tc + ((long long)e * n + i) * kPanel;
-  const long long brow = ((long long)e * d.nblk64 + i / 64) * 128 + (i % 64);
-  float* bre = Bop + brow * (2 * kPanel);
-  float* bim = Bop + (brow + 64) * (2 * kPanel);
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    arow[c0 + c] = tc::to_tf32(acc[c].x);
-    arow[kPanel + c0 + c] = tc::to_tf32(acc[c].y);
-    trow[c0 + c] = acc[c];
-    const f2 l = Ls[r][c0 + c];
-    bre[c0 + c] = tc::to_tf32(l.x);
-    bre[kPanel + c0 + c] = tc::to_tf32(-l.y);
-    bim[c0 + c] = tc::to_tf32(l.y);
-    bim[kPanel + c0 + c] = tc::to_tf32(l.x);
+  for (int q = 0; q < 8; ++q) {
+    const int r = rq + 4 * q;
+    const int i = r0 + r;
+    if (i >= n) continue;
+    float* arow = Aop + ((long long)e * n + i) * (2 * kPanel);
+    arow[c] = tc::to_tf32(acc[q].x);
+    arow[kPanel + c] = tc::to_tf32(acc[q].y);
+    Tc[((long long)e * n + i) * kPanel + c] = acc[q];
+    const long long brow = ((long long)e * d.nblk64 + i / 64) * 128 + (i % 64);
+    float* bre = Bop + brow * (2 * kPanel);
+    float* bim = Bop + (brow + 64) * (2 * kPanel);
+    const f2 l = Ls[r][c];
+    bre[c] = tc::to_tf32(l.x);
+    bre[kPanel + c] = tc::to_tf32(-l.y);
+    bim[c] = tc::to_tf32(l.y);
+    bim[kPanel + c] = tc::to_tf32(l.x);
   }
 }
 
@@ -575,14 +633,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 EncodeTiledFn encode_fn() {
   static EncodeTiledFn fn = nullptr;
-  if (!fn) {
+  static std::once_flag once;
+  std::call_once(once, [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
+  });
   return fn;
 }
 
@@ -605,13 +664,13 @@ template <int BN, int STAGES, class Epi>
 cudaError_t launch_tc(cudaStream_t s, dim3 grid, const CUtensorMap& a, const CUtensorMap& b, tc::Geom geo,
                       const Epi& epi, int* status) {
   constexpr size_t smem = tc::Smem<BN, STAGES>::kBytes;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e =
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err =
         cudaFuncSetAttribute(tc::k_tc_gemm<BN, STAGES, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  });
+  if (attr_err != cudaSuccess) return attr_err;
   tc::k_tc_gemm<BN, STAGES, Epi><<<grid, tc::kThreads, smem, s>>>(a, b, geo, epi, status);
   return cudaGetLastError();
 }
@@ -640,7 +699,7 @@ T* buf(MixedWork& w, int idx) {
   return static_cast<T*>(w.bufs[idx]);
 }
 
-Dims make_dims(Grid g, int Ne, int k) {
+Dims make_dims(Grid g, int Ne, int k, int cb = 0) {
   Dims d;
   d.nx = g.nx;
   d.ny = g.ny;
@@ -651,7 +710,7 @@ Dims make_dims(Grid g, int Ne, int k) {
   d.ldF = ((2 * d.n + 31) / 32) * 32;
   d.nblk64 = (d.n + 63) / 64;
   d.k = k;
-  d.CB = k <= 8 ? 8 : (k <= 16 ? 16 : (k <= 32 ? 32 : 64));
+  d.CB = cb > 0 ? cb : (k <= 8 ? 8 : (k <= 16 ? 16 : (k <= 32 ? 32 : 64)));
   d.nblkCB = (k + d.CB - 1) / d.CB;
   d.ldB = d.ldF;
   return d;
@@ -666,6 +725,11 @@ void MixedWork::release() {
     sizes[i] = 0;
   }
   nz_factored = 0;
+  if (side) cudaStreamDestroy(side);
+  if (ev_narrow) cudaEventDestroy(ev_narrow);
+  if (ev_side) cudaEventDestroy(ev_side);
+  side = nullptr;
+  ev_narrow = ev_side = nullptr;
 }
 
 const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
@@ -676,25 +740,73 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
   if (!ensure(w, B_F, fbytes, s)) return "out of device memory (mixed factors)";
   if (!ensure(w, B_FW, sizeof(float) * (size_t)Ne * 2 * d.n * d.ldF, s)) return "out of device memory (working layers)";
   if (!ensure(w, B_T1, sizeof(float) * (size_t)Ne * d.n * d.ldF, s)) return "out of device memory (schur scratch)";
-  if (!ensure(w, B_AOP, sizeof(float) * (size_t)Ne * d.n * 2 * kPanel, s, true)) return "out of device memory";
-  if (!ensure(w, B_BOP, sizeof(float) * (size_t)Ne * d.nblk64 * 128 * 2 * kPanel, s, true)) return "out of device memory";
-  if (!ensure(w, B_TC, sizeof(f2) * (size_t)Ne * d.n * kPanel, s)) return "out of device memory";
-  if (!ensure(w, B_PINV, sizeof(f2) * (size_t)Ne * kPanel * kPanel, s)) return "out of device memory";
+  // panel operands are double-buffered by panel parity (lookahead)
+  const size_t aop_sz = (size_t)Ne * d.n * 2 * kPanel;
+  const size_t bop_sz = (size_t)Ne * d.nblk64 * 128 * 2 * kPanel;
+  const size_t tc_sz = (size_t)Ne * d.n * kPanel;
+  const size_t pinv_sz = (size_t)Ne * kPanel * kPanel;
+  if (!ensure(w, B_AOP, sizeof(float) * 2 * aop_sz, s, true)) return "out of device memory";
+  if (!ensure(w, B_BOP, sizeof(float) * 2 * bop_sz, s, true)) return "out of device memory";
+  if (!ensure(w, B_TC, sizeof(f2) * 2 * tc_sz, s)) return "out of device memory";
+  if (!ensure(w, B_PINV, sizeof(f2) * 2 * pinv_sz, s)) return "out of device memory";
   if (!ensure(w, B_CF, sizeof(f2) * (size_t)Ne * 27 * d.N, s)) return "out of device memory (coefficients)";
+  if (!w.side) {
+    // highest priority: the lookahead chain is the critical path, its few
+    // CTAs must not queue behind the wide update's
+    int lo_prio = 0, hi_prio = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    if (cudaStreamCreateWithPriority(&w.side, cudaStreamNonBlocking, hi_prio) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w.ev_narrow, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w.ev_side, cudaEventDisableTiming) != cudaSuccess)
+      return "could not create the lookahead stream";
+  }
+  cudaStream_t s2 = w.side;
   // The row-split padding [2n, ldF) is never read (the tensor maps stop at 2n).
   float* Fr = buf<float>(w, B_F);    // TF32-rounded S'_i of every layer (solve operand)
   float* F = buf<float>(w, B_FW);    // fp32 working layers (ping-pong)
-  float* Aop = buf<float>(w, B_AOP);
-  float* Bop = buf<float>(w, B_BOP);
   f2* Cf = buf<f2>(w, B_CF);
   k_mx_coef<<<dim3((unsigned)std::min<long long>(4096, (27 * d.N + 255) / 256), Ne), 256, 0, s>>>(d, Z, A27, B27, Cf);
   prof::count_launch();
-  CUtensorMap tmA, tmB;
-  if (!make_map(&tmA, Aop, 2 * kPanel, (long long)Ne * d.n, 2 * kPanel, 128)) return "tensor map (Aop) rejected";
-  if (!make_map(&tmB, Bop, 2 * kPanel, (long long)Ne * d.nblk64 * 128, 2 * kPanel, 128))
-    return "tensor map (Bop) rejected";
+  float* Aop[2] = {buf<float>(w, B_AOP), buf<float>(w, B_AOP) + aop_sz};
+  float* Bop[2] = {buf<float>(w, B_BOP), buf<float>(w, B_BOP) + bop_sz};
+  f2* Tc[2] = {buf<f2>(w, B_TC), buf<f2>(w, B_TC) + tc_sz};
+  f2* Pv[2] = {buf<f2>(w, B_PINV), buf<f2>(w, B_PINV) + pinv_sz};
+  CUtensorMap tmA[2], tmB[2];
+  for (int q = 0; q < 2; ++q) {
+    if (!make_map(&tmA[q], Aop[q], 2 * kPanel, (long long)Ne * d.n, 2 * kPanel, 128)) return "tensor map (Aop) rejected";
+    if (!make_map(&tmB[q], Bop[q], 2 * kPanel, (long long)Ne * d.nblk64 * 128, 2 * kPanel, 128))
+      return "tensor map (Bop) rejected";
+  }
   const long long sF = 2LL * d.n * d.ldF;
   const long long sFr = (long long)d.nz * d.n * d.ldF;
+  const int npan = d.nblk64;
+  auto panel = [&](cudaStream_t st, int layer, int kp) {
+    const int k0 = kp * kPanel, bw = std::min(kPanel, d.n - k0), q = kp & 1;
+    prof::begin(st, prof::PINV);
+    prof::add_work(prof::PINV, 8.0 * kPanel * kPanel * kPanel * Ne);
+    k_mx_pinv<<<Ne, kPinvThreads, 0, st>>>(d, layer, k0, bw, F, Pv[q], status);
+    prof::end(st, prof::PINV);
+    prof::begin(st, prof::PANEL_T);
+    prof::add_work(prof::PANEL_T, 8.0 * d.n * kPanel * kPanel * Ne);
+    k_mx_panel_T<<<dim3(cdiv(d.n, kRowsPerPanelCta), Ne), 256, 0, st>>>(d, layer, k0, bw, F, Pv[q], Aop[q], Bop[q],
+                                                                      Tc[q]);
+    prof::end(st, prof::PANEL_T);
+    prof::count_launch(2);
+  };
+  // trailing update of panel kp over the column tiles [base, base + count) except `skip`
+  auto update = [&](int layer, int kp, int base, int count, int skip) -> cudaError_t {
+    const int k0 = kp * kPanel, bw = std::min(kPanel, d.n - k0), q = kp & 1;
+    const bool last = kp == npan - 1;
+    SweepEpi epi{F + (long long)(layer & 1) * d.n * d.ldF, sF, last ? Fr + (long long)layer * d.n * d.ldF : nullptr,
+                 sFr, d.ldF, d.n, k0, bw, Tc[q], Pv[q]};
+    tc::Geom geo{0, d.n, 0, d.nblk64 * 128, (2 * kPanel) / tc::kBlockK, base, skip};
+    prof::begin(s, prof::SWEEP_GEMM);
+    prof::add_work(prof::SWEEP_GEMM, 8.0 * d.n * (64.0 * count) * bw * Ne);
+    cudaError_t err = launch_tc<128, 2>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status);
+    prof::end(s, prof::SWEEP_GEMM);
+    prof::count_launch();
+    return err;
+  };
   for (int layer = 0; layer < d.nz; ++layer) {
     prof::begin(s, prof::SCHUR);
     prof::add_work(prof::SCHUR, (layer > 0 ? 144.0 : 0.0) * d.n * (double)d.n * Ne);
@@ -703,27 +815,22 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
     k_mx_schur2<<<dim3(cdiv(d.n, 256), d.n, Ne), 256, 0, s>>>(d, layer, Cf, buf<float>(w, B_T1), F);
     prof::end(s, prof::SCHUR);
     prof::count_launch(layer > 0 ? 2 : 1);
-    for (int k0 = 0; k0 < d.n; k0 += kPanel) {
-      const int bw = d.n - k0 < kPanel ? d.n - k0 : kPanel;
-      prof::begin(s, prof::PINV);
-      prof::add_work(prof::PINV, 8.0 * kPanel * kPanel * kPanel * Ne);
-      k_mx_pinv<<<Ne, kPinvThreads, 0, s>>>(d, layer, k0, bw, F, buf<f2>(w, B_PINV), status);
-      prof::end(s, prof::PINV);
-      prof::begin(s, prof::PANEL_T);
-      prof::add_work(prof::PANEL_T, 8.0 * d.n * kPanel * kPanel * Ne);
-      k_mx_panel_T<<<dim3(cdiv(d.n, kRowsPerPanelCta), Ne), 256, 0, s>>>(d, layer, k0, bw, F, buf<f2>(w, B_PINV), Aop,
-                                                                       Bop, buf<f2>(w, B_TC));
-      prof::end(s, prof::PANEL_T);
-      prof::count_launch(3);
-      const bool last = k0 + kPanel >= d.n;
-      SweepEpi epi{F + (long long)(layer & 1) * d.n * d.ldF, sF, last ? Fr + (long long)layer * d.n * d.ldF : nullptr,
-                   sFr, d.ldF, d.n, k0, bw, buf<f2>(w, B_TC), buf<f2>(w, B_PINV)};
-      tc::Geom geo{0, d.n, 0, d.nblk64 * 128, (2 * kPanel) / tc::kBlockK};
-      prof::begin(s, prof::SWEEP_GEMM);
-      prof::add_work(prof::SWEEP_GEMM, 8.0 * d.n * (double)d.n * bw * Ne);
-      cudaError_t err = launch_tc<128, 2>(s, dim3(d.nblk64, cdiv(d.n, 128), Ne), tmA, tmB, geo, epi, status);
-      prof::end(s, prof::SWEEP_GEMM);
-      if (err != cudaSuccess) return "tcgen05 sweep-update launch failed";
+    panel(s, layer, 0);
+    for (int kp = 0; kp < npan; ++kp) {
+      if (kp + 1 < npan) {
+        // narrow update: the next panel's columns first ...
+        if (update(layer, kp, kp + 1, 1, -1) != cudaSuccess) return "tcgen05 sweep-update launch failed";
+        cudaEventRecord(w.ev_narrow, s);
+        // ... so its inversion and product overlap the wide update
+        cudaStreamWaitEvent(s2, w.ev_narrow, 0);
+        panel(s2, layer, kp + 1);
+        cudaEventRecord(w.ev_side, s2);
+        if (npan > 1 && update(layer, kp, 0, npan - 1, kp + 1) != cudaSuccess)
+          return "tcgen05 sweep-update launch failed";
+        cudaStreamWaitEvent(s, w.ev_side, 0);
+      } else {
+        if (update(layer, kp, 0, npan, -1) != cudaSuccess) return "tcgen05 sweep-update launch failed";
+      }
     }
   }
   w.nz_factored = d.nz;
@@ -773,6 +880,68 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
   return nullptr;
 }
 
+// ---- autotuner of the solve-GEMM tile width (complex columns per CTA tile)
+template <int CB>
+float time_solve_gemm(cudaStream_t s, const Dims& d0, MixedWork& w, int* status) {
+  Dims d = d0;
+  d.CB = CB;
+  d.nblkCB = (d.k + CB - 1) / CB;
+  CUtensorMap tmF, tmB;
+  if (!make_map(&tmF, buf<float>(w, B_F), 2 * d.n, (long long)d.Ne * d.nz * d.n, d.ldF, 128)) return 1e30f;
+  if (!make_map(&tmB, buf<float>(w, B_BEMB), 2 * d.n, (long long)d.Ne * d.nblkCB * 2 * CB, d.ldB, 2 * CB)) return 1e30f;
+  const int nk = (2 * d.n + tc::kBlockK - 1) / tc::kBlockK;
+  SolveEpi<CB> epi{buf<f2>(w, B_TOUT), (long long)d.n * d.k, d.n, d.n, d.k, 1.0f};
+  tc::Geom geo{0, d.nz * d.n, 0, d.nblkCB * 2 * CB, nk};
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(a, s);
+    launch_tc<2 * CB, 4>(s, dim3(d.nblkCB, cdiv(d.n, 128), d.Ne), tmF, tmB, geo, epi, status);
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (rep > 0) best = std::min(best, ms);   // first launch warms up
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  prof::count_launch(4);
+  return best;
+}
+
+std::mutex g_tune_mutex;
+std::vector<std::pair<long long, int>> g_tuned;   // (n, k, Ne) key -> CB
+
+int tuned_cb(cudaStream_t s, const Dims& d, MixedWork& w, int* status) {
+  const long long key = ((long long)d.n << 32) ^ ((long long)d.k << 8) ^ d.Ne;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    for (auto& kv : g_tuned)
+      if (kv.first == key) return kv.second;
+  }
+  int best_cb = d.CB;
+  float best = 1e30f;
+  auto consider = [&](int cb, float ms) {
+    if (ms < best) {
+      best = ms;
+      best_cb = cb;
+    }
+  };
+  if (d.k <= 16) {
+    consider(8, time_solve_gemm<8>(s, d, w, status));
+    consider(16, time_solve_gemm<16>(s, d, w, status));
+  } else {
+    consider(16, time_solve_gemm<16>(s, d, w, status));
+    consider(32, time_solve_gemm<32>(s, d, w, status));
+    consider(64, time_solve_gemm<64>(s, d, w, status));
+  }
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tuned.push_back({key, best_cb});
+  return best_cb;
+}
+
 const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const double* A27, const double* B27,
                        MixedWork& w, const double* Rreal, const f2* Rc, int* status) {
   switch (d.CB) {
@@ -794,18 +963,19 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
   if (!ensure(w, B_GC, sizeof(f2) * (size_t)Ne * sG, s)) return "out of device memory (node sweeps)";
   if (!ensure(w, B_RC, sizeof(f2) * (size_t)Ne * sG, s)) return "out of device memory (residuals)";
   if (!ensure(w, B_TOUT, sizeof(f2) * (size_t)Ne * d.n * k, s)) return "out of device memory";
-  const size_t bemb = sizeof(float) * (size_t)Ne * d.nblkCB * 2 * d.CB * d.ldB;
-  // rows of columns >= k and the padding stay zero; re-zero when the shape changes
-  const bool shape_changed = w.sizes[B_BEMB] != bemb || w.bemb_k != k;
+  // embedded RHS operand, sized for every tile width (rows of columns >= k
+  // stay zero; re-zeroed when the column count changes)
+  const size_t bemb = sizeof(float) * (size_t)Ne * (2 * (size_t)k + 128) * d.ldB;
+  const bool shape_changed = w.sizes[B_BEMB] < bemb || w.bemb_k != k;
   if (!ensure(w, B_BEMB, bemb, s, shape_changed)) return "out of device memory";
   w.bemb_k = k;
+  d = make_dims(g, Ne, k, tuned_cb(s, d, w, status));
+  if (shape_changed) cudaMemsetAsync(w.bufs[B_BEMB], 0, bemb, s);
   const dim3 rgrid(cdiv(d.N, kResRows), Ne);
   const long long nblk = rgrid.x;
-  static bool res_attr = false;
-  if (!res_attr) {
-    cudaFuncSetAttribute(k_mx_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResSmem);
-    res_attr = true;
-  }
+  static std::once_flag res_once;
+  std::call_once(res_once,
+                 [] { cudaFuncSetAttribute(k_mx_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResSmem); });
   if (!ensure(w, B_PART, sizeof(double) * 2 * (size_t)Ne * nblk, s)) return "out of device memory";
   if (!ensure(w, B_REL, sizeof(double) * Ne, s)) return "out of device memory";
   if (!ensure(w, B_ACTIVE, sizeof(int) * Ne, s)) return "out of device memory";

@@ -17,6 +17,8 @@ struct MixedWork {
   size_t sizes[16] = {};
   int nz_factored = 0, ne_factored = 0;   // shape of the factors held
   int bemb_k = 0;                         // right-hand sides the RHS operand was zeroed for
+  cudaStream_t side = nullptr;            // lookahead stream of the factorisation
+  cudaEvent_t ev_narrow = nullptr, ev_side = nullptr;
   void release();
 };
 

@@ -1,4 +1,5 @@
 // Kernel accounting (see prof.cuh).
+#include <atomic>
 #include <vector>
 
 #include "prof.cuh"
@@ -16,14 +17,14 @@ struct Pair {
 };
 
 struct State {
-  bool on = false;
+  std::atomic<bool> on{false};
   std::vector<Pair> ring;
   int head = 0, count = 0;   // pending pairs: ring[(head - count) mod kRing] .. ring[head - 1]
   int open = -1;             // index of the pair begun but not ended
   double ms[NCLS] = {};
   long long n[NCLS] = {};
   double work[NCLS] = {};
-  long long launches = 0;
+  std::atomic<long long> launches{0};
 };
 
 State& st() {
@@ -45,6 +46,8 @@ void fold_oldest(State& s) {
 
 }  // namespace
 
+// Timing is for one host thread (a single handle); the launch counter is
+// shared by every thread.
 void set_enabled(bool on) {
   State& s = st();
   if (on && s.ring.empty()) {

@@ -1,5 +1,7 @@
 // Rayleigh-Ritz in FP64 (Fig. 2 steps 3-5; Eqs. 6-9) and the residuals of
 // Table I.
+#include <mutex>
+
 #include "kernels.cuh"
 #include "prof.cuh"
 
@@ -400,11 +402,8 @@ void reduced_eig(cudaStream_t s, int m, const double* AQ, const double* BQ, doub
                  double* work, int* status) {
   const size_t smem = sizeof(double) * ((size_t)m * (m + 1) + 2 * (m / 2 + 2) + 2 * m) +
                       sizeof(int) * (2 * (m / 2 + 2) + 1);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_reduced_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  static std::once_flag once;
+  std::call_once(once, [] { cudaFuncSetAttribute(k_reduced_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); });
   k_reduced_eig<<<1, 1024, smem, s>>>(m, AQ, BQ, eps, Phi, work, status);
   prof::count_launch();
 }

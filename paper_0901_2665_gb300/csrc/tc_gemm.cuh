@@ -117,6 +117,22 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
       : "memory");
 }
 
+// BF16 A and B (kind::f16, K = 16 per instruction, 32 bytes like TF32's 8).
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -144,12 +160,15 @@ __device__ __forceinline__ float to_tf32(float x) {
 }
 
 // Geometry of a batched launch: grid (n tiles, m tiles, batch).  The A tile
-// of CTA (tn, tm, e) starts at row a_row0 + e*a_batch + tm*128 of A's tensor
-// map, the B tile at row b_row0 + e*b_batch + tn*BN; nk K-blocks of 32.
+// of CTA (x, tm, e) starts at row a_row0 + e*a_batch + tm*128 of A's tensor
+// map, the B tile at row b_row0 + e*b_batch + tn*BN with tn = x + tn_base,
+// moved past tn_skip; nk K-blocks of 32.
 struct Geom {
   int a_row0, a_batch;
   int b_row0, b_batch;
   int nk;
+  int tn_base = 0;    // first n tile of the launch
+  int tn_skip = -1;   // n tile left out (the grid's x covers the others), -1 = none
 };
 
 template <int BN, int STAGES>
@@ -169,7 +188,10 @@ __device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 1, 128;
 // address of that lane at column 0, ept in [0, 128) the thread's index in the
 // epilogue group and stage the pipeline shared memory (Smem::kPipeBytes),
 // free for reuse once the accumulator is complete.
-template <int BN, int STAGES, class Epi>
+// KIND 0: fp32 operands read as TF32 (kind::tf32); KIND 1: BF16 operands
+// (kind::f16).  A K-block is one 128-byte swizzle row either way: 32 fp32 or
+// 64 bf16 elements; geo.nk counts K-blocks.
+template <int BN, int STAGES, class Epi, int KIND = 0>
 __global__ void __launch_bounds__(kThreads)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Geom geo, Epi epi,
               int* status) {
@@ -186,7 +208,9 @@ __global__ void __launch_bounds__(kThreads)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int e = blockIdx.z, tm = blockIdx.y, tn = blockIdx.x;
+  const int e = blockIdx.z, tm = blockIdx.y;
+  int tn = (int)blockIdx.x + geo.tn_base;
+  if (geo.tn_skip >= 0 && tn >= geo.tn_skip) ++tn;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -213,8 +237,9 @@ __global__ void __launch_bounds__(kThreads)
         const uint32_t ph = (kb / kStages) & 1;
         if (kb >= kStages && !mbar_wait(&empty[s], ph ^ 1, status, abort_flag)) break;
         mbar_arrive_expect_tx(&full[s], S::kStageBytes);
-        tma_load_2d(sA + s * kATileBytes, &tmA, &full[s], kb * kBlockK, ay);
-        tma_load_2d(sB + s * S::kBTileBytes, &tmB, &full[s], kb * kBlockK, by);
+        constexpr int kElems = KIND == 0 ? kBlockK : 2 * kBlockK;   // elements per 128-byte row
+        tma_load_2d(sA + s * kATileBytes, &tmA, &full[s], kb * kElems, ay);
+        tma_load_2d(sB + s * S::kBTileBytes, &tmB, &full[s], kb * kElems, by);
         issued = kb + 1;
       }
       if (*abort_flag) {
@@ -227,7 +252,7 @@ __global__ void __launch_bounds__(kThreads)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32(kBlockM, BN);
+      constexpr uint32_t idesc = KIND == 0 ? idesc_tf32(kBlockM, BN) : idesc_bf16(kBlockM, BN);
       for (int kb = 0; kb < geo.nk; ++kb) {
         const int s = kb % kStages;
         const uint32_t ph = (kb / kStages) & 1;
@@ -236,8 +261,12 @@ __global__ void __launch_bounds__(kThreads)
         const uint32_t a0 = smem_u32(sA + s * kATileBytes);
         const uint32_t b0 = smem_u32(sB + s * S::kBTileBytes);
 #pragma unroll
-        for (int kk = 0; kk < kBlockK / 8; ++kk)
-          mma_tf32(tmem, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc, (kb | kk) != 0);
+        for (int kk = 0; kk < 4; ++kk) {   // four 32-byte K steps per 128-byte row
+          if constexpr (KIND == 0)
+            mma_tf32(tmem, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc, (kb | kk) != 0);
+          else
+            mma_bf16(tmem, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc, (kb | kk) != 0);
+        }
         mma_commit(&empty[s]);
       }
       // always signal: the epilogue (and the TMEM release) wait for every

@@ -268,3 +268,68 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     assert err_with(lambda x, w, th, Z, r: (x, w, th, Z, 1.0)) > 1e-3
     # rotated phase (e^{i theta} -> i e^{i theta} picks the imaginary part)
     assert err_with(lambda x, w, th, Z, r: (x, w, th + math.pi / 2, Z, r)) > 1e-3
+
+
+# ---------------------------------------------------------------- learned start (CPU reference)
+
+def test_mlp_backward_matches_finite_differences():
+    """The reference MLP's backward pass against central differences of its
+    loss (float64, no rounding)."""
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    sizes = [7, 12, 12, 12, 9]
+    params = mlp.init_params(sizes, 1)
+    params = [(W, rng.standard_normal(b.shape) * 0.1) for W, b in params]
+    x = rng.standard_normal((5, 7))
+    target = rng.standard_normal((5, 9))
+    weights = rng.uniform(0.5, 1.5, 9)
+    out, cache = mlp.forward(params, x)
+    grads = mlp.backward(params, cache, out, target, weights)
+    eps = 1e-6
+    for k in range(len(params)):
+        W, b = params[k]
+        for (i, j) in [(0, 0), (W.shape[0] - 1, W.shape[1] - 1), (W.shape[0] // 2, 1)]:
+            Wp, Wm = W.copy(), W.copy()
+            Wp[i, j] += eps
+            Wm[i, j] -= eps
+            lp = mlp.loss(mlp.forward([(Wp, b) if q == k else params[q] for q in range(len(params))], x)[0],
+                          target, weights)
+            lm = mlp.loss(mlp.forward([(Wm, b) if q == k else params[q] for q in range(len(params))], x)[0],
+                          target, weights)
+            assert abs((lp - lm) / (2 * eps) - grads[k][0][i, j]) < 1e-7
+        bp, bm = b.copy(), b.copy()
+        bp[0] += eps
+        bm[0] -= eps
+        lp = mlp.loss(mlp.forward([(W, bp) if q == k else params[q] for q in range(len(params))], x)[0], target, weights)
+        lm = mlp.loss(mlp.forward([(W, bm) if q == k else params[q] for q in range(len(params))], x)[0], target, weights)
+        assert abs((lp - lm) / (2 * eps) - grads[k][1][0]) < 1e-7
+
+
+def test_sine_basis_orthonormal_and_projection_is_adjoint():
+    """The discrete sine vectors diagonalise tridiag(-1,2,-1) (a closed form:
+    eigenvalue 2 - 2 cos(p pi/(m+1))), are orthonormal, and `project` is the
+    adjoint (and on its range the inverse) of `expand`."""
+    from oracle import mlp
+    m = 11
+    S = mlp.sine_basis(m, m)
+    assert np.abs(S.T @ S - np.eye(m)).max() < 1e-13
+    T = 2 * np.eye(m) - np.eye(m, k=1) - np.eye(m, k=-1)
+    lam = 2 - 2 * np.cos(np.arange(1, m + 1) * math.pi / (m + 1))
+    assert np.abs(T @ S - S * lam[None, :]).max() < 1e-13
+    rng = np.random.default_rng(2)
+    nx, ny, nz, c, px, py = 6, 5, 3, 4, 3, 2
+    coef = rng.standard_normal((nz, c, px * py))
+    X = rng.standard_normal((nx * ny * nz, c))
+    Y = mlp.expand(coef, nx, ny, nz, px, py)
+    assert abs(np.sum(Y * X) - np.sum(coef * mlp.project(X, nx, ny, nz, px, py))) < 1e-12
+    assert np.abs(mlp.project(Y, nx, ny, nz, px, py) - coef).max() < 1e-13
+
+
+def test_bf16_rounding_nearest_even():
+    from oracle import mlp
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -2.5, 3.0e-40], dtype=np.float32)
+    r = mlp.round_bf16(x)
+    assert r[0] == 1.0
+    assert r[1] == 1.0                                             # 1 + 2^-8 is a tie: even is 1.0
+    assert r[2] == 1.0 + 2 ** -7                                   # above the tie rounds up
+    assert r[3] == -2.5

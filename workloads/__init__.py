@@ -246,3 +246,38 @@ WORKLOADS = {
     # 24x24x100 grid, n=576; lowest 40 eigenpairs, M0=64 (learned-start family)
     "q1_24x24x100_fp64": Workload("q1_24x24x100_fp64", 24, 24, 100, 16, 40, 64),
 }
+
+
+# ----------------------------------------------------------------------------
+# Batched workload: 64 independent instances of uneven size
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class BatchInstance:
+    index: int
+    nx: int
+    ny: int
+    nz: int
+    M0: int
+    potential_seed: int
+    gaussians: int = 8
+
+    def operator(self) -> Operator:
+        pot = gaussian_potential(self.gaussians, self.potential_seed, self.nx, self.ny, self.nz)
+        return q1_operator(self.nx, self.ny, self.nz, pot)
+
+
+def batch_instances(count: int = 64, master_seed: int = 3, nz_range=(50, 400), sides=(16, 24, 32),
+                    m0_choices=(32, 64, 128)):
+    """Instance i draws its cross-section side from `sides` (block sizes
+    256/576/1024), its layer count uniformly in `nz_range` and M0 from
+    `m0_choices`, from the stream PCG64([master_seed, i]); its potential uses
+    8 Gaussians with seed 1000*master_seed + i."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(np.random.PCG64([master_seed, i]))
+        side = int(rng.choice(sides))
+        nz = int(rng.integers(nz_range[0], nz_range[1] + 1))
+        M0 = int(rng.choice(m0_choices))
+        out.append(BatchInstance(i, side, side, nz, M0, 1000 * master_seed + i))
+    return out
