@@ -240,6 +240,49 @@ feast_status feast_rayleigh_ritz(feast_handle* h, const feast_operator* op, cons
 feast_status feast_residuals(feast_handle* h, const feast_operator* op, const double* lambda,
                              const double* X, int k, double* resid, double* resid_paper);
 
+/* ---------------------------------------------------------------------------
+ * Learned initial subspace.  The paper's refinement (Sec. III.B (i)) and its
+ * warm starts over a sequence of close problems (Sec. IV.C, Fig. 3) show that
+ * a good start block Y shortens the loop; here a small network predicts Y.
+ * An MLP maps the features of one z-layer of an instance (in_dim <= 64
+ * scalars) through three hidden layers of `width` (a multiple of 128, SiLU)
+ * to out_dim = M0 * px * py coefficients: layer l's block of Y is
+ *   Y[l n + ix + nx iy, c] = sum_{q<py, p<px} coef[l, c, q px + p] s_p(ix) s_q(iy),
+ *   s_p(i) = sqrt(2/(m+1)) sin((p+1) pi (i+1)/(m+1)) on an axis of m nodes
+ * (0-based p).  Products run on the tensor cores in BF16 with FP32
+ * accumulation; parameters are FP32 and trained with Adam.  Buffers are
+ * DEVICE pointers unless stated; calls are ordered on the network's stream
+ * and synchronise it.
+ * ------------------------------------------------------------------------- */
+typedef struct feast_mlp feast_mlp;
+
+/* Allocates a network for batches of up to max_batch rows (FEAST_ERR_ARG on
+   bad sizes, FEAST_ERR_OOM).  Parameters start at zero: set them with
+   feast_mlp_set_layer. */
+feast_status feast_mlp_create(feast_mlp** net, int in_dim, int width, int out_dim, int max_batch, void* cuda_stream);
+feast_status feast_mlp_destroy(feast_mlp* net);
+/* Layer k (0..3): W (out x in, row-major, fp32) and b (out), host or device;
+   resets the optimiser state. */
+feast_status feast_mlp_set_layer(feast_mlp* net, int k, const float* W, const float* b);
+/* Copies layer k's parameters and last gradients out (any pointer may be NULL). */
+feast_status feast_mlp_get_layer(feast_mlp* net, int k, float* W, float* b, float* gW, float* gb);
+/* out (B x out_dim) = network(X (B x in_dim)), row-major fp32. */
+feast_status feast_mlp_forward(feast_mlp* net, const float* X, int B, float* out);
+/* Loss L = sum_{r,o} weights[o] (out[r,o] - target[r,o])^2 / (2 B) of B rows,
+   its gradients (kept in the network, see feast_mlp_get_layer) and, when
+   lr > 0, one Adam step (beta 0.9 / 0.999, eps 1e-8).  *loss may be NULL. */
+feast_status feast_mlp_train_step(feast_mlp* net, const float* X, const float* target, const float* weights, int B,
+                                  float lr, double* loss);
+/* Y (N x M0, column-major fp64) from coef (nz x M0 x px*py fp32), formula above. */
+feast_status feast_sine_expand(const float* coef, int nx, int ny, int nz, int M0, int px, int py, double* Y,
+                               void* cuda_stream);
+/* The adjoint: coef[l, c, q px + p] = sum_{ix, iy} X[l n + ix + nx iy, c] s_p(ix) s_q(iy). */
+feast_status feast_sine_project(const double* X, int nx, int ny, int nz, int M0, int px, int py, float* coef,
+                                void* cuda_stream);
+/* Y = expansion of the network's output for the nz layer features (nz x in_dim). */
+feast_status feast_predict_Y(feast_mlp* net, const float* features, int nx, int ny, int nz, int M0, int px, int py,
+                             double* Y);
+
 /*
  * Allocation-free reduced eigensolve.  The paper has no counterpart: this is
  * a library convenience.  It computes exactly what feast_reduced_eig computes

@@ -46,7 +46,8 @@ EXPORTED = [
     "feast_default_options", "feast_init", "feast_destroy", "feast_last_error", "feast_get_info",
     "feast_solve", "feast_contour", "feast_stencil_apply", "feast_node_solve", "feast_quadrature",
     "feast_reduced_eig", "feast_rayleigh_ritz", "feast_residuals", "feast_reduced_eig_noalloc",
-    "feast_solve_batched",
+    "feast_solve_batched", "feast_mlp_create", "feast_mlp_destroy", "feast_mlp_set_layer", "feast_mlp_get_layer",
+    "feast_mlp_forward", "feast_mlp_train_step", "feast_sine_expand", "feast_sine_project", "feast_predict_Y",
 ]
 
 
@@ -94,6 +95,15 @@ _lib.feast_reduced_eig.argtypes = [_vp, _vp, _vp, _i, _vp, _vp]
 _lib.feast_rayleigh_ritz.argtypes = [_vp, ctypes.POINTER(feast_operator), _vp, _i, _vp, _vp, _vp, _vp]
 _lib.feast_residuals.argtypes = [_vp, ctypes.POINTER(feast_operator), _vp, _vp, _i, _vp, _vp]
 _lib.feast_reduced_eig_noalloc.argtypes = [_vp, _vp, _i, _vp, _vp, _vp]
+_lib.feast_mlp_create.argtypes = [ctypes.POINTER(_vp), _i, _i, _i, _i, _vp]
+_lib.feast_mlp_destroy.argtypes = [_vp]
+_lib.feast_mlp_set_layer.argtypes = [_vp, _i, _vp, _vp]
+_lib.feast_mlp_get_layer.argtypes = [_vp, _i, _vp, _vp, _vp, _vp]
+_lib.feast_mlp_forward.argtypes = [_vp, _vp, _i, _vp]
+_lib.feast_mlp_train_step.argtypes = [_vp, _vp, _vp, _vp, _i, ctypes.c_float, ctypes.POINTER(_d)]
+_lib.feast_sine_expand.argtypes = [_vp, _i, _i, _i, _i, _i, _i, _vp, _vp]
+_lib.feast_sine_project.argtypes = [_vp, _i, _i, _i, _i, _i, _i, _vp, _vp]
+_lib.feast_predict_Y.argtypes = [_vp, _vp, _i, _i, _i, _i, _i, _i, _vp]
 _lib.feast_solve_batched.argtypes = [_vp, _i, ctypes.POINTER(feast_operator), _vp, _vp, _vp, _i, _d, _vp, _vp, _vp,
                                      _vp, _vp, _vp, _vp, _i]
 for _f in EXPORTED:
@@ -259,6 +269,66 @@ def feast_reduced_eig_noalloc(AQ, BQ, M0, eps, Phi, stream=None) -> int:
     the feast_status code (FEAST_OK, FEAST_ERR_ARG, FEAST_ERR_BQ_NOT_SPD, ...)."""
     return _lib.feast_reduced_eig_noalloc(_ptr(AQ), _ptr(BQ), int(M0), _ptr(eps), _ptr(Phi),
                                           stream if stream is not None else _current_stream())
+
+
+class Mlp:
+    """Owns one feast_mlp (the learned-start network)."""
+
+    def __init__(self, in_dim, width, out_dim, max_batch, stream=None):
+        self._n = _vp()
+        st = _lib.feast_mlp_create(ctypes.byref(self._n), int(in_dim), int(width), int(out_dim), int(max_batch),
+                                   stream if stream is not None else _current_stream())
+        if st != FEAST_OK:
+            raise FeastError(st, "feast_mlp_create")
+        self.in_dim, self.width, self.out_dim = in_dim, width, out_dim
+
+    def close(self):
+        if self._n:
+            _lib.feast_mlp_destroy(self._n)
+            self._n = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _ok(st, what):
+        if st != FEAST_OK:
+            raise FeastError(st, what)
+
+    def feast_mlp_set_layer(self, k, W, b):
+        self._ok(_lib.feast_mlp_set_layer(self._n, int(k), _ptr(W), _ptr(b)), "feast_mlp_set_layer")
+
+    def feast_mlp_get_layer(self, k, W=None, b=None, gW=None, gb=None):
+        self._ok(_lib.feast_mlp_get_layer(self._n, int(k), _ptr(W), _ptr(b), _ptr(gW), _ptr(gb)), "feast_mlp_get_layer")
+
+    def feast_mlp_forward(self, X, B, out):
+        self._ok(_lib.feast_mlp_forward(self._n, _ptr(X), int(B), _ptr(out)), "feast_mlp_forward")
+
+    def feast_mlp_train_step(self, X, target, weights, B, lr):
+        loss = ctypes.c_double(0.0)
+        self._ok(_lib.feast_mlp_train_step(self._n, _ptr(X), _ptr(target), _ptr(weights), int(B), float(lr),
+                                           ctypes.byref(loss)), "feast_mlp_train_step")
+        return loss.value
+
+    def feast_predict_Y(self, features, nx, ny, nz, M0, px, py, Y):
+        self._ok(_lib.feast_predict_Y(self._n, _ptr(features), nx, ny, nz, M0, px, py, _ptr(Y)), "feast_predict_Y")
+
+
+def feast_sine_expand(coef, nx, ny, nz, M0, px, py, Y, stream=None):
+    st = _lib.feast_sine_expand(_ptr(coef), nx, ny, nz, M0, px, py, _ptr(Y),
+                                stream if stream is not None else _current_stream())
+    if st != FEAST_OK:
+        raise FeastError(st, "feast_sine_expand")
+
+
+def feast_sine_project(X, nx, ny, nz, M0, px, py, coef, stream=None):
+    st = _lib.feast_sine_project(_ptr(X), nx, ny, nz, M0, px, py, _ptr(coef),
+                                 stream if stream is not None else _current_stream())
+    if st != FEAST_OK:
+        raise FeastError(st, "feast_sine_project")
 
 
 def library_path() -> str:
