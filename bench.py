@@ -38,6 +38,32 @@ Y_SEED = 1000
 TF32_NOMINAL_RATIO = 1.1 / 2.25       # dense TF32 / BF16 tensor rate (nominal)
 FP64_PEAK_TFLOPS = 1.25               # GB300 FP64 rate (CUDA cores and tensor cores alike)
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+FP32_LANES = 152 * 128                # FP32 lanes of a GB300 (152 SMs x 128)
+SM_MAX_MHZ = 2070.0
+FF_OPS_PER_ENTRY = 27 * 4 * 11        # fp32 instructions per complex entry of the double-float residual
+
+
+def roofline(name, ms, flops, launches, pk, pk_src):
+    """Roofline object of one kernel class from its summed device time and
+    algorithmic work (216 flops per complex entry for the residuals)."""
+    achieved = flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+    if name == "fp64_residual":
+        roof = {"kernel": "k_mx_residual (FP64 refinement residual)", "bound": "alu", "unit": "TFLOP/s",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "peak_source": "GB300 FP64 rate (derived)"}
+    elif name == "ff_residual":
+        ops = flops / 216.0 * FF_OPS_PER_ENTRY
+        roof = {"kernel": "k_mx_residual_inc (double-float refinement residual)", "bound": "alu",
+                "unit": "T fp32 instr/s", "achieved": ops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0,
+                "peak": FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (derived)"}
+    else:
+        roof = {"kernel": name, "bound": "tensor", "unit": "TFLOP/s", "achieved": achieved,
+                "peak": pk["bf16_tflops_sustained"] * TF32_NOMINAL_RATIO,
+                "peak_source": f"{pk_src} bf16 sustained x TF32/BF16 nominal ratio"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["flops_per_launch"] = flops / launches if launches else None
+    roof["traffic"] = None
+    return roof
 
 
 def parse():
@@ -47,8 +73,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched64"],
+                    help="single: the 32x32x400 pencil; batched64: 64 uneven instances in one batched call")
     ap.add_argument("--skip-fp64", action="store_true", help="do not time the plain FP64 GPU path")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--no-ir-early", action="store_true",
+                    help="refine every loop to 1e-12 (default: looser targets in loops 1 and 2)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--layers", type=int, default=400,
@@ -286,7 +316,7 @@ def run_ours(args):
     resid = torch.zeros(M0, dtype=torch.float64, device=dev)
     prec = F.FEAST_PREC_MIXED if args.precision == "mixed" else F.FEAST_PREC_FP64
     stream = torch.cuda.current_stream()
-    h = F.Handle(precision=prec, seed=Y_SEED, stream=stream.cuda_stream, profile=True)
+    h = F.Handle(precision=prec, seed=Y_SEED, stream=stream.cuda_stream, profile=True, ir_early=not args.no_ir_early)
 
     def step():
         r = h.feast_solve(dop, iv["lmin"], iv["lmax"], M0, Ne, wl.tol, None, lam, X, resid, allow=())
@@ -304,9 +334,9 @@ def run_ours(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     results = []
-    kms = np.zeros(8)
-    kfl = np.zeros(8)
-    kn = np.zeros(8)
+    kms = np.zeros(F.KERNEL_CLASS_SLOTS)
+    kfl = np.zeros(F.KERNEL_CLASS_SLOTS)
+    kn = np.zeros(F.KERNEL_CLASS_SLOTS)
     launches = 0
     for _ in range(args.steps):
         r, ok = step()
@@ -332,25 +362,24 @@ def run_ours(args):
     if not args.skip_e2e:
         A_h = torch.from_numpy(op.A27).pin_memory()
         B_h = torch.from_numpy(op.B27).pin_memory()
-        Y_h = torch.from_numpy(np.ascontiguousarray(workloads.random_Y(N, M0, Y_SEED).T)).pin_memory()
         lam_h = torch.zeros(M0, dtype=torch.float64).pin_memory()
         X_h = torch.zeros((M0, N), dtype=torch.float64).pin_memory()
         res_h = torch.zeros(M0, dtype=torch.float64).pin_memory()
         hop = F.make_operator(op.nx, op.ny, op.nz, A_h, B_h)
-        h_e2e = F.Handle(precision=prec, seed=Y_SEED, stream=stream.cuda_stream)
-        h_e2e.feast_solve(hop, iv["lmin"], iv["lmax"], M0, Ne, wl.tol, Y_h, lam_h, X_h, res_h, allow=())
+        h_e2e = F.Handle(precision=prec, seed=Y_SEED, stream=stream.cuda_stream, ir_early=not args.no_ir_early)
+        h_e2e.feast_solve(hop, iv["lmin"], iv["lmax"], M0, Ne, wl.tol, None, lam_h, X_h, res_h, allow=())
         barrier(world)
         t0 = time.perf_counter()
         e2e_found = 0
         for _ in range(args.e2e_steps):
-            r = h_e2e.feast_solve(hop, iv["lmin"], iv["lmax"], M0, Ne, wl.tol, Y_h, lam_h, X_h, res_h, allow=())
+            r = h_e2e.feast_solve(hop, iv["lmin"], iv["lmax"], M0, Ne, wl.tol, None, lam_h, X_h, res_h, allow=())
             if r.m_found == M and float(res_h[:M].max()) <= 1e-10:
                 e2e_found += r.m_found
         t_e2e = allreduce_max(time.perf_counter() - t0, world)
         e2e_total = allreduce_sum(e2e_found, world)
         h_e2e.close()
         e2e = {"value": e2e_total / t_e2e, "unit": UNIT, "steps": args.e2e_steps,
-               "h2d_bytes_per_step": 2 * 27 * N * 8 + N * M0 * 8, "d2h_bytes_per_step": N * M0 * 8 + 2 * M0 * 8}
+               "h2d_bytes_per_step": 2 * 27 * N * 8, "d2h_bytes_per_step": N * M0 * 8 + 2 * M0 * 8}
 
     # ---- plain FP64 GPU path, one solve (the comparison baseline)
     fp64 = None
@@ -372,23 +401,19 @@ def run_ours(args):
     tf32_peak = pk["bf16_tflops_sustained"] * TF32_NOMINAL_RATIO
     names = F.KERNEL_CLASSES
     kernels = {}
-    for c in range(8):
+    for c in range(len(names)):
         if kn[c] > 0:
             kernels[names[c]] = {"ms_total": round(kms[c], 3), "launches": int(kn[c]),
                                  "avg_us": round(kms[c] / kn[c] * 1e3, 2),
                                  "tflops": round(kfl[c] / (kms[c] * 1e-3) / 1e12, 3) if kms[c] > 0 else None}
     # the dominant kernel class by device time
     dom = int(np.argmax(kms))
-    achieved = kfl[dom] / (kms[dom] * 1e-3) / 1e12 if kms[dom] > 0 else 0.0
-    if names[dom] == "fp64_residual":
-        roof = {"kernel": "k_mx_residual (FP64 refinement residual)", "bound": "alu", "unit": "TFLOP/s",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "peak_source": "GB300 FP64 rate (derived)"}
-    else:
-        roof = {"kernel": names[dom], "bound": "tensor", "unit": "TFLOP/s", "achieved": achieved,
-                "peak": tf32_peak, "peak_source": f"{pk_src} bf16 sustained x TF32/BF16 nominal ratio"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["flops_per_launch"] = kfl[dom] / kn[dom] if kn[dom] else None
-    roof["traffic"] = None
+    roof = roofline(names[dom], kms[dom], kfl[dom], kn[dom], pk, pk_src)
+    for c, nm in enumerate(names):
+        if nm in kernels and kms[c] > 0:
+            rc = roofline(nm, kms[c], kfl[c], kn[c], pk, pk_src)
+            kernels[nm]["roofline_frac"] = round(rc["frac"], 4)
+            kernels[nm]["bound"] = rc["bound"]
     lu = kfl[0] / (kms[0] * 1e-3) / 1e12 if kms[0] > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -397,6 +422,7 @@ def run_ours(args):
         "config": {"workload": "Q1 FE 32x32x400 (N=409600, 400 layers of 1024), 32 Gaussians seed 0, "
                                "lowest 100 eigenpairs, M0=128, Ne=8, tol 1e-12",
                    "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "ir_early": not args.no_ir_early,
                    "l2": "inputs larger than L2 (27 GB of factors per solve)"},
         "valid": valid, "m_found": last.m_found, "loops": last.loops, "resid_max": last.info.resid_max,
         "ir_steps_max": last.info.ir_steps_max,
@@ -407,6 +433,130 @@ def run_ours(args):
         "cpu_baseline": cpu_baseline_obj(cpu) if cpu and "value" in cpu else cpu,
     }
     return line
+
+
+def run_batched(args):
+    """The batched form: 64 independent Q1 instances of uneven size (cross
+    sections 16/24/32, 50-400 layers, M0 32/64/128, intervals certified by the
+    oracle's inertia count) solved by one feast_solve_batched call per step.
+    Beside it: the same instances one after another on one handle, and the
+    plain FP64 path on a 4-instance sample."""
+    import numpy as np
+    import torch
+
+    import paper_0901_2665_gb300 as F
+    import workloads
+
+    world, rank, local = dist_setup(args.gpus)
+    rank0 = rank == 0
+    dev = torch.device("cuda", torch.cuda.current_device())
+    with open(os.path.join(ROOT, "tests", "golden", "batch_intervals.json")) as f:
+        ivs = json.load(f)
+    inst = workloads.batch_instances(len(ivs))
+    keep, ops, lo, hi, m0s, Ms, lams, Xs, res = [], [], [], [], [], [], [], [], []
+    for bi in inst:
+        iv = ivs[str(bi.index)]
+        op = bi.operator()
+        A = torch.from_numpy(op.A27).to(dev)
+        B = torch.from_numpy(op.B27).to(dev)
+        keep += [A, B]
+        ops.append(F.make_operator(op.nx, op.ny, op.nz, A, B))
+        lo.append(iv["lmin"])
+        hi.append(iv["lmax"])
+        m0s.append(bi.M0)
+        Ms.append(iv["M"])
+        lams.append(torch.zeros(bi.M0, dtype=torch.float64, device=dev))
+        Xs.append(torch.zeros((bi.M0, op.N), dtype=torch.float64, device=dev))
+        res.append(torch.zeros(bi.M0, dtype=torch.float64, device=dev))
+    Ne, tol = 8, 1e-12
+    stream = torch.cuda.current_stream()
+    h = F.Handle(precision=F.FEAST_PREC_MIXED, seed=Y_SEED, stream=stream.cuda_stream)
+
+    def check(mf, idx):
+        ok = 0
+        for i in idx:
+            if mf[i] == Ms[i] and float(res[i][:Ms[i]].max()) <= 1e-10:
+                ok += Ms[i]
+        return ok
+
+    def batched():
+        st, mf, lp, sts = h.feast_solve_batched(ops, lo, hi, m0s, Ne, tol, None, lams, Xs, res, workers=0)
+        return check(mf, range(len(ops))), lp, h.info().gpu_launches
+
+    for _ in range(args.warmup):
+        batched()
+    clocks = ClockSampler(gpu_uuid() if rank0 else None)
+    barrier(world)
+    torch.cuda.synchronize()
+    if rank0:
+        clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    found, loops, launches = 0, None, 0
+    for _ in range(args.steps):
+        f, loops, nl = batched()
+        found += f
+        launches += nl
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop() if rank0 else None
+    t_max = allreduce_max(ev0.elapsed_time(ev1), world)
+    total = allreduce_sum(found, world)
+    wanted = sum(Ms) * args.steps
+    value = total / (t_max * 1e-3)
+
+    def sequential(handle, idx):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mf = [0] * len(ops)
+        kinfo = []
+        for i in idx:
+            r = handle.feast_solve(ops[i], lo[i], hi[i], m0s[i], Ne, tol, None, lams[i], Xs[i], res[i], allow=())
+            mf[i] = r.m_found
+            kinfo.append(r.info)
+        torch.cuda.synchronize()
+        return check(mf, idx) / (time.perf_counter() - t0), kinfo
+
+    seq_value, _ = sequential(h, range(len(ops)))
+    sample = [0, 16, 32, 48]
+    hp = F.Handle(precision=F.FEAST_PREC_MIXED, seed=Y_SEED, stream=stream.cuda_stream, profile=True)
+    mixed_sample, infos = sequential(hp, sample)
+    hp.close()
+    fp64_sample = None
+    if not args.skip_fp64:
+        h64 = F.Handle(precision=F.FEAST_PREC_FP64, seed=Y_SEED, stream=stream.cuda_stream)
+        fp64_sample, _ = sequential(h64, sample)
+        h64.close()
+    h.close()
+    if not rank0:
+        return None
+    names = F.KERNEL_CLASSES
+    kms = np.sum([np.array(i.kernel_ms[:]) for i in infos], axis=0)
+    kfl = np.sum([np.array(i.kernel_flops[:]) for i in infos], axis=0)
+    kn = np.sum([np.array(i.kernel_launches[:]) for i in infos], axis=0)
+    dom = int(np.argmax(kms))
+    pk, pk_src = peaks()
+    roof = roofline(names[dom], kms[dom], kfl[dom], kn[dom], pk, pk_src)
+    roof["measured_on"] = "profiled sequential solves of instances 0, 16, 32, 48"
+    sides = sorted({(b.nx, b.M0) for b in inst})
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "tf32+f64", "data": "synthetic",
+        "config": {"workload": f"{len(ops)} independent Q1 FE instances, cross sections 16/24/32, 50-400 layers, "
+                               "M0 32/64/128, 8 Gaussians each, certified intervals (~0.75 M0 pairs), Ne=8, tol 1e-12",
+                   "form": "batched (feast_solve_batched, memory-bounded workers, largest first)",
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (factors of several GB)"},
+        "valid": total == allreduce_sum(sum(Ms) * args.steps, world) if world > 1 else total == wanted,
+        "eigenpairs_per_step": sum(Ms), "loops_max": int(max(loops)) if loops is not None else None,
+        "sequential": {"value": seq_value, "unit": UNIT, "what": "the same 64 instances one after another"},
+        "mixed_sample": {"value": mixed_sample, "unit": UNIT, "instances": sample},
+        "fp64_sample": {"value": fp64_sample, "unit": UNIT, "instances": sample,
+                        "what": "plain FP64 GPU path, sequential"},
+        "roofline": roof, "gpu_launches": int(launches), "clocks": clk, "shapes": sides,
+    }
 
 
 def run_reference(args):
@@ -440,7 +590,12 @@ def main():
         os.environ.setdefault("CUDA_VISIBLE_DEVICES", "")
         print(json.dumps(oracle_sample(args.sample_layers, args.loops)))
         return
-    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        line = run_reference(args)
+    elif args.workload == "batched64":
+        line = run_batched(args)
+    else:
+        line = run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)
 

@@ -59,7 +59,8 @@ typedef enum {
   FEAST_ERR_OOM = 6,             /* device workspace allocation failed */
   FEAST_ERR_CUDA = 7,            /* CUDA runtime error */
   FEAST_ERR_TIMEOUT = 8,         /* a bounded device wait gave up */
-  FEAST_ERR_JACOBI = 9           /* reduced eigensolve did not converge */
+  FEAST_ERR_JACOBI = 9,          /* reduced eigensolve did not converge */
+  FEAST_ERR_NONFINITE = 10       /* a predicted start block holds a non-finite value */
 } feast_status;
 
 enum { FEAST_PREC_FP64 = 0, FEAST_PREC_MIXED = 1 };
@@ -87,9 +88,15 @@ typedef struct {
   uint64_t seed;      /* start block when Y0 == NULL: Y(row, col) = uniform [-1, 1)
                          from SplitMix64 output col*N + row of this seed */
   int profile;        /* 1: time the main kernel classes with CUDA events (feast_info.kernel_ms) */
+  int ir_early;       /* MIXED, random start (Y0 == NULL) only: 1 (default) loosens the refinement
+                         target of loop 1 to 1e-5 and of loop 2 to 1e-8 (never below ir_tol); a
+                         loop with a loosened target never ends the iteration.  0, or a given
+                         start block: ir_tol in every loop. */
 } feast_options;
 
 /* Per-solve diagnostics, valid after feast_solve (also after a failing one). */
+#define FEAST_KERNEL_CLASSES 12
+
 typedef struct {
   int loops;
   int m_found;
@@ -102,17 +109,18 @@ typedef struct {
   double t_rr_ms;           /* device time of Rayleigh-Ritz (Gram, eigensolve, X = Q Phi) */
   double t_total_ms;        /* wall time of the call */
   int ir_steps_max;         /* MIXED: most refinement steps taken by one node solve */
-  double ir_resid_max;      /* MIXED: worst final relative residual of a node solve */
+  double ir_resid_max;      /* MIXED: worst final relative residual of a node solve run to ir_tol */
   long long factor_flops;   /* algorithmic flops of the factorisation (8 n^3 per layer per node) */
   /* kernel accounting of the call: launches of the library's kernels, and
      with options.profile the summed device time and launch count per class:
      0 sweep-update GEMM, 1 block-solve GEMM, 2 panel inversion, 3 panel
      product/packing, 4 Schur complements, 5 solve couplings, 6 FP64
-     refinement residual, 7 FP64-path factor/solve kernels */
+     refinement residual, 7 FP64-path factor/solve kernels, 8 incremental
+     double-float refinement residual; the rest are zero */
   long long gpu_launches;
-  double kernel_ms[8];
-  long long kernel_launches[8];
-  double kernel_flops[8];   /* algorithmic flops of each class (complex FMA = 8 real flops;
+  double kernel_ms[FEAST_KERNEL_CLASSES];
+  long long kernel_launches[FEAST_KERNEL_CLASSES];
+  double kernel_flops[FEAST_KERNEL_CLASSES];   /* algorithmic flops of each class (complex FMA = 8 real flops;
                                a TF32 product counts once) */
 } feast_info;
 
@@ -166,7 +174,9 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
  * Worker threads, each with its own stream and workspace, take the instances
  * largest first; `workers` bounds their number (0 = as many as the device
  * memory allows, at most 8).  Returns FEAST_OK when every instance
- * succeeded, else the status of the first failing instance.  Synchronises.
+ * succeeded, else the status of the first failing instance; the handle's
+ * feast_info.gpu_launches then counts every worker's kernel launches.
+ * Synchronises.
  */
 feast_status feast_solve_batched(feast_handle* h, int count, const feast_operator* ops, const double* lmin,
                                  const double* lmax, const int* M0, int Ne, double tol, const double* const* Y0,
@@ -279,7 +289,9 @@ feast_status feast_sine_expand(const float* coef, int nx, int ny, int nz, int M0
 /* The adjoint: coef[l, c, q px + p] = sum_{ix, iy} X[l n + ix + nx iy, c] s_p(ix) s_q(iy). */
 feast_status feast_sine_project(const double* X, int nx, int ny, int nz, int M0, int px, int py, float* coef,
                                 void* cuda_stream);
-/* Y = expansion of the network's output for the nz layer features (nz x in_dim). */
+/* Y = expansion of the network's output for the nz layer features (nz x in_dim).
+   FEAST_ERR_NONFINITE (Y untouched) if an output coefficient is not finite:
+   the caller then starts from a random block instead. */
 feast_status feast_predict_Y(feast_mlp* net, const float* features, int nx, int ny, int nz, int M0, int px, int py,
                              double* Y);
 

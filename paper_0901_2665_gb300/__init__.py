@@ -37,6 +37,7 @@ FEAST_ERR_OOM = 6
 FEAST_ERR_CUDA = 7
 FEAST_ERR_TIMEOUT = 8
 FEAST_ERR_JACOBI = 9
+FEAST_ERR_NONFINITE = 10
 STATUS_NAMES = {v: k for k, v in globals().items() if k.startswith("FEAST_ERR_") or k == "FEAST_OK"}
 
 FEAST_PREC_FP64 = 0
@@ -58,7 +59,11 @@ class feast_operator(ctypes.Structure):
 
 class feast_options(ctypes.Structure):
     _fields_ = [("max_loops", ctypes.c_int), ("precision", ctypes.c_int), ("ir_tol", ctypes.c_double),
-                ("ir_max", ctypes.c_int), ("seed", ctypes.c_uint64), ("profile", ctypes.c_int)]
+                ("ir_max", ctypes.c_int), ("seed", ctypes.c_uint64), ("profile", ctypes.c_int),
+                ("ir_early", ctypes.c_int)]
+
+
+KERNEL_CLASS_SLOTS = 12   # FEAST_KERNEL_CLASSES
 
 
 class feast_info(ctypes.Structure):
@@ -69,12 +74,13 @@ class feast_info(ctypes.Structure):
                 ("t_rr_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double),
                 ("ir_steps_max", ctypes.c_int), ("ir_resid_max", ctypes.c_double),
                 ("factor_flops", ctypes.c_longlong), ("gpu_launches", ctypes.c_longlong),
-                ("kernel_ms", ctypes.c_double * 8), ("kernel_launches", ctypes.c_longlong * 8),
-                ("kernel_flops", ctypes.c_double * 8)]
+                ("kernel_ms", ctypes.c_double * KERNEL_CLASS_SLOTS),
+                ("kernel_launches", ctypes.c_longlong * KERNEL_CLASS_SLOTS),
+                ("kernel_flops", ctypes.c_double * KERNEL_CLASS_SLOTS)]
 
 
 KERNEL_CLASSES = ["sweep_gemm", "solve_gemm", "panel_inverse", "panel_product", "schur", "solve_coupling",
-                  "fp64_residual", "fp64_path"]
+                  "fp64_residual", "fp64_path", "ff_residual"]
 
 
 _vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
@@ -174,10 +180,11 @@ class Handle:
     """Owns one feast_handle (feast_init / feast_destroy)."""
 
     def __init__(self, precision: int = FEAST_PREC_FP64, max_loops: int = 20, ir_tol: float = 1e-12,
-                 ir_max: int = 30, seed: int = 1000, stream=None, profile: bool = False):
+                 ir_max: int = 30, seed: int = 1000, stream=None, profile: bool = False, ir_early: bool = True):
         opt = default_options()
         opt.precision, opt.max_loops, opt.ir_tol, opt.ir_max, opt.seed = precision, max_loops, ir_tol, ir_max, seed
         opt.profile = 1 if profile else 0
+        opt.ir_early = 1 if ir_early else 0
         self._h = _vp()
         st = _lib.feast_init(ctypes.byref(self._h), ctypes.byref(opt), stream if stream is not None else _current_stream())
         if st != FEAST_OK:
@@ -280,7 +287,7 @@ class Mlp:
                                    stream if stream is not None else _current_stream())
         if st != FEAST_OK:
             raise FeastError(st, "feast_mlp_create")
-        self.in_dim, self.width, self.out_dim = in_dim, width, out_dim
+        self.in_dim, self.width, self.out_dim, self.max_batch = in_dim, width, out_dim, max_batch
 
     def close(self):
         if self._n:

@@ -259,7 +259,8 @@ void factor_nodes(feast_handle* h, const OpView& op, int Ne, int precision) {
 }
 
 // Solve the Ne node systems for RHS (N x k real) into G (Ne x N x k complex).
-void solve_nodes(feast_handle* h, const OpView& op, int Ne, int precision, const double* RHS, cplx* G, int k) {
+void solve_nodes(feast_handle* h, const OpView& op, int Ne, int precision, const double* RHS, cplx* G, int k,
+                 double ir_tol) {
   const int n = op.g.n();
   if (precision == FEAST_PREC_FP64) {
     h->Tmp.ensure(sizeof(cplx) * (size_t)Ne * n * k, "solve scratch");
@@ -268,10 +269,10 @@ void solve_nodes(feast_handle* h, const OpView& op, int Ne, int precision, const
   } else {
     MixedSolveStats st;
     const char* msg = mixed_solve(h->stream, op.g, Ne, h->Zd.as<cplx>(), op.A27, op.B27, h->mixed, RHS, G, k,
-                                  h->opt.ir_tol, h->opt.ir_max, &st, h->status.as<int>());
+                                  ir_tol, h->opt.ir_max, &st, h->status.as<int>());
     if (msg) fail(FEAST_ERR_CUDA, msg);
     h->info.ir_steps_max = std::max(h->info.ir_steps_max, st.steps_max);
-    h->info.ir_resid_max = std::max(h->info.ir_resid_max, st.resid_max);
+    if (ir_tol <= h->opt.ir_tol) h->info.ir_resid_max = std::max(h->info.ir_resid_max, st.resid_max);
   }
 }
 
@@ -328,6 +329,7 @@ void feast_default_options(feast_options* opt) {
   opt->precision = FEAST_PREC_FP64;
   opt->ir_tol = 1e-12;
   opt->ir_max = 30;
+  opt->ir_early = 1;
   opt->seed = 1000;
   opt->profile = 0;
 }
@@ -415,7 +417,7 @@ feast_status feast_node_solve(feast_handle* h, const feast_operator* op, double 
     h->info.ir_resid_max = 0.0;
     factor_nodes(h, v, 1, precision);
     check_status(h);
-    solve_nodes(h, v, 1, precision, RHS, reinterpret_cast<cplx*>(Qe), k);
+    solve_nodes(h, v, 1, precision, RHS, reinterpret_cast<cplx*>(Qe), k, h->opt.ir_tol);
     check_status(h);
   });
 }
@@ -435,7 +437,7 @@ feast_status feast_quadrature(feast_handle* h, const feast_operator* op, double 
     factor_nodes(h, v, Ne, precision);
     check_status(h);
     h->G.ensure(sizeof(cplx) * (size_t)Ne * N * k, "node solutions");
-    solve_nodes(h, v, Ne, precision, RHS, h->G.as<cplx>(), k);
+    solve_nodes(h, v, Ne, precision, RHS, h->G.as<cplx>(), k, h->opt.ir_tol);
     quadrature_sum(h->stream, N, k, Ne, h->coefd.as<cplx>(), h->G.as<cplx>(), N * k, Q);
     check_status(h);
   });
@@ -546,7 +548,13 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
       ck(cudaEventRecord(h->ev[2], s), "event");
       // step 2: RHS = B Y, node solves, quadrature (Eq. 15)
       stencil_apply(s, v.g, v.B27, h->Yb.as<double>(), N, h->RHS.as<double>(), N, M0);
-      solve_nodes(h, v, Ne, prec, h->RHS.as<double>(), h->G.as<cplx>(), M0);
+      // refinement target of this loop: loosened in loops 1 and 2 (their subspace
+      // is still far from converged, so their solves need less accuracy)
+      double ir_loop = h->opt.ir_tol;
+      if (h->opt.ir_early && !Y0 && prec == FEAST_PREC_MIXED && loop <= 2)
+        ir_loop = std::max(ir_loop, loop == 1 ? 1e-5 : 1e-8);
+      const bool exact_loop = ir_loop <= h->opt.ir_tol;
+      solve_nodes(h, v, Ne, prec, h->RHS.as<double>(), h->G.as<cplx>(), M0, ir_loop);
       quadrature_sum(s, N, M0, Ne, h->coefd.as<cplx>(), h->G.as<cplx>(), N * M0, h->Q.as<double>());
       ck(cudaEventRecord(h->ev[3], s), "event");
       // steps 3-5: Rayleigh-Ritz
@@ -572,7 +580,7 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
       if (prev_count >= 0) {
         const double change = scale > 0 ? std::fabs(trace - prev_trace) / scale : 0.0;
         if (loop - 1 < 64) h->info.rel_change[loop - 1] = change;
-        if (count == prev_count && change <= tol) converged = true;
+        if (count == prev_count && change <= tol && exact_loop) converged = true;
       }
       std::swap(h->Xb, h->Yb);  // Y = X: the next right-hand side is B X
       if (converged) break;
@@ -655,6 +663,7 @@ feast_status feast_solve_batched(feast_handle* h, int count, const feast_operato
   if (count < 0 || (count > 0 && (!ops || !lmin || !lmax || !M0 || !lambda || !X || !m_found || !loops || !statuses)))
     return FEAST_ERR_ARG;
   if (count == 0) return FEAST_OK;
+  const long long launches0 = prof::launches();
   // largest instances first
   std::vector<int> order(count);
   std::vector<double> bytes(count);
@@ -703,6 +712,7 @@ feast_status feast_solve_batched(feast_handle* h, int count, const feast_operato
     });
   }
   for (auto& t : pool) t.join();
+  h->info.gpu_launches = prof::launches() - launches0;   // every worker's launches
   for (int i = 0; i < count; ++i)
     if (statuses[i] != FEAST_OK) {
       h->err = "instance " + std::to_string(i) + ": " + errs[i];

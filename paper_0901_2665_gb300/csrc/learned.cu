@@ -241,6 +241,14 @@ __global__ void k_mlp_cast(const float* __restrict__ W, int rows, int cols, int 
   }
 }
 
+// flag[0] = 1 if any of the n values is not finite
+__global__ void k_mlp_finite(const float* __restrict__ v, long long n, int* __restrict__ flag) {
+  bool bad = false;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    bad |= !isfinite(v[t]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
 // ---------------------------------------------------------------- sine basis
 __device__ __forceinline__ float sine_vec(int p1, int i, int m) {
   // sqrt(2/(m+1)) sin(p pi (i+1)/(m+1)), p1 = p (1-based)
@@ -543,6 +551,15 @@ feast_status feast_predict_Y(feast_mlp* net, const float* features, int nx, int 
                                                                       net->HT[0]);
   feast::prof::count_launch();
   if (forward_rows(net, nz) != FEAST_OK) return FEAST_ERR_CUDA;
+  const long long nout = (long long)nz * net->out_dim;
+  cudaMemsetAsync(net->status + 1, 0, sizeof(int), net->stream);
+  k_mlp_finite<<<blocks_for(nout), 256, 0, net->stream>>>(net->Z[4], nout, net->status + 1);
+  feast::prof::count_launch();
+  int bad = 0;
+  if (cudaMemcpyAsync(&bad, net->status + 1, sizeof(int), cudaMemcpyDeviceToHost, net->stream) != cudaSuccess ||
+      cudaStreamSynchronize(net->stream) != cudaSuccess)
+    return FEAST_ERR_CUDA;
+  if (bad) return FEAST_ERR_NONFINITE;
   // rows of Z[4] are layers, columns (c, pq): exactly the coefficient layout
   const feast_status st = feast_sine_expand(net->Z[4], nx, ny, nz, M0, px, py, Y, net->stream);
   if (st != FEAST_OK) return st;

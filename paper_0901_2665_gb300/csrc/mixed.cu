@@ -526,13 +526,15 @@ constexpr size_t kResSmem = sizeof(cplx) * 27 * kResRows;
 // R_e = RHS - (Z_e B - A) Q_e in FP64 (108 FP64 FMAs per complex entry, the
 // only FP64 arithmetic of the kernel): the block's 128 rows keep their 27
 // complex coefficients in shared memory while the threads sweep the columns.
-// Stores R as complex64 and per-block partial sums of |R|^2 and |RHS|^2.
+// Stores R in FP64 (R64, the start of the incremental residuals) and as
+// complex64 (the next correction's right-hand side), and per-block partial
+// sums of |R|^2 and |RHS|^2.
 __global__ void __launch_bounds__(kResThreads) k_mx_residual(Dims d, const cplx* __restrict__ Z,
                                                              const double* __restrict__ A27,
                                                              const double* __restrict__ B27,
                                                              const double* __restrict__ RHS,
                                                              const cplx* __restrict__ Q, f2* __restrict__ Rc,
-                                                             double* __restrict__ partial,
+                                                             cplx* __restrict__ R64, double* __restrict__ partial,
                                                              const int* __restrict__ active) {
   extern __shared__ cplx rsm[];
   __shared__ double red[2][kResThreads];
@@ -584,6 +586,7 @@ __global__ void __launch_bounds__(kResThreads) k_mx_residual(Dims d, const cplx*
         aim = fma(-c.im, v.re, aim);
       }
       Rc[e * sG + (long long)m * d.N + i] = f2{(float)are, (float)aim};
+      R64[e * sG + (long long)m * d.N + i] = cplx{are, aim};
       rr += are * are + aim * aim;
       bb += b * b;
     }
@@ -602,6 +605,129 @@ __global__ void __launch_bounds__(kResThreads) k_mx_residual(Dims d, const cplx*
     partial[((long long)e * gridDim.x + blockIdx.x) * 2] = red[0][0];
     partial[((long long)e * gridDim.x + blockIdx.x) * 2 + 1] = red[1][0];
   }
+}
+
+// ---- incremental residual in double-float arithmetic
+//
+// After a correction delta (the complex64 solution of the previous residual,
+// added exactly into Q_e in FP64) the residual moves by -(Z_e B - A) delta:
+//   R <- R - (Z_e B - A) delta.
+// delta is exact in fp32 and its size falls by the refinement's contraction
+// each step, so the product needs about twice fp32's precision relative to
+// |C| |delta|, not FP64's relative to |C| |Q|.  Each coefficient c (FP64) is
+// split into c_hi + c_lo (fp32); c_hi * delta is formed exactly as a pair by
+// one FMA (Dekker's product) and the 27-term sums are compensated with
+// Knuth's TwoSum, i.e. the accurate dot product of Ogita, Rump and Oishi
+// (SIAM J. Sci. Comput. 26, 2005) with the low coefficient part folded into the
+// error term.  The rounding-explicit intrinsics keep the compiler from fusing
+// the product into the sum, which would break the exact error terms.
+__device__ __forceinline__ void ff_axpy(float ch, float cl, float v, float& sh, float& sl) {
+  const float p = __fmul_rn(ch, v);
+  const float pe = __fmaf_rn(ch, v, -p);            // ch * v = p + pe exactly
+  const float t = __fadd_rn(sh, p);
+  const float bp = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(p, bp));   // sh + p = t + err
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(err, __fmaf_rn(cl, v, pe)));
+}
+
+// R64 <- R64 - (Z_e B - A) delta, Rc <- complex64(R64), partial |R|^2 per block
+// (the |RHS|^2 partials of the first residual are kept).
+__global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, const cplx* __restrict__ Z,
+                                                                 const double* __restrict__ A27,
+                                                                 const double* __restrict__ B27,
+                                                                 const f2* __restrict__ delta, f2* __restrict__ Rc,
+                                                                 cplx* __restrict__ R64, double* __restrict__ partial,
+                                                                 const int* __restrict__ active) {
+  extern __shared__ float4 csm[];   // per (slot, row): Re c hi/lo, Im c hi/lo
+  __shared__ double red[kResThreads];
+  const int e = blockIdx.y;
+  const int tid = threadIdx.x;
+  if (!active[e]) return;
+  const long long i0 = (long long)blockIdx.x * kResRows;
+  const cplx z = Z[e];
+  for (int t = tid; t < 27 * kResRows; t += kResThreads) {
+    const int s = t / kResRows, r = t % kResRows;
+    const long long i = i0 + r;
+    float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < d.N) {
+      const int ix = (int)(i % d.nx), iy = (int)((i / d.nx) % d.ny), iz = (int)(i / d.n);
+      const int dx = slot_dx(s), dy = slot_dy(s), dz = slot_dz(s);
+      if (ix + dx >= 0 && ix + dx < d.nx && iy + dy >= 0 && iy + dy < d.ny && iz + dz >= 0 && iz + dz < d.nz) {
+        const double a = A27[(long long)s * d.N + i], b = B27[(long long)s * d.N + i];
+        const double cr = z.re * b - a, ci = z.im * b;
+        c.x = (float)cr;
+        c.y = (float)(cr - (double)c.x);
+        c.z = (float)ci;
+        c.w = (float)(ci - (double)c.z);
+      }
+    }
+    csm[t] = c;
+  }
+  __syncthreads();
+  const int r = tid % kResRows;
+  const long long i = i0 + r;
+  double rr = 0.0;
+  if (i < d.N) {
+    const int ix = (int)(i % d.nx), iy = (int)((i / d.nx) % d.ny), iz = (int)(i / d.n);
+    // neighbour validity per axis; an absent neighbour has a zero coefficient
+    // and is read at offset 0 (the row itself) to stay in bounds
+    const bool xm = ix > 0, xp = ix + 1 < d.nx, ym = iy > 0, yp = iy + 1 < d.ny, zm = iz > 0, zp = iz + 1 < d.nz;
+    const int sx = 1, sy = d.nx, sz = d.n;
+    const long long sG = d.N * d.k;
+    const int g = tid / kResRows;   // column group: columns g, g + 2, g + 4, ...
+    constexpr int kGroups = kResThreads / kResRows;
+    for (int m = g; m < d.k; m += 2 * kGroups) {
+      const bool two = m + kGroups < d.k;
+      const f2* v0 = delta + e * sG + (long long)m * d.N + i;
+      const f2* v1 = two ? v0 + (long long)kGroups * d.N : v0;
+      float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;   // column m: Re, Im (hi, lo)
+      float ch = 0.f, cl = 0.f, eh = 0.f, el = 0.f;   // column m + 2
+#pragma unroll 9
+      for (int s = 0; s < 27; ++s) {
+        const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+        const bool ok = (dx < 0 ? xm : (dx > 0 ? xp : true)) && (dy < 0 ? ym : (dy > 0 ? yp : true)) &&
+                        (dz < 0 ? zm : (dz > 0 ? zp : true));
+        const int off = ok ? dx * sx + dy * sy + dz * sz : 0;
+        const float4 c = csm[s * kResRows + r];
+        const f2 x = v0[off];
+        const f2 y = v1[off];
+        ff_axpy(c.x, c.y, x.x, ah, al);      // + Re c Re x
+        ff_axpy(c.x, c.y, x.y, bh, bl);      // + Re c Im x
+        ff_axpy(c.x, c.y, y.x, ch, cl);
+        ff_axpy(c.x, c.y, y.y, eh, el);
+        ff_axpy(-c.z, -c.w, x.y, ah, al);    // - Im c Im x
+        ff_axpy(c.z, c.w, x.x, bh, bl);      // + Im c Re x
+        ff_axpy(-c.z, -c.w, y.y, ch, cl);
+        ff_axpy(c.z, c.w, y.x, eh, el);
+      }
+      {
+        const long long at = e * sG + (long long)m * d.N + i;
+        cplx R = R64[at];
+        R.re -= (double)ah + (double)al;
+        R.im -= (double)bh + (double)bl;
+        R64[at] = R;
+        Rc[at] = f2{(float)R.re, (float)R.im};
+        rr += R.re * R.re + R.im * R.im;
+      }
+      if (two) {
+        const long long at = e * sG + (long long)(m + kGroups) * d.N + i;
+        cplx R = R64[at];
+        R.re -= (double)ch + (double)cl;
+        R.im -= (double)eh + (double)el;
+        R64[at] = R;
+        Rc[at] = f2{(float)R.re, (float)R.im};
+        rr += R.re * R.re + R.im * R.im;
+      }
+    }
+  }
+  red[tid] = rr;
+  __syncthreads();
+  for (int w = kResThreads / 2; w > 0; w >>= 1) {
+    if (tid < w) red[tid] += red[tid + w];
+    __syncthreads();
+  }
+  if (tid == 0) partial[((long long)e * gridDim.x + blockIdx.x) * 2] = red[0];
 }
 
 // rel[e] = sqrt(sum |R|^2 / sum |RHS|^2), blocks summed in order
@@ -647,7 +773,9 @@ cudaError_t launch_tc(cudaStream_t s, dim3 grid, const CUtensorMap& a, const CUt
   return cudaGetLastError();
 }
 
-enum Buf { B_F = 0, B_T1, B_AOP, B_BOP, B_TC, B_PINV, B_GC, B_RC, B_BEMB, B_TOUT, B_PART, B_REL, B_ACTIVE, B_CF, B_FW, B_COUNT };
+enum Buf { B_F = 0, B_T1, B_AOP, B_BOP, B_TC, B_PINV, B_GC, B_RC, B_BEMB, B_TOUT, B_PART, B_REL, B_ACTIVE, B_CF, B_FW,
+           B_R64, B_COUNT };
+static_assert(B_COUNT <= 16, "MixedWork holds 16 buffers");
 
 bool ensure(MixedWork& w, int idx, size_t bytes, cudaStream_t s, bool zero = false) {
   if (w.sizes[idx] >= bytes && w.bufs[idx]) {
@@ -946,11 +1074,14 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
   const dim3 rgrid(cdiv(d.N, kResRows), Ne);
   const long long nblk = rgrid.x;
   static std::once_flag res_once;
-  std::call_once(res_once,
-                 [] { cudaFuncSetAttribute(k_mx_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResSmem); });
+  std::call_once(res_once, [] {
+    cudaFuncSetAttribute(k_mx_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResSmem);
+    cudaFuncSetAttribute(k_mx_residual_inc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResSmem);
+  });
   if (!ensure(w, B_PART, sizeof(double) * 2 * (size_t)Ne * nblk, s)) return "out of device memory";
   if (!ensure(w, B_REL, sizeof(double) * Ne, s)) return "out of device memory";
   if (!ensure(w, B_ACTIVE, sizeof(int) * Ne, s)) return "out of device memory";
+  if (!ensure(w, B_R64, sizeof(cplx) * (size_t)Ne * sG, s)) return "out of device memory (residuals)";
   std::vector<int> active(Ne, 1);
   cudaMemcpyAsync(w.bufs[B_ACTIVE], active.data(), sizeof(int) * Ne, cudaMemcpyHostToDevice, s);
   std::vector<double> rel(Ne, 0.0), final_rel(Ne, 0.0);
@@ -961,15 +1092,27 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
   prof::count_launch();
   int steps = 0;
   for (;;) {
-    prof::begin(s, prof::RESIDUAL);
     {
       int nact = 0;
       for (int e = 0; e < Ne; ++e) nact += active[e];
-      prof::add_work(prof::RESIDUAL, 216.0 * (double)d.N * k * nact);   // 108 FP64 FMAs per complex entry
+      if (steps == 0) {
+        // the first residual in FP64 from Q_e itself
+        prof::begin(s, prof::RESIDUAL);
+        prof::add_work(prof::RESIDUAL, 216.0 * (double)d.N * k * nact);   // 108 FP64 FMAs per complex entry
+        k_mx_residual<<<rgrid, kResThreads, kResSmem, s>>>(d, Z, A27, B27, RHS, G, buf<f2>(w, B_RC),
+                                                           buf<cplx>(w, B_R64), buf<double>(w, B_PART),
+                                                           buf<int>(w, B_ACTIVE));
+        prof::end(s, prof::RESIDUAL);
+      } else {
+        // later residuals move by the last correction, in double-float
+        prof::begin(s, prof::FF_RESIDUAL);
+        prof::add_work(prof::FF_RESIDUAL, 216.0 * (double)d.N * k * nact);
+        k_mx_residual_inc<<<rgrid, kResThreads, kResSmem, s>>>(d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC),
+                                                               buf<cplx>(w, B_R64), buf<double>(w, B_PART),
+                                                               buf<int>(w, B_ACTIVE));
+        prof::end(s, prof::FF_RESIDUAL);
+      }
     }
-    k_mx_residual<<<rgrid, kResThreads, kResSmem, s>>>(d, Z, A27, B27, RHS, G, buf<f2>(w, B_RC),
-                                                       buf<double>(w, B_PART), buf<int>(w, B_ACTIVE));
-    prof::end(s, prof::RESIDUAL);
     prof::count_launch(2);
     k_mx_resnorm<<<Ne, 256, 0, s>>>(Ne, nblk, buf<double>(w, B_PART), buf<double>(w, B_REL), buf<int>(w, B_ACTIVE));
     int st = 0;

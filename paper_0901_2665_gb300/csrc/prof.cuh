@@ -19,7 +19,8 @@ enum Cls {
   COUPLE = 5,       // layer couplings of the solve sweeps
   RESIDUAL = 6,     // FP64 refinement residual
   FP64_SOLVE = 7,   // plain FP64 path: factor and solve kernels
-  NCLS = 8
+  FF_RESIDUAL = 8,  // incremental refinement residual in double-float
+  NCLS = 9
 };
 
 void set_enabled(bool on);

@@ -7,24 +7,35 @@ per-layer features -- those 48 scalars (terms ordered by z-centre, fixed
 affine scaling), the search interval and the layer position -- to the
 coefficients of the start block Y on the layer's 8x8 separable sine basis.
 
-Training targets are FEAST's own converged Ritz vectors (sign-normalised,
-projected on the basis by the library's projection kernel).  The network, the
-projection and the expansion all run in the library's kernels; this module
-only marshals arrays and orders the calls.  A learned start that fails (B_Q
-not positive definite, or a non-finite block) falls back to the random start.
+Training target.  FEAST needs only the span of the wanted eigenvectors, so the
+loss must not depend on their signs or on the basis chosen inside the span.
+The target is therefore the spectral projector (the density matrix of Eq. 3,
+restricted to the sine basis) applied to a fixed probe block: with U an
+orthonormal basis of the coefficient vectors of the M wanted Ritz vectors and
+S fixed seeded probes, columns c < M hold sqrt(D/M) U U^T s_c (D = nz*px*py)
+and columns c >= M hold s_c itself, which keeps Y of full rank M0 (the start
+block of an ideal filter, Eq. 15, applied to the probes).
+
+The network, the projection onto the basis and the expansion run in the
+library's kernels; this module marshals arrays, orders the calls and prepares
+the training labels (a QR of a D x M matrix per instance, on the host: data
+preparation, not part of a solve).  A learned start that FEAST rejects (B_Q not
+positive definite, a failed reduced eigensolve or pivot, a non-finite block)
+falls back to the random start.
 """
 
 from __future__ import annotations
 
 import dataclasses
+import os
 import time
 
 import numpy as np
 
 import workloads
 
-from . import FEAST_ERR_BQ_NOT_SPD, FEAST_ERR_JACOBI, FEAST_ERR_PIVOT, FEAST_OK, FEAST_PREC_MIXED, FeastError, \
-    Handle, Mlp, feast_sine_project, make_operator
+from . import FEAST_ERR_BQ_NOT_SPD, FEAST_ERR_JACOBI, FEAST_ERR_NONFINITE, FEAST_ERR_PIVOT, FEAST_OK, \
+    FEAST_PREC_MIXED, FeastError, Handle, Mlp, feast_sine_project, make_operator
 
 NX, NY, NZ = 24, 24, 100
 GAUSSIANS = 16
@@ -34,7 +45,10 @@ IN_DIM = 3 * GAUSSIANS + 3
 WIDTH = 512
 OUT_DIM = M0 * PX * PY
 FAMILY_XY_SEED = 4
+PROBE_SEED = 77
+D = NZ * PX * PY
 TOL = 1e-12
+FALLBACK = (FEAST_ERR_BQ_NOT_SPD, FEAST_ERR_JACOBI, FEAST_ERR_PIVOT, FEAST_ERR_NONFINITE)
 
 
 def potential(seed: int):
@@ -59,10 +73,44 @@ def features(seed: int, lmin: float, lmax: float) -> np.ndarray:
 
 
 def loss_weights() -> np.ndarray:
-    """Columns of the lowest M pairs weigh 1, the others 1/4."""
+    """Projector columns weigh 1; the probe columns (a constant target) 1/4."""
     w = np.full((M0, PX * PY), 0.25, dtype=np.float32)
     w[:M] = 1.0
     return w.ravel()
+
+
+def probes() -> np.ndarray:
+    """Fixed probe block S (D x M0) of standard normal entries in coefficient
+    space (row l*PX*PY + pq), so that targets have entries of unit size."""
+    return np.random.default_rng(PROBE_SEED).standard_normal((D, M0))
+
+
+def to_columns(coef: np.ndarray) -> np.ndarray:
+    """(NZ, M0', PX*PY) layer-major coefficients -> (D, M0') columns."""
+    return coef.transpose(0, 2, 1).reshape(D, coef.shape[1])
+
+
+def to_layers(cols: np.ndarray) -> np.ndarray:
+    """(D, M0') columns -> (NZ, M0' * PX*PY) rows of the network's output."""
+    return cols.reshape(NZ, PX * PY, cols.shape[1]).transpose(0, 2, 1).reshape(NZ, -1)
+
+
+def subspace_target(coef_wanted: np.ndarray, S: np.ndarray) -> np.ndarray:
+    """Target rows (NZ, M0*PX*PY) for the wanted Ritz vectors' coefficients
+    coef_wanted (NZ, M, PX*PY): projector columns, then probe columns."""
+    U, _ = np.linalg.qr(to_columns(coef_wanted.astype(np.float64)))
+    T = np.concatenate([np.sqrt(D / M) * (U @ (U.T @ S[:, :M])), S[:, M:]], axis=1)
+    return to_layers(T).astype(np.float32)
+
+
+def subspace_sines(pred_rows: np.ndarray, U: np.ndarray):
+    """Largest and mean sine of the principal angles between span(U) (D x M,
+    orthonormal) and the span of all M0 predicted columns."""
+    P = to_columns(pred_rows.reshape(NZ, M0, PX * PY).astype(np.float64))
+    Qp, _ = np.linalg.qr(P)
+    c = np.clip(np.linalg.svd(U.T @ Qp, compute_uv=False), 0.0, 1.0)
+    s = np.sqrt(1.0 - c ** 2)
+    return float(s.max()), float(s.mean())
 
 
 def wide_interval(seed: int):
@@ -87,13 +135,16 @@ class Sample:
     lmax: float
     feats: np.ndarray       # (NZ, IN_DIM)
     coef: np.ndarray        # (NZ, M0 * PX * PY) targets
+    U: np.ndarray           # (D, M) orthonormal basis of the wanted coefficients
+    trunc: float            # largest sine of a wanted vector to the sine basis
 
 
 def generate(seeds, torch, workers: int = 4, log=None):
     """Converged FEAST subspaces for `seeds` (mixed precision, batched), their
-    lowest-M intervals and sine-basis targets."""
+    lowest-M intervals and projector targets."""
     dev = torch.device("cuda")
     h = Handle(precision=FEAST_PREC_MIXED)
+    S = probes()
     out = []
     chunk = 16
     for c0 in range(0, len(seeds), chunk):
@@ -116,18 +167,18 @@ def generate(seeds, torch, workers: int = 4, log=None):
         for i, s in enumerate(part):
             if sts[i] != FEAST_OK or mf[i] <= M:
                 continue
-            lam = lams[i].cpu().numpy()
-            inside = np.sort(lam[:mf[i]])
+            # in-interval pairs come first, ascending: columns 0..M-1 are the lowest M
+            inside = lams[i].cpu().numpy()[:mf[i]]
             lmin = float(inside[0] - 0.5 * (inside[M] - inside[M - 1]))
             lmax = float(0.5 * (inside[M - 1] + inside[M]))
             coef = torch.zeros((NZ, M0, PX * PY), dtype=torch.float32, device=dev)
             feast_sine_project(Xs[i], NX, NY, NZ, M0, PX, PY, coef)
-            C = coef.cpu().numpy()
-            # sign: the largest coefficient of every column positive
-            flat = C.transpose(1, 0, 2).reshape(M0, -1)
-            sgn = np.sign(flat[np.arange(M0), np.abs(flat).argmax(axis=1)])
-            C = C * sgn[None, :, None]
-            out.append(Sample(s, lmin, lmax, features(s, lmin, lmax), C.reshape(NZ, -1).astype(np.float32)))
+            C = coef.cpu().numpy()[:, :M, :]
+            xn = np.linalg.norm(Xs[i][:M].cpu().numpy(), axis=1)
+            cn = np.sqrt((C.astype(np.float64) ** 2).sum(axis=(0, 2)))
+            trunc = float(np.sqrt(np.clip(1.0 - (cn / xn) ** 2, 0.0, 1.0)).max())
+            U, _ = np.linalg.qr(to_columns(C.astype(np.float64)))
+            out.append(Sample(s, lmin, lmax, features(s, lmin, lmax), subspace_target(C, S), U, trunc))
         if log:
             log(f"generated {len(out)} / {c0 + len(part)}")
     h.close()
@@ -142,66 +193,169 @@ def init_params(seed: int):
             for fi, fo in zip(sizes[:-1], sizes[1:])]
 
 
-def train_network(samples, torch, epochs: int = 40, batch_instances: int = 32, lr: float = 1e-3, seed: int = 0,
-                  log=None):
-    """Trains a fresh network on `samples` with the library's kernels (Adam,
-    minibatches of whole instances, gathered on the host).  Returns
-    (net, target scale, per-epoch losses)."""
+def predict_rows(net: Mlp, samples, torch) -> np.ndarray:
+    """Network output rows (n, NZ, OUT_DIM) for the samples' features."""
+    dev = torch.device("cuda")
+    per = max(1, net_capacity(net) // NZ)
+    out = np.zeros((len(samples), NZ, OUT_DIM), dtype=np.float32)
+    for b0 in range(0, len(samples), per):
+        part = samples[b0:b0 + per]
+        x = torch.from_numpy(np.concatenate([s.feats for s in part])).to(dev)
+        y = torch.zeros((len(part) * NZ, OUT_DIM), dtype=torch.float32, device=dev)
+        net.feast_mlp_forward(x, len(part) * NZ, y)
+        out[b0:b0 + len(part)] = y.cpu().numpy().reshape(len(part), NZ, OUT_DIM)
+    return out
+
+
+def net_capacity(net: Mlp) -> int:
+    return net.max_batch
+
+
+def validate(net: Mlp, samples, torch):
+    """Mean over samples of the largest and of the mean principal-angle sine
+    between the wanted coefficient space and the predicted span."""
+    pred = predict_rows(net, samples, torch)
+    r = np.array([subspace_sines(p, s.U) for p, s in zip(pred, samples)])
+    return float(r[:, 0].mean()), float(r[:, 1].mean())
+
+
+def train_network(samples, torch, epochs: int = 40, batch_instances: int = 32, lr: float = 1e-3, lr_end: float = 1e-5,
+                  seed: int = 0, val=None, val_every: int = 10, log=None):
+    """Trains a fresh network on `samples` with the library's kernels (Adam with
+    a cosine learning-rate decay, minibatches of whole instances gathered on
+    the host).  Returns (net, per-epoch losses, validation history)."""
     dev = torch.device("cuda")
     X = np.stack([s.feats for s in samples])          # (n, NZ, IN_DIM)
     T = np.stack([s.coef for s in samples])           # (n, NZ, OUT_DIM)
-    scale = float(np.sqrt(np.mean(T ** 2)))
-    T = (T / scale).astype(np.float32)
     wd = torch.from_numpy(loss_weights()).to(dev)
     rows = batch_instances * NZ
     net = Mlp(IN_DIM, WIDTH, OUT_DIM, rows)
     for k, (W, b) in enumerate(init_params(seed)):
         net.feast_mlp_set_layer(k, W, b)
     rng = np.random.default_rng(seed + 1)
-    losses = []
+    losses, history = [], []
     n = len(samples)
+    steps_per_epoch = (n + batch_instances - 1) // batch_instances
+    total = epochs * steps_per_epoch
+    step = 0
     for ep in range(epochs):
         perm = rng.permutation(n)
         tot = 0.0
         for b0 in range(0, n, batch_instances):
-            idx = perm[b0:b0 + batch_instances]
+            idx = np.sort(perm[b0:b0 + batch_instances])
+            a = lr_end + 0.5 * (lr - lr_end) * (1.0 + np.cos(np.pi * step / total))
             xb = torch.from_numpy(np.ascontiguousarray(X[idx].reshape(-1, IN_DIM))).to(dev)
             tb = torch.from_numpy(np.ascontiguousarray(T[idx].reshape(-1, OUT_DIM))).to(dev)
-            tot += net.feast_mlp_train_step(xb, tb, wd, len(idx) * NZ, lr) * len(idx)
+            tot += net.feast_mlp_train_step(xb, tb, wd, len(idx) * NZ, a) * len(idx)
+            step += 1
         losses.append(tot / n)
+        msg = f"epoch {ep}: loss {losses[-1]:.4e}"
+        if val is not None and ((ep + 1) % val_every == 0 or ep == epochs - 1):
+            vmax, vmean = validate(net, val, torch)
+            history.append(dict(epoch=ep, loss=losses[-1], sin_max=vmax, sin_mean=vmean))
+            msg += f"  held-out sin(angle) max {vmax:.3e} mean {vmean:.3e}"
         if log:
-            log(f"epoch {ep}: loss {losses[-1]:.4e}")
-    return net, scale, losses
+            log(msg)
+    return net, losses, history
 
 
-def solve(h: Handle, op_dev, lmin, lmax, Y0, lam, X, torch):
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "learned_start_24x24x100.npz")
+
+
+def save_weights(net: Mlp, path: str):
+    """The four layers as an .npz: W_k as bfloat16 bit patterns (uint16, the
+    values the forward kernels read), b_k in fp32."""
+    sizes = [IN_DIM, WIDTH, WIDTH, WIDTH, OUT_DIM]
+    arrs = {}
+    for k in range(4):
+        W = np.zeros((sizes[k + 1], sizes[k]), dtype=np.float32)
+        b = np.zeros(sizes[k + 1], dtype=np.float32)
+        net.feast_mlp_get_layer(k, W=W, b=b)
+        u = W.view(np.uint32).astype(np.uint64)
+        arrs[f"W{k}"] = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)   # nearest even
+        arrs[f"b{k}"] = b
+    np.savez_compressed(path, **arrs)
+
+
+def load_weights(path: str = WEIGHTS, max_batch: int = NZ) -> Mlp:
+    z = np.load(path)
+    net = Mlp(IN_DIM, WIDTH, OUT_DIM, max_batch)
+    for k in range(4):
+        W = z[f"W{k}"]
+        if W.dtype == np.uint16:
+            W = (W.astype(np.uint32) << 16).view(np.float32)
+        net.feast_mlp_set_layer(k, np.ascontiguousarray(W, dtype=np.float32), np.ascontiguousarray(z[f"b{k}"]))
+    return net
+
+
+def solve(h: Handle, op_dev, lmin, lmax, Y0, lam, X, torch, tol=TOL):
     """FEAST from start block Y0 (None = random); returns (result, seconds)."""
     torch.cuda.synchronize()
     t = time.perf_counter()
-    r = h.feast_solve(op_dev, lmin, lmax, M0, NE, TOL, Y0, lam, X)
+    r = h.feast_solve(op_dev, lmin, lmax, M0, NE, tol, Y0, lam, X)
     torch.cuda.synchronize()
     return r, time.perf_counter() - t
 
 
-def learned_solve(h: Handle, net: Mlp, seed: int, op_dev, lmin, lmax, lam, X, torch):
+def learned_solve(h: Handle, net: Mlp, seed: int, op_dev, lmin, lmax, lam, X, torch, tol=TOL):
     """FEAST from the network's start block, falling back to the random start
-    when that block is unusable (FEAST rejects a degenerate or non-finite start
-    through B_Q, the Jacobi sweeps or a pivot).  Returns (result, seconds, used_learned)."""
+    when FEAST rejects that block.  Returns (result, seconds, fallback status
+    or FEAST_OK when the learned block was used)."""
     dev = torch.device("cuda")
     torch.cuda.synchronize()
     t = time.perf_counter()
-    Y = torch.zeros((M0, NX * NY * NZ), dtype=torch.float64, device=dev)
-    net.feast_predict_Y(torch.from_numpy(features(seed, lmin, lmax)).to(dev), NX, NY, NZ, M0, PX, PY, Y)
-    used = True
+    Y = torch.empty((M0, NX * NY * NZ), dtype=torch.float64, device=dev)
+    used = FEAST_OK
     try:
-        r = h.feast_solve(op_dev, lmin, lmax, M0, NE, TOL, Y, lam, X)
+        net.feast_predict_Y(torch.from_numpy(features(seed, lmin, lmax)).to(dev), NX, NY, NZ, M0, PX, PY, Y)
+        r = h.feast_solve(op_dev, lmin, lmax, M0, NE, tol, Y, lam, X)
     except FeastError as ex:
-        if ex.status not in (FEAST_ERR_BQ_NOT_SPD, FEAST_ERR_JACOBI, FEAST_ERR_PIVOT):
+        if ex.status not in FALLBACK:
             raise
-        used = False
-        r = h.feast_solve(op_dev, lmin, lmax, M0, NE, TOL, None, lam, X)
+        used = ex.status
+        r = h.feast_solve(op_dev, lmin, lmax, M0, NE, tol, None, lam, X)
     torch.cuda.synchronize()
     return r, time.perf_counter() - t, used
+
+
+def evaluate(h: Handle, net: Mlp, samples, torch, tols=(1e-10, TOL)):
+    """Per held-out instance and stopping tolerance: loops, time and residual
+    of the random and the learned start, and whether both found the same
+    eigenvalues."""
+    dev = torch.device("cuda")
+    rows = []
+    for smp in samples:
+        op = operator(smp.seed)
+        A = torch.from_numpy(op.A27).to(dev)
+        B = torch.from_numpy(op.B27).to(dev)
+        dop = make_operator(NX, NY, NZ, A, B)
+        lam = torch.zeros(M0, dtype=torch.float64, device=dev)
+        X = torch.zeros((M0, op.N), dtype=torch.float64, device=dev)
+        solve(h, dop, smp.lmin, smp.lmax, None, lam, X, torch)          # warm caches and tuner
+        for tol in tols:
+            r0, t_rand = solve(h, dop, smp.lmin, smp.lmax, None, lam, X, torch, tol)
+            lam_rand = lam.cpu().numpy()[:r0.m_found].copy()
+            r1, t_learn, used = learned_solve(h, net, smp.seed, dop, smp.lmin, smp.lmax, lam, X, torch, tol)
+            lam_learn = lam.cpu().numpy()[:r1.m_found].copy()
+            same = r0.m_found == r1.m_found and np.abs(lam_rand - lam_learn).max() <= 1e-10 * np.abs(lam_rand).max()
+            rows.append(dict(seed=smp.seed, tol=tol, m=r1.m_found, loops_random=r0.loops, loops_learned=r1.loops,
+                             t_random=t_rand, t_learned=t_learn, resid_random=r0.info.resid_max,
+                             resid_learned=r1.info.resid_max, fallback_status=int(used),
+                             same_eigenvalues=bool(same)))
+    return rows
+
+
+def summarise(rows, tol):
+    r = [x for x in rows if x["tol"] == tol]
+    return dict(tol=tol, n=len(r),
+                mean_loops_random=float(np.mean([x["loops_random"] for x in r])),
+                mean_loops_learned=float(np.mean([x["loops_learned"] for x in r])),
+                mean_t_random=float(np.mean([x["t_random"] for x in r])),
+                mean_t_learned=float(np.mean([x["t_learned"] for x in r])),
+                all_same=all(x["same_eigenvalues"] for x in r),
+                max_resid_random=float(max(x["resid_random"] for x in r)),
+                max_resid_learned=float(max(x["resid_learned"] for x in r)),
+                fallbacks=sum(x["fallback_status"] != FEAST_OK for x in r))
 
 
 def main():
@@ -215,47 +369,40 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--eval", type=int, default=200)
-    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--epochs", default="40", help="comma-separated: one network per entry")
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--workers", type=int, default=6)
     ap.add_argument("--out", default="learned_results.json")
+    ap.add_argument("--weights", default=None)
     args = ap.parse_args()
     t0 = time.time()
     log = lambda m: print(f"[{time.time() - t0:7.1f}s] {m}", flush=True)  # noqa: E731
     train = generate(list(range(args.train)), torch, workers=args.workers, log=log)
-    t_gen = time.time() - t0
-    net, scale, losses = train_network(train, torch, epochs=args.epochs, log=log)
-    t_train = time.time() - t0 - t_gen
     evalset = generate(list(range(10000, 10000 + args.eval)), torch, workers=args.workers)
-    dev = torch.device("cuda")
+    t_gen = time.time() - t0
+    log(f"truncation sine: train max {max(s.trunc for s in train):.3e}, mean {np.mean([s.trunc for s in train]):.3e}")
+    best = None
+    runs = []
+    for ep in [int(e) for e in args.epochs.split(",")]:
+        t1 = time.time()
+        net, losses, history = train_network(train, torch, epochs=ep, batch_instances=args.batch, lr=args.lr,
+                                             val=evalset, log=log)
+        runs.append(dict(epochs=ep, first_loss=losses[0], final_loss=losses[-1], train_s=time.time() - t1,
+                         validation=history, losses=losses))
+        if best is None or history[-1]["sin_mean"] < best[1]:
+            best = (net, history[-1]["sin_mean"], ep)
+    net = best[0]
+    if args.weights:
+        save_weights(net, args.weights)
     h = Handle(precision=FEAST_PREC_MIXED)
-    rows = []
-    for smp in evalset:
-        op = operator(smp.seed)
-        A = torch.from_numpy(op.A27).to(dev)
-        B = torch.from_numpy(op.B27).to(dev)
-        dop = make_operator(NX, NY, NZ, A, B)
-        lam = torch.zeros(M0, dtype=torch.float64, device=dev)
-        X = torch.zeros((M0, op.N), dtype=torch.float64, device=dev)
-        solve(h, dop, smp.lmin, smp.lmax, None, lam, X, torch)          # warm caches and tuner
-        r0, t_rand = solve(h, dop, smp.lmin, smp.lmax, None, lam, X, torch)
-        lam_rand = lam.cpu().numpy()[:r0.m_found].copy()
-        r1, t_learn, used = learned_solve(h, net, smp.seed, dop, smp.lmin, smp.lmax, lam, X, torch)
-        lam_learn = lam.cpu().numpy()[:r1.m_found].copy()
-        same = r0.m_found == r1.m_found and np.abs(lam_rand - lam_learn).max() <= 1e-10 * np.abs(lam_rand).max()
-        rows.append(dict(seed=smp.seed, m=r1.m_found, loops_random=r0.loops, loops_learned=r1.loops,
-                         t_random=t_rand, t_learned=t_learn, resid_random=r0.info.resid_max,
-                         resid_learned=r1.info.resid_max, used_learned=used, same_eigenvalues=bool(same)))
-    summary = dict(train=len(train), eval=len(rows), epochs=args.epochs, final_loss=losses[-1],
-                   first_loss=losses[0], gen_s=t_gen, train_s=t_train,
-                   mean_loops_random=float(np.mean([r["loops_random"] for r in rows])),
-                   mean_loops_learned=float(np.mean([r["loops_learned"] for r in rows])),
-                   mean_t_random=float(np.mean([r["t_random"] for r in rows])),
-                   mean_t_learned=float(np.mean([r["t_learned"] for r in rows])),
-                   all_same=all(r["same_eigenvalues"] for r in rows),
-                   max_resid_learned=float(max(r["resid_learned"] for r in rows)),
-                   fallbacks=sum(not r["used_learned"] for r in rows))
+    rows = evaluate(h, net, evalset, torch)
+    summary = dict(train=len(train), eval=len(evalset), lr=args.lr, batch=args.batch, gen_s=t_gen, chosen_epochs=best[2],
+                   trunc_max=max(s.trunc for s in train + evalset),
+                   runs=[{k: v for k, v in r.items() if k != "losses"} for r in runs],
+                   by_tol=[summarise(rows, t) for t in sorted({x["tol"] for x in rows})])
     with open(args.out, "w") as f:
-        json.dump(dict(summary=summary, rows=rows, losses=losses), f, indent=1)
+        json.dump(dict(summary=summary, rows=rows, runs=runs), f, indent=1)
     print(json.dumps(summary))
 
 

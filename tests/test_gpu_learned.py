@@ -123,3 +123,38 @@ def test_sine_expand_and_project_match_reference():
     F().feast_sine_project(torch.from_numpy(np.ascontiguousarray(X.T)).cuda(), nx, ny, nz, M0, px, py, C)
     refc = mlp.project(X, nx, ny, nz, px, py)
     assert np.abs(C.cpu().numpy() - refc).max() <= 1e-4 * np.abs(refc).max()
+
+
+def test_trained_network_saves_a_loop_on_held_out_instances():
+    """The committed network (trained on 2000 converged instances of the
+    24x24x100 family) starts FEAST on held-out instances whose intervals the
+    oracle certified: same eigenvalues and residual gate as the random start,
+    one refinement loop fewer at trace tolerance 1e-10."""
+    import json
+    import os
+
+    import paper_0901_2665_gb300 as F
+    from paper_0901_2665_gb300 import learned as L
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "learned_intervals.json")) as f:
+        ivs = json.load(f)
+    assert ivs
+    net = L.load_weights()
+    h = F.Handle(precision=F.FEAST_PREC_MIXED)
+    for key in sorted(ivs):
+        iv = ivs[key]
+        op = L.operator(iv["seed"])
+        A = torch.from_numpy(op.A27).cuda()
+        B = torch.from_numpy(op.B27).cuda()
+        dop = F.make_operator(op.nx, op.ny, op.nz, A, B)
+        lam = torch.zeros(L.M0, dtype=torch.float64, device="cuda")
+        X = torch.zeros((L.M0, op.N), dtype=torch.float64, device="cuda")
+        r0, _ = L.solve(h, dop, iv["lmin"], iv["lmax"], None, lam, X, torch, tol=1e-10)
+        lam0 = lam.cpu().numpy()[:iv["M"]].copy()
+        r1, _, used = L.learned_solve(h, net, iv["seed"], dop, iv["lmin"], iv["lmax"], lam, X, torch, tol=1e-10)
+        lam1 = lam.cpu().numpy()[:iv["M"]]
+        assert used == F.FEAST_OK, key
+        assert r0.m_found == r1.m_found == iv["M"], key
+        assert np.abs(lam1 - lam0).max() <= 1e-10 * np.abs(lam0).max(), key
+        assert r0.info.resid_max <= 1e-10 and r1.info.resid_max <= 1e-10, key
+        assert r1.loops < r0.loops, (key, r0.loops, r1.loops)
