@@ -41,6 +41,16 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 FP32_LANES = 152 * 128                # FP32 lanes of a GB300 (152 SMs x 128)
 SM_MAX_MHZ = 2070.0
 FF_OPS_PER_ENTRY = 27 * 4 * 11        # fp32 instructions per complex entry of the double-float residual
+# DRAM bytes (read + write) per full-size launch from one ncu capture of the
+# current kernels (profiles/kernels_q1_32x32x24_mixed.md; the residual kernels
+# were captured on 24 of 400 layers and scaled by 400/24, their traffic being
+# proportional to the rows).  An entry is removed when its kernel changes.
+TRAFFIC = {
+    "sweep_gemm": 0.5 * ((71.36 + 8.93) + (76.17 + 77.24)) * 1e6,
+    "solve_gemm": 0.5 * ((83.91 + 1.92) + (83.91 + 2.01)) * 1e6,
+    "fp64_residual": (718.93 + 564.79) * 1e6 * 400 / 24,
+    "ff_residual": (663.74 + 549.21) * 1e6 * 400 / 24,
+}
 
 
 def roofline(name, ms, flops, launches, pk, pk_src):
@@ -62,7 +72,7 @@ def roofline(name, ms, flops, launches, pk, pk_src):
                 "peak_source": f"{pk_src} bf16 sustained x TF32/BF16 nominal ratio"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["flops_per_launch"] = flops / launches if launches else None
-    roof["traffic"] = None
+    roof["traffic"] = TRAFFIC.get(name)
     return roof
 
 
@@ -414,7 +424,9 @@ def run_ours(args):
             rc = roofline(nm, kms[c], kfl[c], kn[c], pk, pk_src)
             kernels[nm]["roofline_frac"] = round(rc["frac"], 4)
             kernels[nm]["bound"] = rc["bound"]
-    lu = kfl[0] / (kms[0] * 1e-3) / 1e12 if kms[0] > 0 else None
+    # block-LU rate: the factorisation's algorithmic flops (8 n^3 per layer
+    # per node: the complex block inverse) over its device time
+    lu = last.info.factor_flops / (last.info.t_factor_ms * 1e-3) / 1e12 if last.info.t_factor_ms > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
