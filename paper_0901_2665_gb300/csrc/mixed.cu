@@ -412,6 +412,172 @@ struct SweepEpi {
   }
 };
 
+// The same trailing update with the read-modify-write of S staged through
+// shared memory by TMA (used when n is a multiple of 64, so that a tile's 64
+// complex columns never straddle the real/imaginary split of a row).  The
+// epilogue threads load the CTA's S tile -- four 128-row x 32-column boxes:
+// real parts of columns tn*64.. and imaginary parts n + tn*64.. -- at kernel
+// start, so the load overlaps the main loop; each thread then updates its row
+// in shared memory (128-byte swizzle: chunk c of row r sits at c ^ (r & 7)) and
+// one thread stores the tile back with TMA (and, after the last panel, the
+// TF32-rounded copy).  The 3-D maps (row, layer plane) clip every box at the
+// layer's n rows.
+struct SweepEpiTma {
+  static constexpr size_t kTileBytes = 4 * 16384;
+  static constexpr size_t kExtraSmem = kTileBytes + 64;
+  CUtensorMap mapF;    // fp32 working layers: inner 2n, rows n, planes Ne*2
+  CUtensorMap mapFr;   // TF32 solve copy: inner 2n, rows n, planes Ne*nz
+  int plane;           // layer & 1
+  int layer, nz;
+  int n, k0, bw;
+  int last;            // last panel: also store the TF32 copy
+  const f2* Tc;
+  const f2* Pinv;
+  __device__ int box_x(int b, int tn) const { return (b >> 1) * n + tn * 64 + (b & 1) * 32; }
+  __device__ void prologue(int e, int tm, int tn, int ept, uint8_t* extra, int*, volatile int*) const {
+    if (ept != 0) return;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(extra + kTileBytes);
+    tc::mbar_init(bar, 1);
+    tc::fence_barrier_init();
+    tc::mbar_arrive_expect_tx(bar, (uint32_t)kTileBytes);
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      tc::tma_load_3d(extra + b * 16384, &mapF, bar, box_x(b, tn), tm * tc::kBlockM, e * 2 + plane);
+  }
+  __device__ void run(int e, int tm, int tn, int row, uint32_t taddr, int ept, uint8_t* stage, uint8_t* extra,
+                      int* status, volatile int* abort_flag) const {
+    uint64_t* bar = reinterpret_cast<uint64_t*>(extra + kTileBytes);
+    // bounded wait for the tile, even when the main loop gave up, so that no
+    // copy into shared memory is in flight when the CTA exits
+    bool ok = false;
+    for (long long it = 0; it < tc::kWaitLimit && !ok; ++it) ok = tc::mbar_try_wait(bar, 0);
+    if (!ok) {
+      *abort_flag = 1;
+      atomicExch(status, (int)DEV_TIMEOUT);
+    }
+    tc::epilogue_sync();
+    if (*abort_flag) return;   // uniform: read after the barrier
+    const f2* T = Tc + (long long)e * n * kPanel;
+    const f2* Pi = Pinv + (long long)e * kPanel * kPanel;
+    const int i = tm * tc::kBlockM + row;
+    const bool iok = i < n;
+    const bool inI = i >= k0 && i < k0 + bw;
+    const int sw = row & 7;
+    const bool strip = tn * 64 == k0;   // the panel's own columns: every entry is T or -Pinv
+    const bool rowsK = tm * tc::kBlockM < k0 + bw && k0 < tm * tc::kBlockM + tc::kBlockM;
+    if (strip) {
+      // row i: T[i, :] (or -Pinv[i - k0, :] on the pivot rows), 16 columns at a time
+#pragma unroll 1
+      for (int c0 = 0; c0 < 64; c0 += 16) {
+        f2 val[16];
+        if (iok) {
+          const float4* src = reinterpret_cast<const float4*>(inI ? Pi + (long long)(i - k0) * kPanel + c0
+                                                                  : T + (long long)i * kPanel + c0);
+          float4 q[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) q[u] = src[u];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            val[2 * u] = f2{q[u].x, q[u].y};
+            val[2 * u + 1] = f2{q[u].z, q[u].w};
+          }
+          if (inI)
+#pragma unroll
+            for (int t = 0; t < 16; ++t) val[t] = f2{-val[t].x, -val[t].y};
+        } else {
+#pragma unroll
+          for (int t = 0; t < 16; ++t) val[t] = f2{0.f, 0.f};
+        }
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          float4* rowp = reinterpret_cast<float4*>(extra + (half * 2 + (c0 >> 5)) * 16384 + row * 128);
+          const int q0 = (c0 & 31) >> 2;
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            float4 x;
+            x.x = half ? val[qq * 4].y : val[qq * 4].x;
+            x.y = half ? val[qq * 4 + 1].y : val[qq * 4 + 1].x;
+            x.z = half ? val[qq * 4 + 2].y : val[qq * 4 + 2].x;
+            x.w = half ? val[qq * 4 + 3].y : val[qq * 4 + 3].x;
+            rowp[(q0 + qq) ^ sw] = x;
+          }
+        }
+      }
+    } else {
+      // pivot rows of this tile: S[i, j] = T[j, i - k0], staged in shared
+      // memory (the free pipeline stage) with coalesced loads
+      f2* Ts = reinterpret_cast<f2*>(stage);   // [64 columns j][64]
+      if (rowsK) {
+        const float4* src = reinterpret_cast<const float4*>(T + (long long)tn * 64 * kPanel);
+        float4* dstp = reinterpret_cast<float4*>(Ts);
+        const int rows_avail = min(64, n - tn * 64);
+        for (int t = ept; t < 64 * kPanel / 2; t += 128)
+          dstp[t] = (t / (kPanel / 2) < rows_avail) ? src[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        tc::epilogue_sync();
+      }
+#pragma unroll 1
+      for (int half = 0; half < 2; ++half) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+          float v[16];
+          tc::tmem_ld16(taddr + half * 64 + c0, v);
+          float4* rowp = reinterpret_cast<float4*>(extra + (half * 2 + (c0 >> 5)) * 16384 + row * 128);
+          const int q0 = (c0 & 31) >> 2;
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            float4 cur = rowp[(q0 + qq) ^ sw];
+            float* cv = reinterpret_cast<float*>(&cur);
+#pragma unroll
+            for (int t4 = 0; t4 < 4; ++t4) {
+              const int t = qq * 4 + t4;
+              if (inI) {
+                const f2 t2 = Ts[(c0 + t) * kPanel + (i - k0)];
+                cv[t4] = half ? t2.y : t2.x;
+              } else {
+                cv[t4] -= v[t];
+              }
+            }
+            rowp[(q0 + qq) ^ sw] = cur;
+          }
+        }
+      }
+    }
+    tc::fence_proxy_async_smem();
+    tc::epilogue_sync();
+    if (ept == 0) {
+#pragma unroll
+      for (int b = 0; b < 4; ++b) tc::tma_store_3d(&mapF, extra + b * 16384, box_x(b, tn), tm * tc::kBlockM, e * 2 + plane);
+      tc::bulk_commit();
+      tc::bulk_wait_read();
+    }
+    if (last) {
+      tc::epilogue_sync();   // the working-copy stores have read the tile
+#pragma unroll 1
+      for (int b = 0; b < 4; ++b) {
+        float4* rowp = reinterpret_cast<float4*>(extra + b * 16384 + row * 128);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          float4 x = rowp[c];
+          x.x = tc::to_tf32(x.x);
+          x.y = tc::to_tf32(x.y);
+          x.z = tc::to_tf32(x.z);
+          x.w = tc::to_tf32(x.w);
+          rowp[c] = x;
+        }
+      }
+      tc::fence_proxy_async_smem();
+      tc::epilogue_sync();
+      if (ept == 0) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          tc::tma_store_3d(&mapFr, extra + b * 16384, box_x(b, tn), tm * tc::kBlockM, e * nz + layer);
+        tc::bulk_commit();
+      }
+    }
+    if (ept == 0) tc::bulk_wait();
+  }
+};
+
 // Solve product: out[m*ldo + p] = alpha * (S' g)[p, m] (complex64); lanes are
 // consecutive rows p, so the stores of a warp are contiguous.
 template <int CB>
@@ -761,7 +927,7 @@ bool make_map(CUtensorMap* map, const float* base, long long inner, long long ro
 template <int BN, int STAGES, class Epi>
 cudaError_t launch_tc(cudaStream_t s, dim3 grid, const CUtensorMap& a, const CUtensorMap& b, tc::Geom geo,
                       const Epi& epi, int* status) {
-  constexpr size_t smem = tc::Smem<BN, STAGES>::kBytes;
+  constexpr size_t smem = tc::smem_bytes<BN, STAGES, Epi>();
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
@@ -893,16 +1059,33 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
     prof::end(st, prof::PANEL_T);
     prof::count_launch(2);
   };
+  // TMA-staged read-modify-write of S when a 64-column tile never straddles
+  // the real/imaginary split of a row
+  const bool tma_rmw = d.n % 64 == 0;
+  CUtensorMap mapF{}, mapFr{};
+  if (tma_rmw) {
+    if (!make_map_3d(&mapF, F, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 2LL * d.n, d.n, 2LL * Ne, d.ldF,
+                     (long long)d.n * d.ldF, 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !make_map_3d(&mapFr, Fr, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 2LL * d.n, d.n, (long long)Ne * d.nz, d.ldF,
+                     (long long)d.n * d.ldF, 32, 128, CU_TENSOR_MAP_SWIZZLE_128B))
+      return "tensor map (working layers) rejected";
+  }
   // trailing update of panel kp over the column tiles [base, base + count) except `skip`
   auto update = [&](int layer, int kp, int base, int count, int skip) -> cudaError_t {
     const int k0 = kp * kPanel, bw = std::min(kPanel, d.n - k0), q = kp & 1;
     const bool last = kp == npan - 1;
-    SweepEpi epi{F + (long long)(layer & 1) * d.n * d.ldF, sF, last ? Fr + (long long)layer * d.n * d.ldF : nullptr,
-                 sFr, d.ldF, d.n, k0, bw, Tc[q], Pv[q]};
     tc::Geom geo{0, d.n, 0, d.nblk64 * 128, (2 * kPanel) / tc::kBlockK, base, skip};
     prof::begin(s, prof::SWEEP_GEMM);
     prof::add_work(prof::SWEEP_GEMM, 8.0 * d.n * (64.0 * count) * bw * Ne);
-    cudaError_t err = launch_tc<128, 2>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status);
+    cudaError_t err;
+    if (tma_rmw) {
+      SweepEpiTma epi{mapF, mapFr, layer & 1, layer, d.nz, d.n, k0, bw, last ? 1 : 0, Tc[q], Pv[q]};
+      err = launch_tc<128, 1>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status);
+    } else {
+      SweepEpi epi{F + (long long)(layer & 1) * d.n * d.ldF, sF, last ? Fr + (long long)layer * d.n * d.ldF : nullptr,
+                   sFr, d.ldF, d.n, k0, bw, Tc[q], Pv[q]};
+      err = launch_tc<128, 2>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status);
+    }
     prof::end(s, prof::SWEEP_GEMM);
     prof::count_launch();
     return err;

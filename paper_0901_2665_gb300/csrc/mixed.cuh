@@ -13,8 +13,8 @@ struct MixedSolveStats {
 };
 
 struct MixedWork {
-  void* bufs[16] = {};
-  size_t sizes[16] = {};
+  void* bufs[20] = {};
+  size_t sizes[20] = {};
   int nz_factored = 0, ne_factored = 0;   // shape of the factors held
   int bemb_k = 0;                         // right-hand sides the RHS operand was zeroed for
   cudaStream_t side = nullptr;            // lookahead stream of the factorisation

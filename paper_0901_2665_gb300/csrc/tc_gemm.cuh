@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace feast {
@@ -72,6 +74,32 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
           smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
+}
+
+// 3-D tiled TMA load / store (coordinates innermost first).  A store reads
+// shared memory through the async proxy: the writing threads fence first.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int x, int y, int z) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// waits until the committed stores have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// waits until the committed stores are complete
+__device__ __forceinline__ void bulk_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
@@ -180,6 +208,27 @@ struct Smem {
   static constexpr size_t kBytes = 1024 /*align slack*/ + kPipeBytes + 256;
 };
 
+// Epilogues may ask for shared memory of their own (static constexpr size_t
+// kExtraSmem, 1024-byte aligned, after the pipeline).  They then provide a
+// prologue, epi.prologue(e, tm, tn, ept, extra, status, abort_flag), that the
+// epilogue threads run at kernel start while the main loop is under way, and
+// take the accumulator through epi.run(e, tm, tn, row, lane_taddr, ept, stage,
+// extra, status, abort_flag) instead of operator() (stage: the pipeline
+// shared memory, free once the accumulator is complete).
+template <class E, class = void>
+struct EpiExtra {
+  static constexpr size_t kBytes = 0;
+};
+template <class E>
+struct EpiExtra<E, std::void_t<decltype(E::kExtraSmem)>> {
+  static constexpr size_t kBytes = E::kExtraSmem;
+};
+
+template <int BN, int STAGES, class Epi>
+constexpr size_t smem_bytes() {
+  return Smem<BN, STAGES>::kBytes + (EpiExtra<Epi>::kBytes ? 1024 + EpiExtra<Epi>::kBytes : 0);
+}
+
 // Named barrier of the 128 epilogue threads (warps 2-5).
 __device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
@@ -193,8 +242,8 @@ __device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 1, 128;
 // 64 bf16 elements; geo.nk counts K-blocks.
 template <int BN, int STAGES, class Epi, int KIND = 0>
 __global__ void __launch_bounds__(kThreads)
-    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Geom geo, Epi epi,
-              int* status) {
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Geom geo,
+              const __grid_constant__ Epi epi, int* status) {
   using S = Smem<BN, STAGES>;
   constexpr int kStages = STAGES;
   extern __shared__ uint8_t smem_raw[];
@@ -276,13 +325,21 @@ __global__ void __launch_bounds__(kThreads)
   } else {
     const int q = warp % 4;
     const int row = q * 32 + lane;
+    if constexpr (EpiExtra<Epi>::kBytes > 0)
+      epi.prologue(e, tm, tn, static_cast<int>(threadIdx.x) - 64, smem + S::kPipeBytes + 1024, status, abort_flag);
     mbar_wait(tfull, 0, status, abort_flag);
     tc_fence_after();
     // one decision for the whole epilogue group: a thread that gave up set
     // the flag before this barrier, so all 128 threads read the same value
     epilogue_sync();
-    if (!*abort_flag)
+    if constexpr (EpiExtra<Epi>::kBytes > 0) {
+      // run() also waits (bounded) for the prologue's copies and checks the
+      // abort flag itself, so that no copy is left in flight on abort
+      epi.run(e, tm, tn, row, tmem + (static_cast<uint32_t>(q * 32) << 16), static_cast<int>(threadIdx.x) - 64,
+              smem, smem + S::kPipeBytes + 1024, status, abort_flag);
+    } else if (!*abort_flag) {
       epi(e, tm, tn, row, tmem + (static_cast<uint32_t>(q * 32) << 16), static_cast<int>(threadIdx.x) - 64, smem);
+    }
   }
   tc_fence_before();
   __syncthreads();

@@ -43,4 +43,22 @@ inline bool make_map_2d(CUtensorMap* map, const void* base, CUtensorMapDataType 
   return r == CUDA_SUCCESS;
 }
 
+// 3-D map over planes of rows: `inner` elements per row (row stride ld_row
+// elements), `rows` rows per plane (plane stride ld_plane elements), `planes`
+// planes; box = box_inner x box_rows x 1; loads past the edges read zeros and
+// stores there are dropped, so a box never spills into the next plane.
+inline bool make_map_3d(CUtensorMap* map, const void* base, CUtensorMapDataType dtype, int elem_bytes,
+                        long long inner, long long rows, long long planes, long long ld_row, long long ld_plane,
+                        int box_inner, int box_rows, CUtensorMapSwizzle swizzle) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)ld_row * elem_bytes, (cuuint64_t)ld_plane * elem_bytes};
+  cuuint32_t box[3] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows, 1u};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  CUresult r = fn(map, dtype, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 }  // namespace feast

@@ -26,7 +26,12 @@ def F():
     return mod
 
 
-@pytest.mark.parametrize("nx,ny,nz,G,seed", GRIDS)
+# cross sections with n a multiple of 64 take the TMA-staged sweep update:
+# 16x12 (n = 192: three panels, a ragged second row tile), 16x16 (n = 256)
+GRIDS_TMA = [(16, 12, 7, 4, 5), (16, 16, 5, 4, 6)]
+
+
+@pytest.mark.parametrize("nx,ny,nz,G,seed", GRIDS + GRIDS_TMA)
 @pytest.mark.parametrize("k", [5, 24])
 def test_node_solve_mixed_matches_oracle(nx, ny, nz, G, seed, k):
     op = workloads.q1_operator(nx, ny, nz, workloads.gaussian_potential(G, seed, nx, ny, nz))
