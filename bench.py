@@ -46,7 +46,6 @@ FF_OPS_PER_ENTRY = 27 * 4 * 11        # fp32 instructions per complex entry of t
 # were captured on 24 of 400 layers and scaled by 400/24, their traffic being
 # proportional to the rows).  An entry is removed when its kernel changes.
 TRAFFIC = {
-    "sweep_gemm": 0.5 * ((71.36 + 8.93) + (76.17 + 77.24)) * 1e6,
     "solve_gemm": 0.5 * ((83.91 + 1.92) + (83.91 + 2.01)) * 1e6,
     "fp64_residual": (718.93 + 564.79) * 1e6 * 400 / 24,
     "ff_residual": (663.74 + 549.21) * 1e6 * 400 / 24,
