@@ -42,11 +42,11 @@ FP32_LANES = 152 * 128                # FP32 lanes of a GB300 (152 SMs x 128)
 SM_MAX_MHZ = 2070.0
 FF_OPS_PER_ENTRY = 27 * 4 * 11        # fp32 instructions per complex entry of the double-float residual
 # DRAM bytes (read + write) per full-size launch from one ncu capture of the
-# current kernels (profiles/kernels_q1_32x32x24_mixed.md; the residual kernels
+# current kernels (profiles/kernels_*_q1_32x32x24_mixed.md; the residual kernels
 # were captured on 24 of 400 layers and scaled by 400/24, their traffic being
 # proportional to the rows).  An entry is removed when its kernel changes.
 TRAFFIC = {
-    "solve_gemm": 0.5 * ((83.91 + 1.92) + (83.91 + 2.01)) * 1e6,
+    "solve_gemm": 0.5 * ((83.91 + 2.27) + (83.91 + 1.97)) * 1e6,
     "fp64_residual": (718.93 + 564.79) * 1e6 * 400 / 24,
     "ff_residual": (663.74 + 549.21) * 1e6 * 400 / 24,
 }
@@ -82,8 +82,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="single", choices=["single", "batched64"],
-                    help="single: the 32x32x400 pencil; batched64: 64 uneven instances in one batched call")
+    ap.add_argument("--workload", default="single", choices=["single", "batched64", "ne_sweep", "warm_sequence"],
+                    help="single: the 32x32x400 pencil; batched64: 64 uneven instances in one batched call; "
+                         "ne_sweep: contour node counts 4/8/16 (Table III); warm_sequence: a potential changed in "
+                         "small steps, each solve started from the previous subspace (Sec. IV.C)")
     ap.add_argument("--skip-fp64", action="store_true", help="do not time the plain FP64 GPU path")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--profile-timed", action="store_true",
@@ -449,6 +451,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (27 GB of factors per solve)"},
         "valid": valid, "m_found": last.m_found, "loops": last.loops, "resid_max": last.info.resid_max,
         "ir_steps_max": last.info.ir_steps_max,
+        "trace_rel_change": [float(x) for x in last.info.rel_change[:last.loops]],
         "phase_ms": {"factor": last.info.t_factor_ms, "solve": last.info.t_solve_ms, "rayleigh_ritz": last.info.t_rr_ms},
         "block_lu_tflops": lu, "block_lu_frac_tf32": (lu / tf32_peak) if lu else None,
         "roofline": roof, "kernels": kernels, "gpu_launches": int(launches), "clocks": clk,
@@ -582,6 +585,126 @@ def run_batched(args):
     }
 
 
+def _single_setup(dev, torch, F, workloads, seed=0, potential=None):
+    wl = workloads.WORKLOADS[WORKLOAD]
+    pot = potential if potential is not None else workloads.gaussian_potential(wl.gaussians, seed, wl.nx, wl.ny, wl.nz)
+    op = workloads.q1_operator(wl.nx, wl.ny, wl.nz, pot)
+    A = torch.from_numpy(op.A27).to(dev)
+    B = torch.from_numpy(op.B27).to(dev)
+    return wl, op, F.make_operator(op.nx, op.ny, op.nz, A, B), (A, B)
+
+
+def run_ne_sweep(args):
+    """Table III on the 32x32x400 workload: loops, time and residual of the
+    mixed path for Ne = 4, 8, 16 contour nodes (same interval, same start)."""
+    import torch
+
+    import paper_0901_2665_gb300 as F
+    import workloads
+
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl, op, dop, keep = _single_setup(dev, torch, F, workloads)
+    iv = load_interval()
+    stream = torch.cuda.current_stream()
+    lam = torch.zeros(wl.M0, dtype=torch.float64, device=dev)
+    X = torch.zeros((wl.M0, op.N), dtype=torch.float64, device=dev)
+    h = F.Handle(precision=F.FEAST_PREC_MIXED, seed=Y_SEED, stream=stream.cuda_stream)
+    rows = []
+    clocks = ClockSampler(gpu_uuid())
+    clocks.start()
+    for Ne in (4, 8, 16):
+        for _ in range(args.warmup):
+            h.feast_solve(dop, iv["lmin"], iv["lmax"], wl.M0, Ne, wl.tol, None, lam, X, allow=())
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        rs = [h.feast_solve(dop, iv["lmin"], iv["lmax"], wl.M0, Ne, wl.tol, None, lam, X, allow=())
+              for _ in range(args.steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        r = rs[-1]
+        ok = all(x.m_found == iv["M"] and x.info.resid_max <= 1e-10 for x in rs)
+        rows.append({"Ne": Ne, "loops": r.loops, "ms_per_solve": ms, "m_found": r.m_found,
+                     "resid_max": r.info.resid_max, "valid": ok,
+                     "eigenpairs_per_s": r.m_found / (ms * 1e-3) if ok else 0.0,
+                     "trace_rel_change": [float(x) for x in r.info.rel_change[:r.loops]]})
+    clk = clocks.stop()
+    h.close()
+    best = max(rows, key=lambda x: x["eigenpairs_per_s"])
+    return {"metric": METRIC, "value": next(x for x in rows if x["Ne"] == 8)["eigenpairs_per_s"], "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": next(x for x in rows if x["Ne"] == 8)["ms_per_solve"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "tf32+f64", "data": "synthetic",
+            "config": {"workload": "Q1 FE 32x32x400, lowest 100 eigenpairs, M0=128, tol 1e-12, mixed; "
+                                   "contour nodes Ne = 4, 8, 16", "form": "node-count sweep (Table III)"},
+            "by_ne": rows, "best_ne": best["Ne"], "clocks": clk}
+
+
+def run_warm_sequence(args):
+    """Sec. IV.C on the 32x32x400 workload: the potential's amplitudes scaled
+    by 1 + 0.01 t, t = 0..steps; each solve started from the previous Ritz
+    vectors against a random start (mixed path, same interval)."""
+    import dataclasses
+
+    import torch
+
+    import paper_0901_2665_gb300 as F
+    import workloads
+
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = workloads.WORKLOADS[WORKLOAD]
+    base = workloads.gaussian_potential(wl.gaussians, 0, wl.nx, wl.ny, wl.nz)
+    iv = load_interval()
+    stream = torch.cuda.current_stream()
+    lam = torch.zeros(wl.M0, dtype=torch.float64, device=dev)
+    X = torch.zeros((wl.M0, wl.N), dtype=torch.float64, device=dev)
+    Xprev = None
+    h = F.Handle(precision=F.FEAST_PREC_MIXED, seed=Y_SEED, stream=stream.cuda_stream)
+    rows = []
+    clocks = ClockSampler(gpu_uuid())
+    clocks.start()
+
+    def timed(dop, Y0):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        r = h.feast_solve(dop, iv["lmin"], iv["lmax"], wl.M0, wl.Ne, wl.tol, Y0, lam, X, allow=())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return r, ev0.elapsed_time(ev1)
+
+    _, op0, dop0, keep0 = _single_setup(dev, torch, F, workloads)
+    for _ in range(args.warmup):
+        timed(dop0, None)
+    for t in range(max(2, args.steps + 1)):
+        pot = dataclasses.replace(base, amps=base.amps * (1.0 + 0.01 * t))
+        _, op, dop, keep = _single_setup(dev, torch, F, workloads, potential=pot)
+        r_rand, ms_rand = timed(dop, None)
+        row = {"step": t, "amplitude_scale": 1.0 + 0.01 * t, "m_found": r_rand.m_found, "loops_random": r_rand.loops,
+               "ms_random": ms_rand, "resid_random": r_rand.info.resid_max}
+        if Xprev is not None:
+            r_warm, ms_warm = timed(dop, Xprev)
+            row.update({"loops_warm": r_warm.loops, "ms_warm": ms_warm, "resid_warm": r_warm.info.resid_max,
+                        "m_found_warm": r_warm.m_found})
+        rows.append(row)
+        Xprev = X.clone()
+    clk = clocks.stop()
+    h.close()
+    warm = [x for x in rows if "ms_warm" in x]
+    ms_w = sum(x["ms_warm"] for x in warm) / len(warm)
+    found = sum(x["m_found_warm"] for x in warm) / len(warm)
+    ok = all(x["resid_warm"] <= 1e-10 for x in warm)
+    return {"metric": METRIC, "value": found / (ms_w * 1e-3) if ok else 0.0, "unit": UNIT, "n_gpus": world,
+            "steps": len(warm), "warmup": args.warmup, "ms_per_step": ms_w, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "tf32+f64", "data": "synthetic",
+            "config": {"workload": "Q1 FE 32x32x400, potential amplitudes scaled by 1 + 0.01 t, interval of t = 0, "
+                                   "M0=128, Ne=8, tol 1e-12, mixed", "form": "warm-started sequence (Sec. IV.C)"},
+            "random_start_ms": sum(x["ms_random"] for x in warm) / len(warm), "sequence": rows, "clocks": clk}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -617,6 +740,10 @@ def main():
         line = run_reference(args)
     elif args.workload == "batched64":
         line = run_batched(args)
+    elif args.workload == "ne_sweep":
+        line = run_ne_sweep(args)
+    elif args.workload == "warm_sequence":
+        line = run_warm_sequence(args)
     else:
         line = run_ours(args)
     if line is not None:

@@ -1,0 +1,105 @@
+"""The experiments of the paper beyond the single solve, on the GPU path:
+
+- other contour node counts (Table III: Ne = 4 and 16 beside 8), against the
+  oracle run with the same Ne;
+- the k(N, M) replica construction of Sec. IV.B: k uncoupled copies make every
+  eigenvalue exactly k-fold and FEAST finds k M pairs;
+- a sequence of close problems (Sec. IV.C, Fig. 3): a potential changed in
+  small steps, each solve started from the previous subspace, needs fewer
+  refinement loops than a random start and finds the same eigenpairs.
+"""
+
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from test_gpu_parity import back, cm, dev_op
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def F():
+    import paper_0901_2665_gb300 as mod
+    return mod
+
+
+def _prec(name):
+    return F().FEAST_PREC_MIXED if name == "mixed" else F().FEAST_PREC_FP64
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("Ne", [4, 16])
+def test_node_count_sweep_matches_oracle(intervals, Ne, precision):
+    wl = workloads.WORKLOADS["q1_10x10x20_fp64"]
+    op = wl.operator(3)
+    iv = intervals["q1_10x10x20/seed3"]
+    Y = workloads.random_Y(op.N, wl.M0, 1003)
+    ref = oracle.feast(op, iv["lmin"], iv["lmax"], wl.M0, Ne, Y, tol=wl.tol)
+    dop, keep = dev_op(op)
+    lam = torch.zeros(wl.M0, dtype=torch.float64, device="cuda")
+    X = torch.zeros((wl.M0, op.N), dtype=torch.float64, device="cuda")
+    h = F().Handle(precision=_prec(precision))
+    r = h.feast_solve(dop, iv["lmin"], iv["lmax"], wl.M0, Ne, wl.tol, cm(Y), lam, X, None, allow=())
+    M = iv["M"]
+    assert r.m_found == ref.m_found == M
+    got = lam.cpu().numpy()[:M]
+    assert np.abs(got - ref.lam[:M]).max() <= 1e-10 * np.abs(ref.lam[:M]).max()
+    assert abs(r.loops - ref.loops) <= 1
+    assert r.info.resid_max <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_k_copies_give_k_fold_eigenvalues(precision):
+    # 8x8 cross section: n = 64 also takes the TMA-staged sweep update
+    blk = workloads.q1_operator(8, 8, 6, workloads.gaussian_potential(4, 21, 8, 8, 6))
+    lam1 = oracle.dense_generalized_eigh(blk)[0]
+    M, k = 8, 3
+    lmin, lmax = lam1[0] - 0.5 * (lam1[M] - lam1[M - 1]), 0.5 * (lam1[M - 1] + lam1[M])
+    rep = workloads.replicate_z(blk, k)
+    M0 = 40
+    dop, keep = dev_op(rep)
+    lam = torch.zeros(M0, dtype=torch.float64, device="cuda")
+    X = torch.zeros((M0, rep.N), dtype=torch.float64, device="cuda")
+    h = F().Handle(precision=_prec(precision))
+    r = h.feast_solve(dop, lmin, lmax, M0, 8, 1e-12, None, lam, X, None, allow=())
+    assert r.m_found == k * M
+    got = np.sort(lam.cpu().numpy()[:k * M]).reshape(M, k)
+    assert np.abs(got - lam1[:M, None]).max() <= 1e-10 * lam1[M - 1]
+    assert r.info.resid_max <= 1e-10
+    # the k copies of each eigenvector span the k decoupled slabs: B-orthonormal
+    B = oracle.assemble(rep.B27, rep.nx, rep.ny, rep.nz)
+    Xg = back(X)[:, :k * M]
+    assert np.abs(Xg.T @ (B @ Xg) - np.eye(k * M)).max() <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_warm_started_sequence_of_close_problems(intervals, precision):
+    wl = workloads.WORKLOADS["q1_10x10x20_fp64"]
+    base = workloads.gaussian_potential(wl.gaussians, 0, wl.nx, wl.ny, wl.nz)
+    iv = intervals["q1_10x10x20/seed0"]
+    M, M0 = iv["M"], wl.M0
+    h = F().Handle(precision=_prec(precision))
+    lam = torch.zeros(M0, dtype=torch.float64, device="cuda")
+    X = torch.zeros((M0, wl.N), dtype=torch.float64, device="cuda")
+    Xprev = None
+    for t in range(4):
+        pot = dataclasses.replace(base, amps=base.amps * (1.0 + 0.002 * t))
+        op = workloads.q1_operator(wl.nx, wl.ny, wl.nz, pot)
+        ref = np.sort(oracle.dense_generalized_eigh(op)[0])
+        inside = ref[(ref >= iv["lmin"]) & (ref <= iv["lmax"])]
+        dop, keep = dev_op(op)
+        r_rand = h.feast_solve(dop, iv["lmin"], iv["lmax"], M0, wl.Ne, wl.tol, None, lam, X, None, allow=())
+        if Xprev is not None:
+            r = h.feast_solve(dop, iv["lmin"], iv["lmax"], M0, wl.Ne, wl.tol, Xprev, lam, X, None, allow=())
+            assert r.loops < r_rand.loops, (t, r.loops, r_rand.loops)
+        else:
+            r = r_rand
+        assert r.m_found == len(inside) == M
+        assert np.abs(lam.cpu().numpy()[:M] - inside).max() <= 1e-10 * np.abs(inside).max()
+        assert r.info.resid_max <= 1e-10
+        Xprev = X.clone()
