@@ -1,5 +1,7 @@
 // Rayleigh-Ritz in FP64 (Fig. 2 steps 3-5; Eqs. 6-9) and the residuals of
 // Table I.
+#include <cooperative_groups.h>
+
 #include <mutex>
 
 #include "kernels.cuh"
@@ -328,6 +330,331 @@ __global__ void __launch_bounds__(1024) k_reduced_eig(int m, const double* __res
   }
 }
 
+// ---------------------------------------------------------------- Jacobi on a cluster
+// The same two-stage eigensolve spread over a thread-block cluster of CL CTAs
+// (8 or 16), so that CL SMs share its FP64 work: CTA r owns the rows
+// i = r, r + CL, r + 2 CL, ... of the working matrix and of the accumulated
+// rotations.  The rotations, their order (round-robin pairs, m' - 1 steps a
+// sweep), the skip criteria and the sweep cap are those of jacobi_block.  One
+// step of the sweep:
+//   1. CTA r computes the rotations of the pairs k = r, r + CL, ... from the
+//      current matrix (a_pp, a_qq, a_pq read from their owners' shared
+//      memory) and stores (c, s) into the shared memory of every CTA;
+//      cluster barrier;
+//   2. every CTA copies the partner row of each of its rows, forms its rows
+//      of J^T A and then of (J^T A) J into the second buffer and applies the
+//      column rotations to its rows of V; cluster barrier; the buffers swap.
+namespace cg = cooperative_groups;
+
+constexpr int kClThreads = 256;
+constexpr int kClMinM = 32;   // smaller reduced problems stay on one CTA
+
+struct ClLayout {
+  int m, CL, R, ld, npairs;
+  __device__ ClLayout(int m_, int cl) : m(m_), CL(cl) {
+    R = (m + CL - 1) / CL;
+    ld = m + 1;
+    npairs = (m + (m & 1)) / 2;
+  }
+};
+
+// shared memory of one CTA (doubles first, then ints)
+__host__ __device__ inline size_t cl_smem_bytes(int m, int CL) {
+  const int R = (m + CL - 1) / CL;
+  const int np = (m + (m & 1)) / 2;
+  return sizeof(double) * (2 * (size_t)R * (m + 1) + 3 * (size_t)R * m + 2 * (size_t)np + 5 * (size_t)m + 8) +
+         sizeof(int) * (3 * (size_t)m + 8);
+}
+
+struct ClSmem {
+  double *A0, *A1, *X, *P, *V, *rc, *rs, *cj, *sj, *dg, *dsc, *aux, *red;
+  int *part, *isp, *rk, *flag;
+  __device__ ClSmem(double* base, const ClLayout& L) {
+    double* d = base;
+    A0 = d; d += L.R * L.ld;
+    A1 = d; d += L.R * L.ld;
+    X = d; d += L.R * L.m;
+    P = d; d += L.R * L.m;
+    V = d; d += L.R * L.m;
+    rc = d; d += L.npairs;
+    rs = d; d += L.npairs;
+    cj = d; d += L.m;
+    sj = d; d += L.m;
+    dg = d; d += L.m;
+    dsc = d; d += L.m;
+    aux = d; d += L.m;
+    red = d; d += 8;
+    int* ip = reinterpret_cast<int*>(d);
+    part = ip; ip += L.m;
+    isp = ip; ip += L.m;
+    rk = ip; ip += L.m;
+    flag = ip;
+  }
+};
+
+// pair k of step `step` in the round-robin order (p < q; q >= m: no pair)
+__device__ __forceinline__ void rr_pair(int k, int step, int mp, int& p, int& q) {
+  if (k == 0) {
+    p = mp - 1;
+    q = step;
+  } else {
+    p = (step + k) % (mp - 1);
+    q = (step - k + (mp - 1)) % (mp - 1);
+  }
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+}
+
+// Cyclic Jacobi over the cluster on the rows in *Acur (swapped in place as the
+// steps alternate buffers).  Every CTA returns the same value: the sweeps
+// used, or -1 when the cap is hit.
+__device__ int jacobi_cluster(cg::cluster_group& cl, const ClLayout& L, ClSmem& S, double*& Acur, double*& Anext,
+                              double abs_tol, int max_sweeps) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int rank = (int)cl.block_rank();
+  const int m = L.m, ld = L.ld, CL = L.CL, R = L.R;
+  const int mp = m + (m & 1);
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) *S.flag = 0;
+    for (int step = 0; step < mp - 1; ++step) {
+      // 1. this CTA's rotations, broadcast to the cluster
+      for (int k = rank + CL * tid; k < L.npairs; k += CL * nth) {
+        int p, q;
+        rr_pair(k, step, mp, p, q);
+        double c = 1.0, sn = 0.0;
+        if (q < m) {
+          const double* rowp = cl.map_shared_rank(Acur, p % CL) + (p / CL) * ld;
+          const double* rowq = cl.map_shared_rank(Acur, q % CL) + (q / CL) * ld;
+          const double apq = rowp[q], app = rowp[p], aqq = rowq[q];
+          if (fabs(apq) > 1e-15 * sqrt(fabs(app)) * sqrt(fabs(aqq)) && fabs(apq) > abs_tol && fabs(apq) > 1e-300) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau)) : -1.0 / (-tau + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+          }
+        }
+        for (int d = 0; d < CL; ++d) {
+          cl.map_shared_rank(S.rc, d)[k] = c;
+          cl.map_shared_rank(S.rs, d)[k] = sn;
+        }
+      }
+      cl.sync();
+      // 2. per-index rotation tables
+      for (int k = tid; k < L.npairs; k += nth) {
+        int p, q;
+        rr_pair(k, step, mp, p, q);
+        const double c = S.rc[k], sn = S.rs[k];
+        if (q < m && sn != 0.0) {
+          S.part[p] = q;
+          S.part[q] = p;
+          S.isp[p] = 1;
+          S.isp[q] = 0;
+          S.cj[p] = S.cj[q] = c;
+          S.sj[p] = S.sj[q] = sn;
+          *S.flag = 1;
+        } else {
+          S.part[p] = -1;
+          if (q < m) S.part[q] = -1;
+        }
+      }
+      __syncthreads();
+      // 3. partner rows (current values) of this CTA's rows
+      for (int t = tid; t < R * m; t += nth) {
+        const int lr = t / m, j = t % m, i = lr * CL + rank;
+        if (i >= m) continue;
+        const int pi = S.part[i];
+        if (pi >= 0) S.P[lr * m + j] = cl.map_shared_rank(Acur, pi % CL)[(pi / CL) * ld + j];
+      }
+      __syncthreads();
+      // 4. rows: X = J^T A (this CTA's rows); V <- V J
+      for (int t = tid; t < R * m; t += nth) {
+        const int lr = t / m, j = t % m, i = lr * CL + rank;
+        if (i >= m) continue;
+        const double a = Acur[lr * ld + j];
+        const int pi = S.part[i];
+        double x = a;
+        if (pi >= 0) {
+          const double c = S.cj[i], sn = S.sj[i], pr = S.P[lr * m + j];
+          x = S.isp[i] ? c * a - sn * pr : sn * pr + c * a;
+        }
+        S.X[lr * m + j] = x;
+        const int pj = S.part[j];
+        if (pj >= 0 && S.isp[j]) {
+          const double c = S.cj[j], sn = S.sj[j];
+          const double vp = S.V[lr * m + j], vq = S.V[lr * m + pj];
+          S.V[lr * m + j] = c * vp - sn * vq;
+          S.V[lr * m + pj] = sn * vp + c * vq;
+        }
+      }
+      __syncthreads();
+      // 5. columns: A' = X J into the second buffer
+      for (int t = tid; t < R * m; t += nth) {
+        const int lr = t / m, j = t % m, i = lr * CL + rank;
+        if (i >= m) continue;
+        const double x = S.X[lr * m + j];
+        const int pj = S.part[j];
+        double v = x;
+        if (pj >= 0) {
+          const double c = S.cj[j], sn = S.sj[j], xo = S.X[lr * m + pj];
+          v = S.isp[j] ? c * x - sn * xo : sn * xo + c * x;
+        }
+        Anext[lr * ld + j] = v;
+      }
+      cl.sync();
+      double* t = Acur;
+      Acur = Anext;
+      Anext = t;
+    }
+    __syncthreads();
+    const int any = *S.flag;
+    __syncthreads();
+    if (!any) return sweep + 1;
+  }
+  return -1;
+}
+
+// diag[i] = A[i, i] for every i, read from the owners (all CTAs get all).
+__device__ void cl_gather_diag(cg::cluster_group& cl, const ClLayout& L, const double* Acur, double* out) {
+  for (int i = threadIdx.x; i < L.m; i += blockDim.x)
+    out[i] = cl.map_shared_rank(Acur, i % L.CL)[(i / L.CL) * L.ld + i];
+  cl.sync();
+}
+
+// Two-stage reduced eigensolve on a cluster (see k_reduced_eig); work as
+// there: U, W, T (m*m doubles each), here row-major.  The work matrices are
+// written and read by different CTAs of the launch, so their reads bypass L1
+// (__ldcg) after the fence and cluster barrier that publish them.
+__global__ void __launch_bounds__(kClThreads) k_reduced_eig_cluster(int m, const double* __restrict__ AQ,
+                                                                    const double* __restrict__ BQ,
+                                                                    double* __restrict__ eps, double* __restrict__ Phi,
+                                                                    double* __restrict__ work, int* status) {
+  extern __shared__ double clsmem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const ClLayout L(m, (int)cl.num_blocks());
+  ClSmem S(clsmem, L);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int rank = (int)cl.block_rank();
+  const int CL = L.CL, R = L.R, ld = L.ld;
+  double* Ug = work;
+  double* Wg = work + (long long)m * m;
+  double* Tg = work + 2LL * m * m;
+  double* Acur = S.A0;
+  double* Anext = S.A1;
+
+  // ---- stage 1: B_Q (symmetrised), V = I
+  for (int t = tid; t < R * m; t += nth) {
+    const int lr = t / m, j = t % m, i = lr * CL + rank;
+    if (i >= m) continue;
+    Acur[lr * ld + j] = 0.5 * (BQ[i + (long long)j * m] + BQ[j + (long long)i * m]);
+    S.V[lr * m + j] = (i == j) ? 1.0 : 0.0;
+  }
+  cl.sync();
+  const int sw = jacobi_cluster(cl, L, S, Acur, Anext, 0.0, 40);
+  cl_gather_diag(cl, L, Acur, S.dg);
+  double dmin = S.dg[0], dmax = S.dg[0];
+  for (int i = 1; i < m; ++i) {
+    dmin = fmin(dmin, S.dg[i]);
+    dmax = fmax(dmax, S.dg[i]);
+  }
+  if (!(dmin > 1e-14 * dmax)) {
+    if (tid == 0 && rank == 0) atomicExch(status, (int)DEV_BQ_NOT_SPD);
+    return;
+  }
+  if (sw < 0) {
+    if (tid == 0 && rank == 0) atomicExch(status, (int)DEV_JACOBI);
+    return;
+  }
+  for (int i = tid; i < m; i += nth) S.dsc[i] = 1.0 / sqrt(S.dg[i]);
+  // U (row-major) to global
+  for (int t = tid; t < R * m; t += nth) {
+    const int lr = t / m, j = t % m, i = lr * CL + rank;
+    if (i < m) Ug[(long long)i * m + j] = S.V[lr * m + j];
+  }
+  __threadfence();
+  cl.sync();
+  // ---- T = A_Q U (this CTA's rows; A_Q symmetrised into the free buffer)
+  for (int t = tid; t < R * m; t += nth) {
+    const int lr = t / m, j = t % m, i = lr * CL + rank;
+    if (i < m) Acur[lr * ld + j] = 0.5 * (AQ[i + (long long)j * m] + AQ[j + (long long)i * m]);
+  }
+  __syncthreads();
+  for (int t = tid; t < R * m; t += nth) {
+    const int lr = t / m, j = t % m, i = lr * CL + rank;
+    if (i >= m) continue;
+    double s = 0.0;
+    for (int l = 0; l < m; ++l) s = fma(Acur[lr * ld + l], __ldcg(Ug + (long long)l * m + j), s);
+    Tg[(long long)i * m + j] = s;
+  }
+  __threadfence();
+  cl.sync();
+  // ---- C = D^{-1/2} U^T T D^{-1/2} (rows to the W area, then symmetrised)
+  for (int t = tid; t < R * m; t += nth) {
+    const int lr = t / m, j = t % m, i = lr * CL + rank;
+    if (i >= m) continue;
+    double s = 0.0;
+    for (int l = 0; l < m; ++l) s = fma(__ldcg(Ug + (long long)l * m + i), __ldcg(Tg + (long long)l * m + j), s);
+    Wg[(long long)i * m + j] = s * S.dsc[i] * S.dsc[j];
+  }
+  __threadfence();
+  cl.sync();
+  double fro2 = 0.0;
+  for (int t = tid; t < R * m; t += nth) {
+    const int lr = t / m, j = t % m, i = lr * CL + rank;
+    if (i >= m) continue;
+    const double v = (i == j) ? __ldcg(Wg + (long long)i * m + i)
+                              : 0.5 * (__ldcg(Wg + (long long)i * m + j) + __ldcg(Wg + (long long)j * m + i));
+    Acur[lr * ld + j] = v;
+    S.V[lr * m + j] = (i == j) ? 1.0 : 0.0;
+    fro2 += v * v;
+  }
+  // ||C||_F: warp sums, the CTA's sum, then the cluster's in rank order
+  for (int o = 16; o > 0; o >>= 1) fro2 += __shfl_down_sync(0xffffffffu, fro2, o);
+  if ((tid & 31) == 0) S.aux[tid >> 5] = fro2;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nth / 32; ++w) t += S.aux[w];
+    S.red[0] = t;
+  }
+  cl.sync();
+  double fro = 0.0;
+  for (int r = 0; r < CL; ++r) fro += cl.map_shared_rank(S.red, r)[0];
+  fro = sqrt(fro);
+  cl.sync();
+  // ---- stage 2
+  const int sw2 = jacobi_cluster(cl, L, S, Acur, Anext, 2.0 * 2.220446049250313e-16 * fro, 40);
+  if (sw2 < 0) {
+    if (tid == 0 && rank == 0) atomicExch(status, (int)DEV_JACOBI);
+    return;
+  }
+  cl_gather_diag(cl, L, Acur, S.dg);   // eigenvalues of C
+  for (int t = tid; t < R * m; t += nth) {
+    const int lr = t / m, j = t % m, i = lr * CL + rank;
+    if (i < m) Wg[(long long)i * m + j] = S.V[lr * m + j];
+  }
+  for (int j = tid; j < m; j += nth) {
+    const double ej = S.dg[j];
+    int r = 0;
+    for (int l = 0; l < m; ++l) r += (S.dg[l] < ej) || (S.dg[l] == ej && l < j);
+    S.rk[j] = r;
+  }
+  __threadfence();
+  cl.sync();
+  // ---- Phi = U D^{-1/2} W, columns at their ascending rank
+  for (int t = tid; t < R * m; t += nth) {
+    const int lr = t / m, j = t % m, i = lr * CL + rank;
+    if (i >= m) continue;
+    double s = 0.0;
+    for (int l = 0; l < m; ++l) s = fma(__ldcg(Ug + (long long)i * m + l) * S.dsc[l], __ldcg(Wg + (long long)l * m + j), s);
+    Phi[i + (long long)S.rk[j] * m] = s;
+  }
+  if (rank == 0)
+    for (int j = tid; j < m; j += nth) eps[S.rk[j]] = S.dg[j];
+}
+
 // ---------------------------------------------------------------- residuals
 __global__ void __launch_bounds__(256) k_residual_norms(long long N, const double* __restrict__ AX,
                                                         const double* __restrict__ BX,
@@ -398,8 +725,59 @@ void dgemm_tall(cudaStream_t s, long long N, int m, int k, const double* Q, cons
   prof::count_launch();
 }
 
+// Cluster size for the reduced eigensolve: 16 CTAs where the device can
+// co-schedule such a cluster (a non-portable size), else 8; 0 when neither
+// launches.
+int reduced_eig_cluster_size(int m) {
+  static std::once_flag once;
+  static int size16 = 0, size8 = 0;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_reduced_eig_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)cl_smem_bytes(128, 8));
+    cudaFuncSetAttribute(k_reduced_eig_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int cl : {16, 8}) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = cl;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(cl);
+      cfg.blockDim = dim3(kClThreads);
+      cfg.dynamicSmemBytes = cl_smem_bytes(128, cl);
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, k_reduced_eig_cluster, &cfg) == cudaSuccess && n > 0)
+        (cl == 16 ? size16 : size8) = cl;
+      cudaGetLastError();
+    }
+  });
+  if (m < kClMinM) return 0;
+  return size16 ? size16 : size8;
+}
+
 void reduced_eig(cudaStream_t s, int m, const double* AQ, const double* BQ, double* eps, double* Phi,
                  double* work, int* status) {
+  if (const int cl = reduced_eig_cluster_size(m)) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = cl_smem_bytes(m, cl);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_reduced_eig_cluster, m, AQ, BQ, eps, Phi, work, status) == cudaSuccess) {
+      prof::count_launch();
+      return;
+    }
+    cudaGetLastError();   // fall through to the one-CTA kernel
+  }
   const size_t smem = sizeof(double) * ((size_t)m * (m + 1) + 2 * (m / 2 + 2) + 2 * m) +
                       sizeof(int) * (2 * (m / 2 + 2) + 1);
   static std::once_flag once;

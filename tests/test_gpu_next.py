@@ -32,19 +32,28 @@ def _prec(name):
     return F().FEAST_PREC_MIXED if name == "mixed" else F().FEAST_PREC_FP64
 
 
+# Sec. III.B (ii): M0 has an upper limit beyond which B_Q is not positive
+# definite.  With 16 nodes the filter is so sharp that the components of the
+# M0 - M extra directions fall below the definiteness threshold of the reduced
+# problem from the second loop on for M0 >= 12 on this workload (the oracle
+# raises BQNotSPD), so that case runs with M0 = 11.
+SWEEP_M0 = {4: 16, 16: 11}
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("Ne", [4, 16])
 def test_node_count_sweep_matches_oracle(intervals, Ne, precision):
     wl = workloads.WORKLOADS["q1_10x10x20_fp64"]
     op = wl.operator(3)
     iv = intervals["q1_10x10x20/seed3"]
-    Y = workloads.random_Y(op.N, wl.M0, 1003)
-    ref = oracle.feast(op, iv["lmin"], iv["lmax"], wl.M0, Ne, Y, tol=wl.tol)
+    M0 = SWEEP_M0[Ne]
+    Y = workloads.random_Y(op.N, M0, 1003)
+    ref = oracle.feast(op, iv["lmin"], iv["lmax"], M0, Ne, Y, tol=wl.tol)
     dop, keep = dev_op(op)
-    lam = torch.zeros(wl.M0, dtype=torch.float64, device="cuda")
-    X = torch.zeros((wl.M0, op.N), dtype=torch.float64, device="cuda")
+    lam = torch.zeros(M0, dtype=torch.float64, device="cuda")
+    X = torch.zeros((M0, op.N), dtype=torch.float64, device="cuda")
     h = F().Handle(precision=_prec(precision))
-    r = h.feast_solve(dop, iv["lmin"], iv["lmax"], wl.M0, Ne, wl.tol, cm(Y), lam, X, None, allow=())
+    r = h.feast_solve(dop, iv["lmin"], iv["lmax"], M0, Ne, wl.tol, cm(Y), lam, X, None, allow=())
     M = iv["M"]
     assert r.m_found == ref.m_found == M
     got = lam.cpu().numpy()[:M]
