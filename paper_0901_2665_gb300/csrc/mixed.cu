@@ -32,7 +32,7 @@ namespace feast {
 namespace {
 
 constexpr int kPanel = 64;   // sweep panel width (complex columns)
-constexpr int kRowsPerPanelCta = 32;
+constexpr int kRowsPerPanelCta = 16;
 
 struct f2 {
   float x, y;
@@ -141,142 +141,108 @@ __device__ __forceinline__ f2 f2inv_fast(f2 a) {
 }
 
 // Pinv = S[K,K]^{-1} for panel K = [k0, k0+bw) of every node (one CTA per
-// node, 256 threads): block sweep of the 64 x 64 diagonal block (fp32,
-// padded with the identity when bw < 64) in four 16-wide sub-panels.  For
-// each sub-panel J, one warp sweeps the 16 x 16 block P[J,J] in registers
-// (shuffles, no block barrier) giving D = P[J,J]^{-1}; then the CTA forms
-// T = P[:,J] D and applies the block sweep to the 64 x 64 block:
-//   i, j outside J: P[i,j] -= T[i,:] P[J,j];  i outside, j in J: P[i,j] = T[i,j];
-//   i in J, j outside: P[i,j] = T[j,i] (symmetry);  both in J: P[i,j] = -D.
-// After the four sub-panels P = -S[K,K]^{-1}.
-constexpr int kPinvThreads = 256;
-constexpr int kSub = 16;
+// node): the Gauss-Jordan sweep of the 64 x 64 diagonal block (fp32, padded
+// with the identity when bw < 64), one pivot at a time:
+//   p = P[k,k];  P[i,j] -= P[i,k] P[k,j] / p  (i, j != k);
+//   P[k,j] /= p;  P[i,k] /= p;  P[k,k] = -1/p,
+// after which P = -S[K,K]^{-1}.  Thread t holds column j = t % 64 of rows
+// t / 64 + 8a (a < 8) in registers.  After each pivot the holders of the next
+// pivot's row and column publish them to shared memory (double-buffered by
+// pivot parity), and the holder of the next pivot publishes its reciprocal,
+// so that one block barrier per pivot suffices and the reciprocal is formed
+// once.  Every thread applies the rank-1 update to its eight entries; the
+// pivot row (two warps) and the pivot column (one lane in eight warps) are
+// then overwritten.  The 64 pivots are the kernel's critical path.
+constexpr int kPinvThreads = 512;
+constexpr int kPinvGroups = kPinvThreads / kPanel;   // row groups
+constexpr int kPinvRows = kPanel / kPinvGroups;      // rows per thread
 
 __global__ void __launch_bounds__(kPinvThreads) k_mx_pinv(Dims d, int layer, int k0, int bw,
                                                           const float* __restrict__ F, f2* __restrict__ PinvOut,
                                                           int* status) {
-  __shared__ f2 P[kPanel][kPanel + 1];
-  __shared__ f2 Dn[kSub][kSub + 1];
-  __shared__ f2 T[kPanel][kSub + 1];
+  __shared__ f2 rowb[2][kPanel];   // row k of P before pivot k
+  __shared__ f2 colb[2][kPanel];   // column k of P before pivot k
+  __shared__ f2 invb[2];           // 1 / P[k, k] before pivot k
   __shared__ int bad;
   const int e = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+  const int tid = threadIdx.x;
+  const int j = tid % kPanel, g = tid / kPanel;   // column, row group (rows g + 8a)
   const int n = d.n;
   const float* Fl = F + ((long long)e * 2 + (layer & 1)) * n * d.ldF;
   if (tid == 0) bad = 0;
-  for (int t = tid; t < kPanel * kPanel; t += kPinvThreads) {
-    const int i = t / kPanel, j = t % kPanel;
+  f2 v[kPinvRows];
+#pragma unroll
+  for (int a = 0; a < kPinvRows; ++a) {
+    const int i = g + kPinvGroups * a;
     f2 x{(i == j) ? 1.f : 0.f, 0.f};
     if (i < bw && j < bw) {
       const float* row = Fl + (long long)(k0 + i) * d.ldF;
       x = f2{row[k0 + j], row[n + k0 + j]};
     }
-    P[i][j] = x;
+    v[a] = x;
   }
-  __syncthreads();
-  for (int sb = 0; sb < kPanel / kSub; ++sb) {
-    const int J0 = sb * kSub;
-    // ---- A: warp 0 sweeps P[J,J]; lane l holds row l/2, columns 8(l%2)..+7
-    if (warp == 0) {
-      const int r = lane >> 1, c0 = (lane & 1) * 8;
-      f2 v[8];
+  __syncthreads();   // `bad` initialised
+  // publish pivot kn from this thread's entries (row kn: threads of row group
+  // kn % 8; column kn: threads j == kn; the pivot's holder: its reciprocal)
+  auto publish = [&](int kn, int buf) {
+    const int an = kn / kPinvGroups;
+    if (g == kn % kPinvGroups) {
+      f2 x = v[0];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) v[t] = P[J0 + r][J0 + c0 + t];
-#pragma unroll
-      for (int k = 0; k < kSub; ++k) {
-        // pivot row k (my 8 columns), pivot column k (my row), pivot value
-        f2 rowk[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          rowk[t].x = __shfl_sync(0xffffffffu, v[t].x, 2 * k + (lane & 1));
-          rowk[t].y = __shfl_sync(0xffffffffu, v[t].y, 2 * k + (lane & 1));
-        }
-        f2 colk, piv;
-        colk.x = __shfl_sync(0xffffffffu, v[k % 8].x, 2 * r + k / 8);
-        colk.y = __shfl_sync(0xffffffffu, v[k % 8].y, 2 * r + k / 8);
-        piv.x = __shfl_sync(0xffffffffu, v[k % 8].x, 2 * k + k / 8);
-        piv.y = __shfl_sync(0xffffffffu, v[k % 8].y, 2 * k + k / 8);
-        const float mag = fabsf(piv.x) + fabsf(piv.y);
+      for (int a = 1; a < kPinvRows; ++a)
+        if (a == an) x = v[a];
+      rowb[buf][j] = x;
+      if (j == kn) {
+        const float mag = fabsf(x.x) + fabsf(x.y);
         const bool good = mag > 0.f && isfinite(mag);
-        if (lane == 0 && !good) bad = 1;
-        const f2 inv = good ? f2inv_fast(piv) : f2{0.f, 0.f};
-        const f2 fac = f2mul(colk, inv);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int j = c0 + t;
-          const f2 u = f2mul(fac, rowk[t]);
-          const f2 upd{v[t].x - u.x, v[t].y - u.y};
-          const f2 rowv = f2mul(rowk[t], inv);
-          v[t] = (r != k) ? ((j != k) ? upd : fac) : ((j != k) ? rowv : f2{-inv.x, -inv.y});
-        }
+        if (!good) bad = 1;
+        invb[buf] = good ? f2inv_fast(x) : f2{0.f, 0.f};
       }
-#pragma unroll
-      for (int t = 0; t < 8; ++t) Dn[r][c0 + t] = f2{-v[t].x, -v[t].y};   // D = P[J,J]^{-1}
     }
-    __syncthreads();
-    // ---- B: T = P[:, J] D (64 x 16), thread -> row tid/4, columns 4(tid%4)..+3
-    {
-      const int i = tid / 4, q0 = (tid % 4) * 4;
-      f2 acc[4] = {f2{0.f, 0.f}, f2{0.f, 0.f}, f2{0.f, 0.f}, f2{0.f, 0.f}};
+    if (j == kn)
 #pragma unroll
-      for (int m = 0; m < kSub; ++m) {
-        const f2 pim = P[i][J0 + m];
+      for (int a = 0; a < kPinvRows; ++a) colb[buf][g + kPinvGroups * a] = v[a];
+  };
+  publish(0, 0);
+  __syncthreads();
+#pragma unroll 1
+  for (int k = 0; k < kPanel; ++k) {
+    const int b = k & 1;
+    const f2 inv = invb[b];
+    const f2 rki = f2mul(rowb[b][j], inv);   // P[k, j] / p
+    // rank-1 update of every entry: P[i, j] -= P[i, k] P[k, j] / p
 #pragma unroll
-        for (int q = 0; q < 4; ++q) f2fma(acc[q], pim, Dn[m][q0 + q]);
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) T[i][q0 + q] = acc[q];
+    for (int a = 0; a < kPinvRows; ++a) {
+      const f2 c = colb[b][g + kPinvGroups * a];
+      v[a].x = fmaf(-c.x, rki.x, v[a].x);
+      v[a].x = fmaf(c.y, rki.y, v[a].x);
+      v[a].y = fmaf(-c.x, rki.y, v[a].y);
+      v[a].y = fmaf(-c.y, rki.x, v[a].y);
     }
-    __syncthreads();
-    // ---- C: the block sweep of the 64 x 64 block; thread -> column j = tid % 64
-    // and rows 16 (tid / 64) .. +15, so a warp reads 32 consecutive entries of
-    // a row (no bank conflicts) and broadcasts T[i, m]
-    {
-      const int j = tid % kPanel, i0 = (tid / kPanel) * 16;
-      const bool inJ = j >= J0 && j < J0 + kSub;
-      f2 out[16];
+    // pivot column: P[i, k] = P[i, k] / p
+    if (j == k)
 #pragma unroll
-      for (int a = 0; a < 16; ++a) out[a] = P[i0 + a][j];
-      if (!inJ) {
-#pragma unroll 4
-        for (int m = 0; m < kSub; ++m) {
-          const f2 pj = P[J0 + m][j];
+      for (int a = 0; a < kPinvRows; ++a) v[a] = f2mul(colb[b][g + kPinvGroups * a], inv);
+    // pivot row: P[k, j] = P[k, j] / p, and P[k, k] = -1 / p
+    if (g == k % kPinvGroups) {
+      const f2 x = (j == k) ? f2{-inv.x, -inv.y} : rki;
 #pragma unroll
-          for (int a = 0; a < 16; ++a) {
-            const f2 u = f2mul(T[i0 + a][m], pj);
-            out[a].x -= u.x;
-            out[a].y -= u.y;
-          }
-        }
-      }
-#pragma unroll
-      for (int a = 0; a < 16; ++a) {
-        const int i = i0 + a;
-        const bool inI = i >= J0 && i < J0 + kSub;
-        if (!inI && inJ) {
-          out[a] = T[i][j - J0];
-        } else if (inI && !inJ) {
-          out[a] = T[j][i - J0];
-        } else if (inI && inJ) {
-          const f2 dv = Dn[i - J0][j - J0];
-          out[a] = f2{-dv.x, -dv.y};
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int a = 0; a < 16; ++a) P[i0 + a][j] = out[a];
+      for (int a = 0; a < kPinvRows; ++a)
+        if (a == k / kPinvGroups) v[a] = x;
     }
+    if (k + 1 < kPanel) publish(k + 1, b ^ 1);
     __syncthreads();
   }
   // P holds -S[K,K]^{-1}
-  for (int t = tid; t < kPanel * kPanel; t += kPinvThreads) {
-    const f2 v = P[t / kPanel][t % kPanel];
-    PinvOut[(long long)e * kPanel * kPanel + t] = f2{-v.x, -v.y};
+#pragma unroll
+  for (int a = 0; a < kPinvRows; ++a) {
+    const int i = g + kPinvGroups * a;
+    PinvOut[(long long)e * kPanel * kPanel + i * kPanel + j] = f2{-v[a].x, -v[a].y};
   }
   if (tid == 0 && bad) atomicExch(status, (int)DEV_PIVOT);
 }
 
-// For panel K and this CTA's 32 rows i:  T[i, :] = S[i, K] Pinv  and
+// For panel K and this CTA's kRowsPerPanelCta rows i:  T[i, :] = S[i, K] Pinv  and
 // L[i, :] = S[i, K], written as the TF32-rounded GEMM operands
 // Aop = [Tr | Ti] (row i) and Bop (embedded L, rows in blocks of 64 complex
 // columns: 64 rows [Lr, -Li] then 64 rows [Li, Lr]), and in fp32 as Tc.
@@ -303,20 +269,21 @@ __global__ void __launch_bounds__(256) k_mx_panel_T(Dims d, int layer, int k0, i
     Ls[r][m] = x;
   }
   __syncthreads();
-  // thread -> column c, rows r0 + rq + 4q (q < 8): the Pinv loads of a warp are
-  // 32 consecutive entries, the L loads a broadcast
+  // thread -> column c, rows r0 + rq + 4q (q < kRowsPerPanelCta / 4): the
+  // Pinv loads of a warp are 32 consecutive entries, the L loads a broadcast
+  constexpr int kRowsPerThread = kRowsPerPanelCta / 4;
   const int c = tid % kPanel, rq = tid / kPanel;
-  f2 acc[8];
+  f2 acc[kRowsPerThread];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) acc[q] = f2{0.f, 0.f};
-#pragma unroll 4
+  for (int q = 0; q < kRowsPerThread; ++q) acc[q] = f2{0.f, 0.f};
+#pragma unroll 8
   for (int m = 0; m < kPanel; ++m) {
     const f2 pv = Ps[m][c];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) f2fma(acc[q], Ls[rq + 4 * q][m], pv);
+    for (int q = 0; q < kRowsPerThread; ++q) f2fma(acc[q], Ls[rq + 4 * q][m], pv);
   }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
+  for (int q = 0; q < kRowsPerThread; ++q) {
     const int r = rq + 4 * q;
     const int i = r0 + r;
     if (i >= n) continue;
@@ -605,6 +572,14 @@ struct SolveEpi {
 };
 
 // ------------------------------------------------------------------ couplings
+// The nodes a sweep works on (bit e set: node e; all Ne nodes in the first
+// solve, the unconverged ones in refinement steps): CTA z of every sweep
+// kernel handles the node of the z-th set bit.
+struct NodeList {
+  int count;
+  unsigned long long mask;
+};
+
 // Writes the embedded, TF32-rounded RHS rows of complex column m.
 __device__ __forceinline__ void write_emb(const Dims& d, float* Bemb, int e, int p, int m, f2 g) {
   const long long blk = (long long)e * d.nblkCB + m / d.CB;
@@ -623,9 +598,9 @@ __device__ __forceinline__ void write_emb(const Dims& d, float* Bemb, int e, int
 __global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, int layer, const f2* __restrict__ Cf,
                                                        const double* __restrict__ Rreal, const f2* __restrict__ Rc,
                                                        const f2* __restrict__ Tout, f2* __restrict__ Gc,
-                                                       float* __restrict__ Bemb) {
+                                                       float* __restrict__ Bemb, NodeList nl) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int m = blockIdx.y, e = blockIdx.z;
+  const int m = blockIdx.y, e = tc::nth_set_bit(nl.mask, (int)blockIdx.z);
   if (p >= d.n) return;
   const long long row = (long long)layer * d.n + p;
   const long long sG = d.N * d.k;
@@ -644,9 +619,10 @@ __global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, int layer, const 
 
 // backward: s_i = g_i - U_i x_{i+1} (U_i = M[i, i+1], empty on the top layer)
 __global__ void __launch_bounds__(128) k_mx_couple_bwd(Dims d, int layer, const f2* __restrict__ Cf,
-                                                       const f2* __restrict__ Gc, float* __restrict__ Bemb) {
+                                                       const f2* __restrict__ Gc, float* __restrict__ Bemb,
+                                                       NodeList nl) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int m = blockIdx.y, e = blockIdx.z;
+  const int m = blockIdx.y, e = tc::nth_set_bit(nl.mask, (int)blockIdx.z);
   if (p >= d.n) return;
   const long long row = (long long)layer * d.n + p;
   const long long sG = d.N * d.k;
@@ -1080,7 +1056,10 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
     cudaError_t err;
     if (tma_rmw) {
       SweepEpiTma epi{mapF, mapFr, layer & 1, layer, d.nz, d.n, k0, bw, last ? 1 : 0, Tc[q], Pv[q]};
-      err = launch_tc<128, 1>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status);
+      // the narrow update (one column tile, few CTAs, on the critical path)
+      // pipelines its K-blocks; the wide one keeps two CTAs per SM instead
+      err = count == 1 ? launch_tc<128, 4>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status)
+                       : launch_tc<128, 1>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status);
     } else {
       SweepEpi epi{F + (long long)(layer & 1) * d.n * d.ldF, sF, last ? Fr + (long long)layer * d.n * d.ldF : nullptr,
                    sFr, d.ldF, d.n, k0, bw, Tc[q], Pv[q]};
@@ -1125,7 +1104,7 @@ namespace {
 
 template <int CB>
 const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const double* A27, const double* B27,
-                         MixedWork& w, const double* Rreal, const f2* Rc, int* status) {
+                         MixedWork& w, const double* Rreal, const f2* Rc, const NodeList& nl, int* status) {
   float* F = buf<float>(w, B_F);
   f2* Gc = buf<f2>(w, B_GC);
   f2* Tout = buf<f2>(w, B_TOUT);
@@ -1136,26 +1115,31 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     return "tensor map (rhs) rejected";
   const int nk = (2 * d.n + tc::kBlockK - 1) / tc::kBlockK;
   const f2* Cf = buf<f2>(w, B_CF);
-  const dim3 cgrid(cdiv(d.n, 128), d.k, d.Ne);
-  const dim3 ggrid(d.nblkCB, cdiv(d.n, 128), d.Ne);
+  const int nn = nl.count;
+  const dim3 cgrid(cdiv(d.n, 128), d.k, nn);
+  const dim3 ggrid(d.nblkCB, cdiv(d.n, 128), nn);
+  tc::Geom geo0{0, d.nz * d.n, 0, d.nblkCB * 2 * CB, nk};
+  geo0.node_mask = nl.mask;
   // forward sweep
-  k_mx_couple_fwd<<<cgrid, 128, 0, s>>>(d, 0, Cf, Rreal, Rc, Tout, Gc, Bemb);
+  k_mx_couple_fwd<<<cgrid, 128, 0, s>>>(d, 0, Cf, Rreal, Rc, Tout, Gc, Bemb, nl);
   for (int i = 1; i < d.nz; ++i) {
     SolveEpi<CB> epi{Tout, (long long)d.n * d.k, d.n, d.n, d.k, 1.0f};
-    tc::Geom geo{(i - 1) * d.n, d.nz * d.n, 0, d.nblkCB * 2 * CB, nk};
+    tc::Geom geo = geo0;
+    geo.a_row0 = (i - 1) * d.n;
     prof::begin(s, prof::SOLVE_GEMM);
-    prof::add_work(prof::SOLVE_GEMM, 8.0 * d.n * (double)d.n * d.k * d.Ne);
+    prof::add_work(prof::SOLVE_GEMM, 8.0 * d.n * (double)d.n * d.k * nn);
     if (launch_tc<2 * CB, 4>(s, ggrid, tmF, tmB, geo, epi, status) != cudaSuccess) return "tcgen05 solve launch failed";
     prof::end(s, prof::SOLVE_GEMM);
-    k_mx_couple_fwd<<<cgrid, 128, 0, s>>>(d, i, Cf, Rreal, Rc, Tout, Gc, Bemb);
+    k_mx_couple_fwd<<<cgrid, 128, 0, s>>>(d, i, Cf, Rreal, Rc, Tout, Gc, Bemb, nl);
   }
   // backward sweep: x_i overwrites g_i
   for (int i = d.nz - 1; i >= 0; --i) {
-    k_mx_couple_bwd<<<cgrid, 128, 0, s>>>(d, i, Cf, Gc, Bemb);
+    k_mx_couple_bwd<<<cgrid, 128, 0, s>>>(d, i, Cf, Gc, Bemb, nl);
     SolveEpi<CB> epi{Gc + (long long)i * d.n, d.N * d.k, d.N, d.n, d.k, -1.0f};
-    tc::Geom geo{i * d.n, d.nz * d.n, 0, d.nblkCB * 2 * CB, nk};
+    tc::Geom geo = geo0;
+    geo.a_row0 = i * d.n;
     prof::begin(s, prof::SOLVE_GEMM);
-    prof::add_work(prof::SOLVE_GEMM, 8.0 * d.n * (double)d.n * d.k * d.Ne);
+    prof::add_work(prof::SOLVE_GEMM, 8.0 * d.n * (double)d.n * d.k * nn);
     if (launch_tc<2 * CB, 4>(s, ggrid, tmF, tmB, geo, epi, status) != cudaSuccess) return "tcgen05 solve launch failed";
     prof::end(s, prof::SOLVE_GEMM);
   }
@@ -1226,12 +1210,20 @@ int tuned_cb(cudaStream_t s, const Dims& d, MixedWork& w, int* status) {
 }
 
 const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const double* A27, const double* B27,
-                       MixedWork& w, const double* Rreal, const f2* Rc, int* status) {
+                       MixedWork& w, const double* Rreal, const f2* Rc, const std::vector<int>& active,
+                       int* status) {
+  NodeList nl{0, 0ULL};
+  for (int e = 0; e < d.Ne; ++e)
+    if (active[e]) {
+      nl.mask |= 1ULL << e;
+      ++nl.count;
+    }
+  if (nl.count == 0) return nullptr;
   switch (d.CB) {
-    case 8: return solve_sweeps<8>(s, d, Z, A27, B27, w, Rreal, Rc, status);
-    case 16: return solve_sweeps<16>(s, d, Z, A27, B27, w, Rreal, Rc, status);
-    case 32: return solve_sweeps<32>(s, d, Z, A27, B27, w, Rreal, Rc, status);
-    default: return solve_sweeps<64>(s, d, Z, A27, B27, w, Rreal, Rc, status);
+    case 8: return solve_sweeps<8>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+    case 16: return solve_sweeps<16>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+    case 32: return solve_sweeps<32>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+    default: return solve_sweeps<64>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
   }
 }
 
@@ -1270,7 +1262,7 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
   std::vector<double> rel(Ne, 0.0), final_rel(Ne, 0.0);
   const int acc_blocks = (int)std::min<long long>(4096, (sG + 255) / 256);
   // first solve: Q_e = M~^{-1} RHS
-  if (const char* m = solve_once(s, d, Z, A27, B27, w, RHS, nullptr, status)) return m;
+  if (const char* m = solve_once(s, d, Z, A27, B27, w, RHS, nullptr, active, status)) return m;
   k_mx_accumulate<<<dim3(acc_blocks, Ne), 256, 0, s>>>(sG, 1, buf<f2>(w, B_GC), G, buf<int>(w, B_ACTIVE));
   prof::count_launch();
   int steps = 0;
@@ -1314,7 +1306,8 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
     if (!any) break;
     if (steps >= ir_max) return "iterative refinement did not reach the tolerance";
     cudaMemcpyAsync(w.bufs[B_ACTIVE], active.data(), sizeof(int) * Ne, cudaMemcpyHostToDevice, s);
-    if (const char* m = solve_once(s, d, Z, A27, B27, w, nullptr, buf<f2>(w, B_RC), status)) return m;
+    // only the unconverged nodes are swept again
+    if (const char* m = solve_once(s, d, Z, A27, B27, w, nullptr, buf<f2>(w, B_RC), active, status)) return m;
     k_mx_accumulate<<<dim3(acc_blocks, Ne), 256, 0, s>>>(sG, 0, buf<f2>(w, B_GC), G, buf<int>(w, B_ACTIVE));
     prof::count_launch();
     ++steps;

@@ -197,7 +197,15 @@ struct Geom {
   int nk;
   int tn_base = 0;    // first n tile of the launch
   int tn_skip = -1;   // n tile left out (the grid's x covers the others), -1 = none
+  unsigned long long node_mask = 0;   // != 0: the batch index of CTA z is the z-th set bit (a compacted batch)
 };
+
+// Position of the z-th set bit (z from 0) of a 64-bit mask.
+__device__ __forceinline__ int nth_set_bit(unsigned long long mask, int z) {
+  const unsigned lo = static_cast<unsigned>(mask), hi = static_cast<unsigned>(mask >> 32);
+  const int c = __popc(lo);
+  return z < c ? static_cast<int>(__fns(lo, 0, z + 1)) : 32 + static_cast<int>(__fns(hi, 0, z - c + 1));
+}
 
 template <int BN, int STAGES>
 struct Smem {
@@ -257,7 +265,8 @@ __global__ void __launch_bounds__(kThreads)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int e = blockIdx.z, tm = blockIdx.y;
+  const int e = geo.node_mask ? nth_set_bit(geo.node_mask, (int)blockIdx.z) : (int)blockIdx.z;
+  const int tm = blockIdx.y;
   int tn = (int)blockIdx.x + geo.tn_base;
   if (geo.tn_skip >= 0 && tn >= geo.tn_skip) ++tn;
 
