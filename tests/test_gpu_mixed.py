@@ -55,6 +55,30 @@ def test_node_solve_mixed_matches_oracle(nx, ny, nz, G, seed, k):
         assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
 
 
+def test_node_solve_mixed_full_cross_section_matches_oracle():
+    """The 32 x 32 cross-section of the full-size workload (n = 1024: sixteen
+    64-wide panels, eight 128-row tiles) with its 128 right-hand sides."""
+    nx, ny, nz, G, seed, k = 32, 32, 3, 4, 7, 128
+    op = workloads.q1_operator(nx, ny, nz, workloads.gaussian_potential(G, seed, nx, ny, nz))
+    lam = oracle.closed_form_eigenvalues_v0(nx, ny, nz)
+    lmin, lmax = lam[0] - 3.0, lam[40]
+    _, _, _, Z, _ = oracle.contour_points(lmin, lmax, 8)
+    RHS = np.random.default_rng(seed + 11).standard_normal((op.N, k))
+    A = oracle.assemble(op.A27, nx, ny, nz)
+    B = oracle.assemble(op.B27, nx, ny, nz)
+    dop, keep = dev_op(op)
+    h = F().Handle(precision=F().FEAST_PREC_MIXED)
+    for z in (Z[0], Z[3]):
+        Qe = torch.zeros((k, op.N), dtype=torch.complex128, device="cuda")
+        info = h.feast_node_solve(dop, complex(z), cm(RHS), Qe, k, precision=F().FEAST_PREC_MIXED)
+        got = back(Qe)
+        M = (z * B - A).astype(np.complex128)
+        res = np.linalg.norm(M @ got - RHS) / np.linalg.norm(RHS)
+        assert res <= 1e-12, res
+        ref = oracle.block_tridiag_factor(M, op.n, nz).solve(RHS.astype(np.complex128))
+        assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
 def test_quadrature_mixed_matches_oracle():
     nx, ny, nz, G, seed = GRIDS[0]
     op = workloads.q1_operator(nx, ny, nz, workloads.gaussian_potential(G, seed, nx, ny, nz))
