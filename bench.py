@@ -46,9 +46,12 @@ FF_OPS_PER_ENTRY = 27 * 4 * 11        # fp32 instructions per complex entry of t
 # were captured on 24 of 400 layers and scaled by 400/24, their traffic being
 # proportional to the rows).  An entry is removed when its kernel changes.
 TRAFFIC = {
-    "solve_gemm": 0.5 * ((83.91 + 2.27) + (83.91 + 1.97)) * 1e6,
-    "fp64_residual": (718.93 + 564.79) * 1e6 * 400 / 24,
-    "ff_residual": (663.74 + 549.21) * 1e6 * 400 / 24,
+    "solve_gemm": 0.5 * ((83.9 + 2.2) + (83.9 + 1.9)) * 1e6,
+    # wide sweep update: 15 regular launches and the last panel's (which also
+    # writes the TF32 solve copy) per layer
+    "sweep_gemm": (15 * (79.2 + 7.6) + (84.0 + 73.2)) / 16 * 1e6,
+    "fp64_residual": (718.9 + 564.9) * 1e6 * 400 / 24,
+    "ff_residual": 0.5 * ((664.0 + 549.2) + (664.1 + 549.1)) * 1e6 * 400 / 24,
 }
 
 
@@ -59,6 +62,16 @@ def roofline(name, ms, flops, launches, pk, pk_src):
     if name == "fp64_residual":
         roof = {"kernel": "k_mx_residual (FP64 refinement residual)", "bound": "alu", "unit": "TFLOP/s",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "peak_source": "GB300 FP64 rate (derived)"}
+    elif name in ("panel_inverse", "panel_product", "schur"):
+        # fp32 CUDA-core arithmetic (complex FMAs counted as 8 flops)
+        roof = {"kernel": name, "bound": "alu", "unit": "TFLOP/s", "achieved": achieved,
+                "peak": 2 * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived)"}
+    elif name == "solve_coupling":
+        # work counted in bytes (couplings between layers of the solve sweeps)
+        gbs = flops / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        roof = {"kernel": "k_mx_couple_fwd/bwd (layer couplings of the solve sweeps)", "bound": "hbm",
+                "unit": "GB/s", "achieved": gbs, "peak": pk["hbm_gbs"], "peak_source": f"{pk_src} HBM copy"}
     elif name == "ff_residual":
         ops = flops / 216.0 * FF_OPS_PER_ENTRY
         roof = {"kernel": "k_mx_residual_inc (double-float refinement residual)", "bound": "alu",
@@ -70,7 +83,10 @@ def roofline(name, ms, flops, launches, pk, pk_src):
                 "peak": pk["bf16_tflops_sustained"] * TF32_NOMINAL_RATIO,
                 "peak_source": f"{pk_src} bf16 sustained x TF32/BF16 nominal ratio"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["flops_per_launch"] = flops / launches if launches else None
+    if roof["bound"] == "hbm":
+        roof["bytes_per_launch"] = flops / launches if launches else None
+    else:
+        roof["flops_per_launch"] = flops / launches if launches else None
     roof["traffic"] = TRAFFIC.get(name)
     return roof
 
@@ -426,9 +442,12 @@ def run_ours(args):
     kernels = {}
     for c in range(len(names)):
         if kn[c] > 0:
+            rate = kfl[c] / (kms[c] * 1e-3) / 1e12 if kms[c] > 0 else None
             kernels[names[c]] = {"ms_total": round(kms[c], 3), "launches": int(kn[c]),
-                                 "avg_us": round(kms[c] / kn[c] * 1e3, 2),
-                                 "tflops": round(kfl[c] / (kms[c] * 1e-3) / 1e12, 3) if kms[c] > 0 else None}
+                                 "avg_us": round(kms[c] / kn[c] * 1e3, 2)}
+            # work of the coupling class is bytes (TB/s), of the others flops
+            kernels[names[c]]["tbs" if names[c] == "solve_coupling" else "tflops"] = (
+                round(rate, 3) if rate is not None else None)
     # the dominant kernel class by device time
     dom = int(np.argmax(kms))
     roof = roofline(names[dom], kms[dom], kfl[dom], kn[dom], pk, pk_src)

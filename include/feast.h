@@ -113,10 +113,11 @@ typedef struct {
   long long factor_flops;   /* algorithmic flops of the factorisation (8 n^3 per layer per node) */
   /* kernel accounting of the call: launches of the library's kernels, and
      with options.profile the summed device time and launch count per class:
-     0 sweep-update GEMM, 1 block-solve GEMM, 2 panel inversion, 3 panel
-     product/packing, 4 Schur complements, 5 solve couplings, 6 FP64
-     refinement residual, 7 FP64-path factor/solve kernels, 8 incremental
-     double-float refinement residual; the rest are zero */
+     0 sweep-update GEMM (wide), 1 block-solve GEMM, 2 panel inversion,
+     3 panel product/packing, 4 Schur complements, 5 solve couplings (work
+     in bytes), 6 FP64 refinement residual, 7 FP64-path factor/solve kernels,
+     8 incremental double-float refinement residual, 9 sweep-update GEMM on
+     the next panel's column tile (narrow); the rest are zero */
   long long gpu_launches;
   double kernel_ms[FEAST_KERNEL_CLASSES];
   long long kernel_launches[FEAST_KERNEL_CLASSES];

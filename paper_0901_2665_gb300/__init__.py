@@ -80,7 +80,7 @@ class feast_info(ctypes.Structure):
 
 
 KERNEL_CLASSES = ["sweep_gemm", "solve_gemm", "panel_inverse", "panel_product", "schur", "solve_coupling",
-                  "fp64_residual", "fp64_path", "ff_residual"]
+                  "fp64_residual", "fp64_path", "ff_residual", "sweep_narrow"]
 
 
 _vp, _i, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double

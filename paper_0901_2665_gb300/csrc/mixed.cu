@@ -1051,8 +1051,9 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
     const int k0 = kp * kPanel, bw = std::min(kPanel, d.n - k0), q = kp & 1;
     const bool last = kp == npan - 1;
     tc::Geom geo{0, d.n, 0, d.nblk64 * 128, (2 * kPanel) / tc::kBlockK, base, skip};
-    prof::begin(s, prof::SWEEP_GEMM);
-    prof::add_work(prof::SWEEP_GEMM, 8.0 * d.n * (64.0 * count) * bw * Ne);
+    const int cls = base > 0 ? prof::SWEEP_NARROW : prof::SWEEP_GEMM;   // the narrow update starts at tile kp+1
+    prof::begin(s, cls);
+    prof::add_work(cls, 8.0 * d.n * (64.0 * count) * bw * Ne);
     cudaError_t err;
     if (tma_rmw) {
       SweepEpiTma epi{mapF, mapFr, layer & 1, layer, d.nz, d.n, k0, bw, last ? 1 : 0, Tc[q], Pv[q]};
@@ -1065,7 +1066,7 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
                    sFr, d.ldF, d.n, k0, bw, Tc[q], Pv[q]};
       err = launch_tc<128, 2>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status);
     }
-    prof::end(s, prof::SWEEP_GEMM);
+    prof::end(s, cls);
     prof::count_launch();
     return err;
   };
@@ -1120,8 +1121,16 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
   const dim3 ggrid(d.nblkCB, cdiv(d.n, 128), nn);
   tc::Geom geo0{0, d.nz * d.n, 0, d.nblkCB * 2 * CB, nk};
   geo0.node_mask = nl.mask;
+  // coupling work is counted in bytes: per entry the right-hand side and the
+  // neighbouring solution (8 B each), g (8 B) and its embedded operand copy
+  // (16 B), plus the 9 coefficients of each row
+  const double couple_fwd_bytes = (double)nn * d.n * ((double)d.k * 40.0 + 72.0);
+  const double couple_bwd_bytes = (double)nn * d.n * ((double)d.k * 32.0 + 72.0);
   // forward sweep
+  prof::begin(s, prof::COUPLE);
+  prof::add_work(prof::COUPLE, couple_fwd_bytes);
   k_mx_couple_fwd<<<cgrid, 128, 0, s>>>(d, 0, Cf, Rreal, Rc, Tout, Gc, Bemb, nl);
+  prof::end(s, prof::COUPLE);
   for (int i = 1; i < d.nz; ++i) {
     SolveEpi<CB> epi{Tout, (long long)d.n * d.k, d.n, d.n, d.k, 1.0f};
     tc::Geom geo = geo0;
@@ -1130,11 +1139,17 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     prof::add_work(prof::SOLVE_GEMM, 8.0 * d.n * (double)d.n * d.k * nn);
     if (launch_tc<2 * CB, 4>(s, ggrid, tmF, tmB, geo, epi, status) != cudaSuccess) return "tcgen05 solve launch failed";
     prof::end(s, prof::SOLVE_GEMM);
+    prof::begin(s, prof::COUPLE);
+    prof::add_work(prof::COUPLE, couple_fwd_bytes);
     k_mx_couple_fwd<<<cgrid, 128, 0, s>>>(d, i, Cf, Rreal, Rc, Tout, Gc, Bemb, nl);
+    prof::end(s, prof::COUPLE);
   }
   // backward sweep: x_i overwrites g_i
   for (int i = d.nz - 1; i >= 0; --i) {
+    prof::begin(s, prof::COUPLE);
+    prof::add_work(prof::COUPLE, couple_bwd_bytes);
     k_mx_couple_bwd<<<cgrid, 128, 0, s>>>(d, i, Cf, Gc, Bemb, nl);
+    prof::end(s, prof::COUPLE);
     SolveEpi<CB> epi{Gc + (long long)i * d.n, d.N * d.k, d.N, d.n, d.k, -1.0f};
     tc::Geom geo = geo0;
     geo.a_row0 = i * d.n;

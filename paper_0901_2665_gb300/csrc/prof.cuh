@@ -11,7 +11,7 @@ namespace feast {
 namespace prof {
 
 enum Cls {
-  SWEEP_GEMM = 0,   // tcgen05 trailing update of the block sweep
+  SWEEP_GEMM = 0,   // tcgen05 trailing update of the block sweep (wide: all but the next panel's tile)
   SOLVE_GEMM = 1,   // tcgen05 block-solve product S' g
   PINV = 2,         // 64 x 64 panel inversion
   PANEL_T = 3,      // T = L Pinv and GEMM operand packing
@@ -20,7 +20,8 @@ enum Cls {
   RESIDUAL = 6,     // FP64 refinement residual
   FP64_SOLVE = 7,   // plain FP64 path: factor and solve kernels
   FF_RESIDUAL = 8,  // incremental refinement residual in double-float
-  NCLS = 9
+  SWEEP_NARROW = 9, // the same update on the next panel's column tile only (critical path)
+  NCLS = 10
 };
 
 void set_enabled(bool on);
