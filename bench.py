@@ -278,12 +278,17 @@ def barrier(world):
         dist.barrier()
 
 
+def _reduce_device():
+    import torch.distributed as dist
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
 def allreduce_max(x, world):
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -293,9 +298,18 @@ def allreduce_sum(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def job_throughput(units_local, t_ms_local, world):
+    """Whole-job rate over all ranks: the units every rank processed divided
+    by the slowest rank's time (max over ranks).  Returns (value per second,
+    t_max in ms, total units)."""
+    t_max = allreduce_max(t_ms_local, world)
+    total = allreduce_sum(units_local, world)
+    return total / (t_max * 1e-3), t_max, total
 
 
 def gpu_uuid():
@@ -380,10 +394,8 @@ def run_ours(args):
     barrier(world)
     clk = clocks.stop() if rank0 else None
     t_ms = ev0.elapsed_time(ev1)
-    t_max = allreduce_max(t_ms, world)
     found = sum(r.m_found for r, ok in results if ok)
-    total_found = allreduce_sum(found, world)
-    value = total_found / (t_max * 1e-3)
+    value, t_max, _ = job_throughput(found, t_ms, world)
     valid = all(ok for _, ok in results)
     last = results[-1][0]
     if not args.profile_timed:
