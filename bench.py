@@ -481,7 +481,7 @@ def run_ours(args):
                    "ir_early": not args.no_ir_early,
                    "l2": "inputs larger than L2 (27 GB of factors per solve)"},
         "valid": valid, "m_found": last.m_found, "loops": last.loops, "resid_max": last.info.resid_max,
-        "ir_steps_max": last.info.ir_steps_max,
+        "ir_steps_max": last.info.ir_steps_max, "sweep_graphs": last.info.sweep_graphs,
         "trace_rel_change": [float(x) for x in last.info.rel_change[:last.loops]],
         "phase_ms": {"factor": last.info.t_factor_ms, "solve": last.info.t_solve_ms, "rayleigh_ritz": last.info.t_rr_ms},
         "block_lu_tflops": lu, "block_lu_frac_tf32": (lu / tf32_peak) if lu else None,

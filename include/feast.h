@@ -123,6 +123,8 @@ typedef struct {
   long long kernel_launches[FEAST_KERNEL_CLASSES];
   double kernel_flops[FEAST_KERNEL_CLASSES];   /* algorithmic flops of each class (complex FMA = 8 real flops;
                                a TF32 product counts once) */
+  long long sweep_graphs;   /* MIXED: forward/backward sweep pairs replayed from captured CUDA graphs
+                               (0 with options.profile, which times the kernels one by one) */
 } feast_info;
 
 /* Fills *opt with the defaults listed above. */

@@ -76,7 +76,8 @@ class feast_info(ctypes.Structure):
                 ("factor_flops", ctypes.c_longlong), ("gpu_launches", ctypes.c_longlong),
                 ("kernel_ms", ctypes.c_double * KERNEL_CLASS_SLOTS),
                 ("kernel_launches", ctypes.c_longlong * KERNEL_CLASS_SLOTS),
-                ("kernel_flops", ctypes.c_double * KERNEL_CLASS_SLOTS)]
+                ("kernel_flops", ctypes.c_double * KERNEL_CLASS_SLOTS),
+                ("sweep_graphs", ctypes.c_longlong)]
 
 
 KERNEL_CLASSES = ["sweep_gemm", "solve_gemm", "panel_inverse", "panel_product", "schur", "solve_coupling",

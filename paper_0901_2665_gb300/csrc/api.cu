@@ -273,6 +273,7 @@ void solve_nodes(feast_handle* h, const OpView& op, int Ne, int precision, const
     if (msg) fail(FEAST_ERR_CUDA, msg);
     h->info.ir_steps_max = std::max(h->info.ir_steps_max, st.steps_max);
     if (ir_tol <= h->opt.ir_tol) h->info.ir_resid_max = std::max(h->info.ir_resid_max, st.resid_max);
+    h->info.sweep_graphs += st.graph_sweeps;
   }
 }
 

@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -900,9 +901,10 @@ bool make_map(CUtensorMap* map, const float* base, long long inner, long long ro
   return make_map_2d(map, base, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, inner, rows, ld, box_rows);
 }
 
+// Shared-memory attribute of a GEMM instantiation, set once per process (and
+// before any stream capture: it is not a stream operation).
 template <int BN, int STAGES, class Epi>
-cudaError_t launch_tc(cudaStream_t s, dim3 grid, const CUtensorMap& a, const CUtensorMap& b, tc::Geom geo,
-                      const Epi& epi, int* status) {
+cudaError_t tc_attr() {
   constexpr size_t smem = tc::smem_bytes<BN, STAGES, Epi>();
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
@@ -910,7 +912,14 @@ cudaError_t launch_tc(cudaStream_t s, dim3 grid, const CUtensorMap& a, const CUt
     attr_err =
         cudaFuncSetAttribute(tc::k_tc_gemm<BN, STAGES, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
-  if (attr_err != cudaSuccess) return attr_err;
+  return attr_err;
+}
+
+template <int BN, int STAGES, class Epi>
+cudaError_t launch_tc(cudaStream_t s, dim3 grid, const CUtensorMap& a, const CUtensorMap& b, tc::Geom geo,
+                      const Epi& epi, int* status) {
+  constexpr size_t smem = tc::smem_bytes<BN, STAGES, Epi>();
+  if (const cudaError_t e = tc_attr<BN, STAGES, Epi>()) return e;
   tc::k_tc_gemm<BN, STAGES, Epi><<<grid, tc::kThreads, smem, s>>>(a, b, geo, epi, status);
   return cudaGetLastError();
 }
@@ -941,6 +950,17 @@ T* buf(MixedWork& w, int idx) {
   return static_cast<T*>(w.bufs[idx]);
 }
 
+// The stream captures are recorded on: the caller's stream may be the legacy
+// default stream, which cannot be captured; the graph is then launched into
+// the caller's stream.
+cudaStream_t capture_stream(MixedWork& w) {
+  if (!w.cap && cudaStreamCreateWithFlags(&w.cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    w.cap = nullptr;
+  }
+  return w.cap;
+}
+
 Dims make_dims(Grid g, int Ne, int k, int cb = 0) {
   Dims d;
   d.nx = g.nx;
@@ -961,6 +981,15 @@ Dims make_dims(Grid g, int Ne, int k, int cb = 0) {
 }  // namespace
 
 void MixedWork::release() {
+  if (factor_graph) cudaGraphExecDestroy(factor_graph);
+  factor_graph = nullptr;
+  if (cap) cudaStreamDestroy(cap);
+  cap = nullptr;
+  for (int g = 0; g < kSweepGraphs; ++g) {
+    if (graphs.exec[g]) cudaGraphExecDestroy(graphs.exec[g]);
+    graphs.exec[g] = nullptr;
+    graphs.used[g] = 0;
+  }
   for (int i = 0; i < 16; ++i) {
     if (bufs[i]) cudaFree(bufs[i]);
     bufs[i] = nullptr;
@@ -1007,92 +1036,143 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
   float* Fr = buf<float>(w, B_F);    // TF32-rounded S'_i of every layer (solve operand)
   float* F = buf<float>(w, B_FW);    // fp32 working layers (ping-pong)
   f2* Cf = buf<f2>(w, B_CF);
-  k_mx_coef<<<dim3((unsigned)std::min<long long>(4096, (27 * d.N + 255) / 256), Ne), 256, 0, s>>>(d, Z, A27, B27, Cf);
-  prof::count_launch();
-  float* Aop[2] = {buf<float>(w, B_AOP), buf<float>(w, B_AOP) + aop_sz};
-  float* Bop[2] = {buf<float>(w, B_BOP), buf<float>(w, B_BOP) + bop_sz};
-  f2* Tc[2] = {buf<f2>(w, B_TC), buf<f2>(w, B_TC) + tc_sz};
-  f2* Pv[2] = {buf<f2>(w, B_PINV), buf<f2>(w, B_PINV) + pinv_sz};
-  CUtensorMap tmA[2], tmB[2];
-  for (int q = 0; q < 2; ++q) {
-    if (!make_map(&tmA[q], Aop[q], 2 * kPanel, (long long)Ne * d.n, 2 * kPanel, 128)) return "tensor map (Aop) rejected";
-    if (!make_map(&tmB[q], Bop[q], 2 * kPanel, (long long)Ne * d.nblk64 * 128, 2 * kPanel, 128))
-      return "tensor map (Bop) rejected";
-  }
-  const long long sF = 2LL * d.n * d.ldF;
-  const long long sFr = (long long)d.nz * d.n * d.ldF;
-  const int npan = d.nblk64;
-  auto panel = [&](cudaStream_t st, int layer, int kp) {
-    const int k0 = kp * kPanel, bw = std::min(kPanel, d.n - k0), q = kp & 1;
-    prof::begin(st, prof::PINV);
-    prof::add_work(prof::PINV, 8.0 * kPanel * kPanel * kPanel * Ne);
-    k_mx_pinv<<<Ne, kPinvThreads, 0, st>>>(d, layer, k0, bw, F, Pv[q], status);
-    prof::end(st, prof::PINV);
-    prof::begin(st, prof::PANEL_T);
-    prof::add_work(prof::PANEL_T, 8.0 * d.n * kPanel * kPanel * Ne);
-    k_mx_panel_T<<<dim3(cdiv(d.n, kRowsPerPanelCta), Ne), 256, 0, st>>>(d, layer, k0, bw, F, Pv[q], Aop[q], Bop[q],
-                                                                      Tc[q]);
-    prof::end(st, prof::PANEL_T);
-    prof::count_launch(2);
-  };
-  // TMA-staged read-modify-write of S when a 64-column tile never straddles
-  // the real/imaginary split of a row
-  const bool tma_rmw = d.n % 64 == 0;
-  CUtensorMap mapF{}, mapFr{};
-  if (tma_rmw) {
-    if (!make_map_3d(&mapF, F, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 2LL * d.n, d.n, 2LL * Ne, d.ldF,
-                     (long long)d.n * d.ldF, 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !make_map_3d(&mapFr, Fr, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 2LL * d.n, d.n, (long long)Ne * d.nz, d.ldF,
-                     (long long)d.n * d.ldF, 32, 128, CU_TENSOR_MAP_SWIZZLE_128B))
-      return "tensor map (working layers) rejected";
-  }
-  // trailing update of panel kp over the column tiles [base, base + count) except `skip`
-  auto update = [&](int layer, int kp, int base, int count, int skip) -> cudaError_t {
-    const int k0 = kp * kPanel, bw = std::min(kPanel, d.n - k0), q = kp & 1;
-    const bool last = kp == npan - 1;
-    tc::Geom geo{0, d.n, 0, d.nblk64 * 128, (2 * kPanel) / tc::kBlockK, base, skip};
-    const int cls = base > 0 ? prof::SWEEP_NARROW : prof::SWEEP_GEMM;   // the narrow update starts at tile kp+1
-    prof::begin(s, cls);
-    prof::add_work(cls, 8.0 * d.n * (64.0 * count) * bw * Ne);
-    cudaError_t err;
-    if (tma_rmw) {
-      SweepEpiTma epi{mapF, mapFr, layer & 1, layer, d.nz, d.n, k0, bw, last ? 1 : 0, Tc[q], Pv[q]};
-      // the narrow update (one column tile, few CTAs, on the critical path)
-      // pipelines its K-blocks; the wide one keeps two CTAs per SM instead
-      err = count == 1 ? launch_tc<128, 4>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status)
-                       : launch_tc<128, 1>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status);
-    } else {
-      SweepEpi epi{F + (long long)(layer & 1) * d.n * d.ldF, sF, last ? Fr + (long long)layer * d.n * d.ldF : nullptr,
-                   sFr, d.ldF, d.n, k0, bw, Tc[q], Pv[q]};
-      err = launch_tc<128, 2>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status);
-    }
-    prof::end(s, cls);
+  // The launches of the factorisation (both streams).  Without kernel timing
+  // they are captured once into a CUDA graph (node priorities kept, so the
+  // lookahead chain still goes first) and replayed while the shape, the
+  // operator and the work buffers stay the same.
+  auto body = [&](cudaStream_t s) -> const char* {
+    k_mx_coef<<<dim3((unsigned)std::min<long long>(4096, (27 * d.N + 255) / 256), Ne), 256, 0, s>>>(d, Z, A27, B27, Cf);
     prof::count_launch();
-    return err;
-  };
-  for (int layer = 0; layer < d.nz; ++layer) {
-    prof::begin(s, prof::SCHUR);
-    prof::add_work(prof::SCHUR, (layer > 0 ? 144.0 : 0.0) * d.n * (double)d.n * Ne);
-    if (layer > 0)
-      k_mx_schur1<<<dim3(cdiv(d.n, 256), d.n, Ne), 256, 0, s>>>(d, layer, Cf, F, buf<float>(w, B_T1));
-    k_mx_schur2<<<dim3(cdiv(d.n, 256), d.n, Ne), 256, 0, s>>>(d, layer, Cf, buf<float>(w, B_T1), F);
-    prof::end(s, prof::SCHUR);
-    prof::count_launch(layer > 0 ? 2 : 1);
-    panel(s, layer, 0);
-    for (int kp = 0; kp < npan; ++kp) {
-      if (kp + 1 < npan) {
-        // narrow update: the next panel's columns first ...
-        if (update(layer, kp, kp + 1, 1, -1) != cudaSuccess) return "tcgen05 sweep-update launch failed";
-        cudaEventRecord(w.ev_narrow, s);
-        // ... so its inversion and product overlap the wide update
-        cudaStreamWaitEvent(s2, w.ev_narrow, 0);
-        panel(s2, layer, kp + 1);
-        cudaEventRecord(w.ev_side, s2);
-        if (npan > 1 && update(layer, kp, 0, npan - 1, kp + 1) != cudaSuccess)
-          return "tcgen05 sweep-update launch failed";
-        cudaStreamWaitEvent(s, w.ev_side, 0);
+    float* Aop[2] = {buf<float>(w, B_AOP), buf<float>(w, B_AOP) + aop_sz};
+    float* Bop[2] = {buf<float>(w, B_BOP), buf<float>(w, B_BOP) + bop_sz};
+    f2* Tc[2] = {buf<f2>(w, B_TC), buf<f2>(w, B_TC) + tc_sz};
+    f2* Pv[2] = {buf<f2>(w, B_PINV), buf<f2>(w, B_PINV) + pinv_sz};
+    CUtensorMap tmA[2], tmB[2];
+    for (int q = 0; q < 2; ++q) {
+      if (!make_map(&tmA[q], Aop[q], 2 * kPanel, (long long)Ne * d.n, 2 * kPanel, 128)) return "tensor map (Aop) rejected";
+      if (!make_map(&tmB[q], Bop[q], 2 * kPanel, (long long)Ne * d.nblk64 * 128, 2 * kPanel, 128))
+        return "tensor map (Bop) rejected";
+    }
+    const long long sF = 2LL * d.n * d.ldF;
+    const long long sFr = (long long)d.nz * d.n * d.ldF;
+    const int npan = d.nblk64;
+    auto panel = [&](cudaStream_t st, int layer, int kp) {
+      const int k0 = kp * kPanel, bw = std::min(kPanel, d.n - k0), q = kp & 1;
+      prof::begin(st, prof::PINV);
+      prof::add_work(prof::PINV, 8.0 * kPanel * kPanel * kPanel * Ne);
+      k_mx_pinv<<<Ne, kPinvThreads, 0, st>>>(d, layer, k0, bw, F, Pv[q], status);
+      prof::end(st, prof::PINV);
+      prof::begin(st, prof::PANEL_T);
+      prof::add_work(prof::PANEL_T, 8.0 * d.n * kPanel * kPanel * Ne);
+      k_mx_panel_T<<<dim3(cdiv(d.n, kRowsPerPanelCta), Ne), 256, 0, st>>>(d, layer, k0, bw, F, Pv[q], Aop[q], Bop[q],
+                                                                        Tc[q]);
+      prof::end(st, prof::PANEL_T);
+      prof::count_launch(2);
+    };
+    // TMA-staged read-modify-write of S when a 64-column tile never straddles
+    // the real/imaginary split of a row
+    const bool tma_rmw = d.n % 64 == 0;
+    CUtensorMap mapF{}, mapFr{};
+    if (tma_rmw) {
+      if (!make_map_3d(&mapF, F, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 2LL * d.n, d.n, 2LL * Ne, d.ldF,
+                       (long long)d.n * d.ldF, 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) ||
+          !make_map_3d(&mapFr, Fr, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 2LL * d.n, d.n, (long long)Ne * d.nz, d.ldF,
+                       (long long)d.n * d.ldF, 32, 128, CU_TENSOR_MAP_SWIZZLE_128B))
+        return "tensor map (working layers) rejected";
+    }
+    // trailing update of panel kp over the column tiles [base, base + count) except `skip`
+    auto update = [&](int layer, int kp, int base, int count, int skip) -> cudaError_t {
+      const int k0 = kp * kPanel, bw = std::min(kPanel, d.n - k0), q = kp & 1;
+      const bool last = kp == npan - 1;
+      tc::Geom geo{0, d.n, 0, d.nblk64 * 128, (2 * kPanel) / tc::kBlockK, base, skip};
+      const int cls = base > 0 ? prof::SWEEP_NARROW : prof::SWEEP_GEMM;   // the narrow update starts at tile kp+1
+      prof::begin(s, cls);
+      prof::add_work(cls, 8.0 * d.n * (64.0 * count) * bw * Ne);
+      cudaError_t err;
+      if (tma_rmw) {
+        SweepEpiTma epi{mapF, mapFr, layer & 1, layer, d.nz, d.n, k0, bw, last ? 1 : 0, Tc[q], Pv[q]};
+        // the narrow update (one column tile, few CTAs, on the critical path)
+        // pipelines its K-blocks; the wide one keeps two CTAs per SM instead
+        err = count == 1 ? launch_tc<128, 4>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status)
+                         : launch_tc<128, 1>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status);
       } else {
-        if (update(layer, kp, 0, npan, -1) != cudaSuccess) return "tcgen05 sweep-update launch failed";
+        SweepEpi epi{F + (long long)(layer & 1) * d.n * d.ldF, sF, last ? Fr + (long long)layer * d.n * d.ldF : nullptr,
+                     sFr, d.ldF, d.n, k0, bw, Tc[q], Pv[q]};
+        err = launch_tc<128, 2>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status);
+      }
+      prof::end(s, cls);
+      prof::count_launch();
+      return err;
+    };
+    for (int layer = 0; layer < d.nz; ++layer) {
+      prof::begin(s, prof::SCHUR);
+      prof::add_work(prof::SCHUR, (layer > 0 ? 144.0 : 0.0) * d.n * (double)d.n * Ne);
+      if (layer > 0)
+        k_mx_schur1<<<dim3(cdiv(d.n, 256), d.n, Ne), 256, 0, s>>>(d, layer, Cf, F, buf<float>(w, B_T1));
+      k_mx_schur2<<<dim3(cdiv(d.n, 256), d.n, Ne), 256, 0, s>>>(d, layer, Cf, buf<float>(w, B_T1), F);
+      prof::end(s, prof::SCHUR);
+      prof::count_launch(layer > 0 ? 2 : 1);
+      panel(s, layer, 0);
+      for (int kp = 0; kp < npan; ++kp) {
+        if (kp + 1 < npan) {
+          // narrow update: the next panel's columns first ...
+          if (update(layer, kp, kp + 1, 1, -1) != cudaSuccess) return "tcgen05 sweep-update launch failed";
+          cudaEventRecord(w.ev_narrow, s);
+          // ... so its inversion and product overlap the wide update
+          cudaStreamWaitEvent(s2, w.ev_narrow, 0);
+          panel(s2, layer, kp + 1);
+          cudaEventRecord(w.ev_side, s2);
+          if (npan > 1 && update(layer, kp, 0, npan - 1, kp + 1) != cudaSuccess)
+            return "tcgen05 sweep-update launch failed";
+          cudaStreamWaitEvent(s, w.ev_side, 0);
+        } else {
+          if (update(layer, kp, 0, npan, -1) != cudaSuccess) return "tcgen05 sweep-update launch failed";
+        }
+      }
+    }
+    return nullptr;
+  };
+  if (prof::enabled()) {
+    if (const char* m = body(s)) return m;
+  } else {
+    const unsigned long long key[kSweepKey] = {
+        (unsigned long long)d.nx | ((unsigned long long)d.ny << 20) | ((unsigned long long)d.nz << 40),
+        (unsigned long long)Ne | ((unsigned long long)d.ldF << 20),
+        (unsigned long long)(uintptr_t)Z, (unsigned long long)(uintptr_t)A27, (unsigned long long)(uintptr_t)B27,
+        (unsigned long long)(uintptr_t)status, (unsigned long long)(uintptr_t)w.bufs[B_F],
+        (unsigned long long)(uintptr_t)w.bufs[B_FW], (unsigned long long)(uintptr_t)w.bufs[B_T1],
+        (unsigned long long)(uintptr_t)w.bufs[B_AOP], (unsigned long long)(uintptr_t)w.bufs[B_BOP],
+        (unsigned long long)(uintptr_t)w.bufs[B_TC], (unsigned long long)(uintptr_t)w.bufs[B_PINV],
+        (unsigned long long)(uintptr_t)w.bufs[B_CF], (unsigned long long)(uintptr_t)s2, 2ULL};
+    if (w.factor_graph && std::memcmp(w.factor_key, key, sizeof(key)) == 0) {
+      if (cudaGraphLaunch(w.factor_graph, s) != cudaSuccess) return "factor graph launch failed";
+      prof::count_launch((int)w.factor_launches);
+      ++w.factor_replays;
+    } else {
+      if (w.factor_graph) cudaGraphExecDestroy(w.factor_graph);
+      w.factor_graph = nullptr;
+      if (tc_attr<128, 1, SweepEpiTma>() || tc_attr<128, 4, SweepEpiTma>() || tc_attr<128, 2, SweepEpi>())
+        return "tcgen05 sweep-update attribute rejected";
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      const long long launches0 = prof::launches();
+      cudaStream_t cs = capture_stream(w);
+      const bool capturing = cs && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      const char* msg = capturing ? body(cs) : "capture not started";
+      const cudaError_t end = capturing ? cudaStreamEndCapture(cs, &graph) : cudaErrorUnknown;
+      if (msg || end != cudaSuccess || !graph ||
+          cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        prof::count_launch((int)(launches0 - prof::launches()));   // nothing of the capture ran
+        if (capturing && msg) return msg;
+        if (const char* m = body(s)) return m;   // direct launches
+      } else {
+        cudaGraphDestroy(graph);
+        w.factor_graph = exec;
+        std::memcpy(w.factor_key, key, sizeof(key));
+        w.factor_launches = prof::launches() - launches0;
+        if (cudaGraphLaunch(exec, s) != cudaSuccess) return "factor graph launch failed";
       }
     }
   }
@@ -1224,9 +1304,23 @@ int tuned_cb(cudaStream_t s, const Dims& d, MixedWork& w, int* status) {
   return best_cb;
 }
 
+const char* solve_direct(cudaStream_t s, const Dims& d, const cplx* Z, const double* A27, const double* B27,
+                         MixedWork& w, const double* Rreal, const f2* Rc, const NodeList& nl, int* status) {
+  switch (d.CB) {
+    case 8: return solve_sweeps<8>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+    case 16: return solve_sweeps<16>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+    case 32: return solve_sweeps<32>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+    default: return solve_sweeps<64>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+  }
+}
+
+// One pair of sweeps.  Without kernel timing the ~4 nz launches are replayed
+// from a CUDA graph captured on first use (key: shape, tile width, node mask
+// and every pointer the launches read or write); a capture that fails falls
+// back to direct launches.
 const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const double* A27, const double* B27,
                        MixedWork& w, const double* Rreal, const f2* Rc, const std::vector<int>& active,
-                       int* status) {
+                       MixedSolveStats* stats, int* status) {
   NodeList nl{0, 0ULL};
   for (int e = 0; e < d.Ne; ++e)
     if (active[e]) {
@@ -1234,12 +1328,55 @@ const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const doubl
       ++nl.count;
     }
   if (nl.count == 0) return nullptr;
-  switch (d.CB) {
-    case 8: return solve_sweeps<8>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
-    case 16: return solve_sweeps<16>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
-    case 32: return solve_sweeps<32>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
-    default: return solve_sweeps<64>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+  if (prof::enabled()) return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+  const unsigned long long key[kSweepKey] = {
+      (unsigned long long)d.nx | ((unsigned long long)d.ny << 20) | ((unsigned long long)d.nz << 40),
+      (unsigned long long)d.k | ((unsigned long long)d.CB << 20) | ((unsigned long long)d.Ne << 40),
+      nl.mask,
+      (unsigned long long)(uintptr_t)Rreal, (unsigned long long)(uintptr_t)Rc, (unsigned long long)(uintptr_t)Z,
+      (unsigned long long)(uintptr_t)A27, (unsigned long long)(uintptr_t)B27, (unsigned long long)(uintptr_t)status,
+      (unsigned long long)(uintptr_t)w.bufs[B_F], (unsigned long long)(uintptr_t)w.bufs[B_GC],
+      (unsigned long long)(uintptr_t)w.bufs[B_TOUT], (unsigned long long)(uintptr_t)w.bufs[B_BEMB],
+      (unsigned long long)(uintptr_t)w.bufs[B_CF], (unsigned long long)d.ldF, 1ULL};
+  SweepGraphCache& gc = w.graphs;
+  ++gc.clock;
+  for (int g = 0; g < kSweepGraphs; ++g) {
+    if (!gc.exec[g] || std::memcmp(gc.key[g], key, sizeof(key)) != 0) continue;
+    gc.used[g] = gc.clock;
+    if (cudaGraphLaunch(gc.exec[g], s) != cudaSuccess) return "sweep graph launch failed";
+    prof::count_launch(4 * d.nz);
+    if (stats) ++stats->graph_sweeps;
+    return nullptr;
   }
+  // capture
+  cudaGraph_t graph = nullptr;
+  cudaStream_t cs = capture_stream(w);
+  if (!cs || cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+  }
+  const long long launches0 = prof::launches();
+  const char* msg = solve_direct(cs, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+  const cudaError_t end = cudaStreamEndCapture(cs, &graph);
+  cudaGraphExec_t exec = nullptr;
+  if (msg || end != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    prof::count_launch(launches0 - prof::launches());   // nothing of the capture ran
+    if (msg) return msg;
+    return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+  }
+  cudaGraphDestroy(graph);
+  int slot = 0;
+  for (int g = 1; g < kSweepGraphs; ++g)
+    if (!gc.exec[g] || (gc.exec[slot] && gc.used[g] < gc.used[slot])) slot = g;
+  if (gc.exec[slot]) cudaGraphExecDestroy(gc.exec[slot]);
+  gc.exec[slot] = exec;
+  std::memcpy(gc.key[slot], key, sizeof(key));
+  gc.used[slot] = gc.clock;
+  if (cudaGraphLaunch(exec, s) != cudaSuccess) return "sweep graph launch failed";
+  if (stats) ++stats->graph_sweeps;
+  return nullptr;
 }
 
 }  // namespace
@@ -1277,7 +1414,7 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
   std::vector<double> rel(Ne, 0.0), final_rel(Ne, 0.0);
   const int acc_blocks = (int)std::min<long long>(4096, (sG + 255) / 256);
   // first solve: Q_e = M~^{-1} RHS
-  if (const char* m = solve_once(s, d, Z, A27, B27, w, RHS, nullptr, active, status)) return m;
+  if (const char* m = solve_once(s, d, Z, A27, B27, w, RHS, nullptr, active, stats, status)) return m;
   k_mx_accumulate<<<dim3(acc_blocks, Ne), 256, 0, s>>>(sG, 1, buf<f2>(w, B_GC), G, buf<int>(w, B_ACTIVE));
   prof::count_launch();
   int steps = 0;
@@ -1322,7 +1459,8 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
     if (steps >= ir_max) return "iterative refinement did not reach the tolerance";
     cudaMemcpyAsync(w.bufs[B_ACTIVE], active.data(), sizeof(int) * Ne, cudaMemcpyHostToDevice, s);
     // only the unconverged nodes are swept again
-    if (const char* m = solve_once(s, d, Z, A27, B27, w, nullptr, buf<f2>(w, B_RC), active, status)) return m;
+    if (const char* m = solve_once(s, d, Z, A27, B27, w, nullptr, buf<f2>(w, B_RC), active, stats, status))
+      return m;
     k_mx_accumulate<<<dim3(acc_blocks, Ne), 256, 0, s>>>(sG, 0, buf<f2>(w, B_GC), G, buf<int>(w, B_ACTIVE));
     prof::count_launch();
     ++steps;

@@ -10,6 +10,19 @@ namespace feast {
 struct MixedSolveStats {
   int steps_max = 0;        // most refinement steps taken by one node solve
   double resid_max = 0.0;   // worst final relative residual ||R||_F / ||RHS||_F
+  long long graph_sweeps = 0;   // pairs of sweeps run from a captured CUDA graph
+};
+
+// Instantiated CUDA graphs of the node-solve sweeps (one forward and one
+// backward sweep over all layers, ~4 launches a layer), keyed by everything
+// the captured launches depend on; least recently used entry replaced.
+constexpr int kSweepGraphs = 8;
+constexpr int kSweepKey = 16;
+struct SweepGraphCache {
+  cudaGraphExec_t exec[kSweepGraphs] = {};
+  unsigned long long key[kSweepGraphs][kSweepKey] = {};
+  unsigned long long used[kSweepGraphs] = {};
+  unsigned long long clock = 0;
 };
 
 struct MixedWork {
@@ -19,6 +32,12 @@ struct MixedWork {
   int bemb_k = 0;                         // right-hand sides the RHS operand was zeroed for
   cudaStream_t side = nullptr;            // lookahead stream of the factorisation
   cudaEvent_t ev_narrow = nullptr, ev_side = nullptr;
+  SweepGraphCache graphs;
+  cudaStream_t cap = nullptr;                  // non-blocking stream that captures (the caller's may be the legacy one)
+  cudaGraphExec_t factor_graph = nullptr;      // the captured factorisation
+  unsigned long long factor_key[kSweepKey] = {};
+  long long factor_launches = 0;               // kernels in it
+  long long factor_replays = 0;
   void release();
 };
 

@@ -52,3 +52,25 @@ def test_contour_rejects_bad_arguments():
         F.feast_contour(2.0, 1.0, 8)
     with pytest.raises(F.FeastError):
         F.feast_contour(1.0, 2.0, 0)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of feast_options and feast_info have the C layout
+    (size and field offsets from a C program built against include/feast.h)."""
+    import ctypes
+
+    import paper_0901_2665_gb300 as F
+    src = tmp_path / "sizes.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "feast.h"\n'
+        'int main(void) {\n'
+        '  printf("%zu %zu %zu %zu %zu\\n", sizeof(feast_options), sizeof(feast_info),\n'
+        '         offsetof(feast_info, factor_flops), offsetof(feast_info, kernel_flops),\n'
+        '         offsetof(feast_info, sweep_graphs));\n'
+        '  return 0;\n}\n')
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(F.feast_options), ctypes.sizeof(F.feast_info), F.feast_info.factor_flops.offset,
+            F.feast_info.kernel_flops.offset, F.feast_info.sweep_graphs.offset]
+    assert got == want
