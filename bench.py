@@ -418,7 +418,9 @@ def run_ours(args):
         res_h = torch.zeros(M0, dtype=torch.float64).pin_memory()
         hop = F.make_operator(op.nx, op.ny, op.nz, A_h, B_h)
         h_e2e = F.Handle(precision=prec, seed=Y_SEED, stream=stream.cuda_stream, ir_early=not args.no_ir_early)
-        h_e2e.feast_solve(hop, iv["lmin"], iv["lmax"], M0, Ne, wl.tol, None, lam_h, X_h, res_h, allow=())
+        # two untimed solves: the second captures the factorisation's graph
+        for _ in range(2):
+            h_e2e.feast_solve(hop, iv["lmin"], iv["lmax"], M0, Ne, wl.tol, None, lam_h, X_h, res_h, allow=())
         barrier(world)
         t0 = time.perf_counter()
         e2e_found = 0

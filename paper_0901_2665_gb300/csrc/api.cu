@@ -300,8 +300,8 @@ void rayleigh_ritz_dev(feast_handle* h, const OpView& op, const double* Q, int M
   stencil_apply(h->stream, op.g, op.B27, Q, N, h->BQf.as<double>(), N, M0);
   double* AQ = AQout ? AQout : h->AQ.as<double>();
   double* BQ = BQout ? BQout : h->BQ.as<double>();
-  gram(h->stream, N, M0, M0, Q, h->AQf.as<double>(), h->part.as<double>(), AQ);
-  gram(h->stream, N, M0, M0, Q, h->BQf.as<double>(), h->part.as<double>(), BQ);
+  gram(h->stream, N, M0, M0, Q, h->AQf.as<double>(), h->part.as<double>(), AQ, true);   // Q^T (A Q), A symmetric
+  gram(h->stream, N, M0, M0, Q, h->BQf.as<double>(), h->part.as<double>(), BQ, true);
   reduced_eig(h->stream, M0, AQ, BQ, eps, h->Phi.as<double>(), h->work.as<double>(), h->status.as<int>());
   dgemm_tall(h->stream, N, M0, M0, Q, h->Phi.as<double>(), X);
 }
@@ -702,6 +702,9 @@ feast_status feast_solve_batched(feast_handle* h, int count, const feast_operato
         cudaStreamDestroy(st);
         return;
       }
+      // the instances are factored and swept once each: graph captures would
+      // not be replayed, and the concurrent workers keep the GPU busy anyway
+      sub->mixed.use_graphs = false;
       for (int j; (j = next.fetch_add(1)) < count;) {
         const int i = order[j];
         statuses[i] = feast_solve(sub, &ops[i], lmin[i], lmax[i], M0[i], Ne, tol, Y0 ? Y0[i] : nullptr, lambda[i],

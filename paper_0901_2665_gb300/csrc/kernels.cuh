@@ -55,8 +55,10 @@ void solve_fp64(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27
 // out (k1 x k2, col-major, ld k1) = X^T Y, X: N x k1, Y: N x k2 (col-major, ld N).
 // partial: scratch of gram_partial_elems(N, k1, k2) doubles.  Deterministic.
 long long gram_partial_elems(long long N, int k1, int k2);
+// symmetric: X^T Y is symmetric (Y = C X with C symmetric, k1 == k2); only
+// the tiles on and above the diagonal are computed and the rest mirrored.
 void gram(cudaStream_t s, long long N, int k1, int k2, const double* X, const double* Y, double* partial,
-          double* out);
+          double* out, bool symmetric = false);
 // C (N x k, ld N) = Q (N x m, ld N) * P (m x k, ld m).
 void dgemm_tall(cudaStream_t s, long long N, int m, int k, const double* Q, const double* P, double* C);
 // Reduced generalized eigensolve A_Q Phi = eps B_Q Phi (two-stage Jacobi), m <= 128.

@@ -1132,7 +1132,7 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
     }
     return nullptr;
   };
-  if (prof::enabled()) {
+  if (prof::enabled() || !w.use_graphs) {
     if (const char* m = body(s)) return m;
   } else {
     const unsigned long long key[kSweepKey] = {
@@ -1148,6 +1148,11 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
       if (cudaGraphLaunch(w.factor_graph, s) != cudaSuccess) return "factor graph launch failed";
       prof::count_launch((int)w.factor_launches);
       ++w.factor_replays;
+    } else if (std::memcmp(w.factor_seen, key, sizeof(key)) != 0) {
+      // first factorisation with this key: direct launches (a one-off shape
+      // would pay for a capture it never replays)
+      std::memcpy(w.factor_seen, key, sizeof(key));
+      if (const char* m = body(s)) return m;
     } else {
       if (w.factor_graph) cudaGraphExecDestroy(w.factor_graph);
       w.factor_graph = nullptr;
@@ -1328,7 +1333,7 @@ const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const doubl
       ++nl.count;
     }
   if (nl.count == 0) return nullptr;
-  if (prof::enabled()) return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+  if (prof::enabled() || !w.use_graphs) return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
   const unsigned long long key[kSweepKey] = {
       (unsigned long long)d.nx | ((unsigned long long)d.ny << 20) | ((unsigned long long)d.nz << 40),
       (unsigned long long)d.k | ((unsigned long long)d.CB << 20) | ((unsigned long long)d.Ne << 40),
@@ -1348,7 +1353,15 @@ const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const doubl
     if (stats) ++stats->graph_sweeps;
     return nullptr;
   }
-  // capture
+  // first sighting of this key: run directly and remember it
+  bool seen = false;
+  for (int g = 0; g < kSweepGraphs && !seen; ++g) seen = std::memcmp(gc.seen[g], key, sizeof(key)) == 0;
+  if (!seen) {
+    std::memcpy(gc.seen[gc.seen_next], key, sizeof(key));
+    gc.seen_next = (gc.seen_next + 1) % kSweepGraphs;
+    return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+  }
+  // second sighting: capture
   cudaGraph_t graph = nullptr;
   cudaStream_t cs = capture_stream(w);
   if (!cs || cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {

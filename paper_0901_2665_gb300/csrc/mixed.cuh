@@ -15,7 +15,9 @@ struct MixedSolveStats {
 
 // Instantiated CUDA graphs of the node-solve sweeps (one forward and one
 // backward sweep over all layers, ~4 launches a layer), keyed by everything
-// the captured launches depend on; least recently used entry replaced.
+// the captured launches depend on; least recently used entry replaced.  A
+// key is captured the second time it is seen (a capture and instantiation
+// cost more than one direct run, so one-off shapes stay direct).
 constexpr int kSweepGraphs = 8;
 constexpr int kSweepKey = 16;
 struct SweepGraphCache {
@@ -23,6 +25,8 @@ struct SweepGraphCache {
   unsigned long long key[kSweepGraphs][kSweepKey] = {};
   unsigned long long used[kSweepGraphs] = {};
   unsigned long long clock = 0;
+  unsigned long long seen[kSweepGraphs][kSweepKey] = {};   // keys run once, directly
+  int seen_next = 0;
 };
 
 struct MixedWork {
@@ -33,9 +37,11 @@ struct MixedWork {
   cudaStream_t side = nullptr;            // lookahead stream of the factorisation
   cudaEvent_t ev_narrow = nullptr, ev_side = nullptr;
   SweepGraphCache graphs;
+  bool use_graphs = true;                      // off for the workers of a batched call (one-off instances)
   cudaStream_t cap = nullptr;                  // non-blocking stream that captures (the caller's may be the legacy one)
   cudaGraphExec_t factor_graph = nullptr;      // the captured factorisation
   unsigned long long factor_key[kSweepKey] = {};
+  unsigned long long factor_seen[kSweepKey] = {};   // last factorisation run directly
   long long factor_launches = 0;               // kernels in it
   long long factor_replays = 0;
   void release();

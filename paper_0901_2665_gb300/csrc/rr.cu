@@ -15,13 +15,26 @@ namespace {
 constexpr int kGramTile = 64;
 constexpr int kGramRows = 4096;   // rows per partial sum (split-K chunk)
 
-// partial[chunk][a + b*k1] = sum_{r in chunk} X[r, a] Y[r, b]
+// partial[chunk][a + b*k1] = sum_{r in chunk} X[r, a] Y[r, b].  With sym set
+// the product is symmetric (X^T C X for a symmetric C): blockIdx.x enumerates
+// only the tiles on and above the diagonal, and the reduction mirrors them.
 __global__ void __launch_bounds__(256) k_gram_partial(long long N, int k1, int k2, const double* __restrict__ X,
-                                                      const double* __restrict__ Y, double* __restrict__ partial) {
+                                                      const double* __restrict__ Y, double* __restrict__ partial,
+                                                      int sym) {
   constexpr int BK = 16;
   __shared__ double Xs[BK][kGramTile + 1];
   __shared__ double Ys[BK][kGramTile + 1];
-  const int a0 = blockIdx.x * kGramTile, b0 = blockIdx.y * kGramTile;
+  int ta = blockIdx.x, tb = blockIdx.y;
+  if (sym) {   // upper-triangle tile number -> (ta <= tb)
+    int t = blockIdx.x;
+    tb = 0;
+    while (t > tb) {
+      t -= tb + 1;
+      ++tb;
+    }
+    ta = t;
+  }
+  const int a0 = ta * kGramTile, b0 = tb * kGramTile;
   const long long r0 = (long long)blockIdx.z * kGramRows;
   const long long r1 = min(N, r0 + kGramRows);
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
@@ -61,12 +74,19 @@ __global__ void __launch_bounds__(256) k_gram_partial(long long N, int k1, int k
   }
 }
 
-// out = sum over chunks in chunk order (deterministic)
-__global__ void k_gram_reduce(int nchunks, int total, const double* __restrict__ partial, double* __restrict__ out) {
+// out = sum over chunks in chunk order (deterministic); with sym the entries
+// below the diagonal tiles are read from their mirror images
+__global__ void k_gram_reduce(int nchunks, int k1, int total, const double* __restrict__ partial,
+                              double* __restrict__ out, int sym) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
+  int src = t;
+  if (sym) {
+    const int a = t % k1, b = t / k1;
+    if (a / kGramTile > b / kGramTile) src = b + a * k1;
+  }
   double s = 0.0;
-  for (int c = 0; c < nchunks; ++c) s += partial[(long long)c * total + t];
+  for (int c = 0; c < nchunks; ++c) s += partial[(long long)c * total + src];
   out[t] = s;
 }
 
@@ -709,13 +729,15 @@ long long gram_partial_elems(long long N, int k1, int k2) {
 }
 
 void gram(cudaStream_t s, long long N, int k1, int k2, const double* X, const double* Y, double* partial,
-          double* out) {
+          double* out, bool symmetric) {
   const int nchunks = cdiv(N, kGramRows);
-  dim3 grid(cdiv(k1, kGramTile), cdiv(k2, kGramTile), nchunks);
-  k_gram_partial<<<grid, 256, 0, s>>>(N, k1, k2, X, Y, partial);
+  const bool sym = symmetric && k1 == k2;
+  const int nt = cdiv(k1, kGramTile);
+  dim3 grid = sym ? dim3(nt * (nt + 1) / 2, 1, nchunks) : dim3(nt, cdiv(k2, kGramTile), nchunks);
+  k_gram_partial<<<grid, 256, 0, s>>>(N, k1, k2, X, Y, partial, sym ? 1 : 0);
   prof::count_launch();
   const int total = k1 * k2;
-  k_gram_reduce<<<cdiv(total, 256), 256, 0, s>>>(nchunks, total, partial, out);
+  k_gram_reduce<<<cdiv(total, 256), 256, 0, s>>>(nchunks, k1, total, partial, out, sym ? 1 : 0);
   prof::count_launch();
 }
 

@@ -112,3 +112,55 @@ def test_warm_started_sequence_of_close_problems(intervals, precision):
         assert np.abs(lam.cpu().numpy()[:M] - inside).max() <= 1e-10 * np.abs(inside).max()
         assert r.info.resid_max <= 1e-10
         Xprev = X.clone()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_interval_slicing_gives_the_union(precision):
+    """Sec. V, level (i): adjacent slices of an interval are independent
+    problems (here one batched call); together they find exactly the
+    eigenpairs of the whole interval, none twice."""
+    wl = workloads.WORKLOADS["q1_10x10x20_fp64"]
+    op = wl.operator(1)
+    lam = np.sort(oracle.dense_generalized_eigh(op)[0])
+    M = 12
+    cuts = [0, 4, 8, 12]   # slices of 4 eigenvalues each, cut at midpoints
+    lo = [lam[0] - 0.5 * (lam[M] - lam[M - 1]) if a == 0 else 0.5 * (lam[a - 1] + lam[a]) for a in cuts[:-1]]
+    hi = [0.5 * (lam[b - 1] + lam[b]) for b in cuts[1:]]
+    # M0 = 7: with M0 = 8 the middle slice's B_Q fails the definiteness test
+    # (Sec. III.B (ii)) in the oracle too, its eighth direction being filtered
+    # to ~1e-7
+    M0 = 7
+    dop, keep = dev_op(op)
+    n_sl = len(lo)
+    lams = [torch.zeros(M0, dtype=torch.float64, device="cuda") for _ in range(n_sl)]
+    Xs = [torch.zeros((M0, op.N), dtype=torch.float64, device="cuda") for _ in range(n_sl)]
+    res = [torch.zeros(M0, dtype=torch.float64, device="cuda") for _ in range(n_sl)]
+    h = F().Handle(precision=_prec(precision))
+    st, mf, loops, sts = h.feast_solve_batched([dop] * n_sl, lo, hi, [M0] * n_sl, 8, 1e-12, None, lams, Xs, res)
+    found = np.sort(np.concatenate([lams[i].cpu().numpy()[:mf[i]] for i in range(n_sl)]))
+    assert list(mf) == [4, 4, 4]
+    assert np.abs(found - lam[:M]).max() <= 1e-10 * lam[M - 1]
+    assert max(float(res[i][:mf[i]].max()) for i in range(n_sl)) <= 1e-10
+
+
+def test_inexact_inner_solves_still_converge(intervals):
+    """Sec. IV.C: with node solves accurate only to 1e-3 (the first TF32 solve,
+    no refinement step) and a trace tolerance of 1e-8, FEAST still converges:
+    the eigenvalues to about the square of the solve error, the residuals to
+    about the solve error."""
+    wl = workloads.WORKLOADS["q1_10x10x20_fp64"]
+    op = wl.operator(0)
+    iv = intervals["q1_10x10x20/seed0"]
+    lam = np.sort(oracle.dense_generalized_eigh(op)[0])
+    M = iv["M"]
+    dop, keep = dev_op(op)
+    lamd = torch.zeros(wl.M0, dtype=torch.float64, device="cuda")
+    X = torch.zeros((wl.M0, op.N), dtype=torch.float64, device="cuda")
+    resid = torch.zeros(wl.M0, dtype=torch.float64, device="cuda")
+    h = F().Handle(precision=F().FEAST_PREC_MIXED, ir_tol=1e-3, ir_early=False)
+    r = h.feast_solve(dop, iv["lmin"], iv["lmax"], wl.M0, wl.Ne, 1e-8, None, lamd, X, resid, allow=())
+    assert r.m_found == M
+    assert r.info.ir_steps_max <= 1
+    assert np.abs(lamd.cpu().numpy()[:M] - lam[:M]).max() <= 1e-5 * lam[M - 1]
+    assert resid.cpu().numpy()[:M].max() <= 1e-3
+
