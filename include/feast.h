@@ -161,6 +161,12 @@ feast_status feast_get_info(const feast_handle* h, feast_info* info);
  * Requirements: nx, ny, nz >= 1; 1 <= M0 <= min(N, 128); 1 <= Ne <= 64; lmin < lmax.
  * Returns FEAST_OK, or one of the codes above; on FEAST_ERR_NO_CONVERGENCE and
  * FEAST_ERR_M0_TOO_SMALL the outputs are filled.  Synchronises the stream.
+ * Repeated work (MIXED precision, options.profile off): a factorisation, or a
+ * pair of solve sweeps, whose shape, operator pointers and work buffers were
+ * seen before on this handle is recorded once as a CUDA graph and replayed
+ * into the stream on later uses (the results are the same bit for bit).  The
+ * graphs hold pointers, not data: new contents at the same addresses are
+ * read at replay; they are released by feast_destroy.
  */
 feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin, double lmax,
                          int M0, int Ne, double tol, const double* Y0,

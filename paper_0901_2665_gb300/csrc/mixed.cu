@@ -133,11 +133,13 @@ __global__ void __launch_bounds__(256) k_mx_schur2(Dims d, int layer, const f2* 
 
 // ------------------------------------------------------------------ panel
 
-// 1/a for complex fp32 with scaling (reciprocal instructions only).
+// 1/a for complex fp32 with scaling, from approximate reciprocals (a couple
+// of ulp, far below the TF32 rounding the factors are used at): on the panel
+// inverse's critical path every pivot waits for one of these.
 __device__ __forceinline__ f2 f2inv_fast(f2 a) {
-  const float rs = __frcp_rn(fmaxf(fabsf(a.x), fabsf(a.y)));
+  const float rs = __fdividef(1.0f, fmaxf(fabsf(a.x), fabsf(a.y)));
   const float x = a.x * rs, y = a.y * rs;
-  const float dinv = __frcp_rn(x * x + y * y);
+  const float dinv = __fdividef(1.0f, x * x + y * y);
   return f2{x * dinv * rs, -y * dinv * rs};
 }
 
