@@ -610,10 +610,16 @@ __global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, int layer, const 
   f2 g = Rc ? Rc[e * sG + (long long)m * d.N + row] : f2{(float)Rreal[(long long)m * d.N + row], 0.f};
   if (layer > 0) {
     const f2* T = Tout + ((long long)e * d.k + m) * d.n;
+    const f2* C = Cf + (long long)e * 27 * d.N + row;
+    const int px = p % d.nx, py = p / d.nx;
+    const bool xm = px > 0, xp = px + 1 < d.nx, ym = py > 0, yp = py + 1 < d.ny;
+    // branch-free taps: an in-plane neighbour outside the grid has a zero
+    // coefficient and is read at offset 0 (the row itself) to stay in bounds
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
-      const f2 c = cf_at(d, Cf, e, t, row);
-      if (c.x != 0.f || c.y != 0.f) f2fma(g, c, T[p + (t % 3 - 1) + d.nx * (t / 3 - 1)]);
+      const int dx = t % 3 - 1, dy = t / 3 - 1;
+      const bool ok = (dx < 0 ? xm : (dx > 0 ? xp : true)) && (dy < 0 ? ym : (dy > 0 ? yp : true));
+      f2fma(g, C[(long long)t * d.N], T[p + (ok ? dx + d.nx * dy : 0)]);
     }
   }
   Gc[e * sG + (long long)m * d.N + row] = g;
@@ -632,11 +638,16 @@ __global__ void __launch_bounds__(128) k_mx_couple_bwd(Dims d, int layer, const 
   const f2* col = Gc + e * sG + (long long)m * d.N + row;
   f2 sv = col[0];
   if (layer + 1 < d.nz) {
+    const f2* C = Cf + ((long long)e * 27 + 18) * d.N + row;
+    const int px = p % d.nx, py = p / d.nx;
+    const bool xm = px > 0, xp = px + 1 < d.nx, ym = py > 0, yp = py + 1 < d.ny;
+    // branch-free taps, as in the forward coupling
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
-      const f2 c = cf_at(d, Cf, e, 18 + t, row);
-      if (c.x == 0.f && c.y == 0.f) continue;
-      const f2 x = col[d.n + (t % 3 - 1) + d.nx * (t / 3 - 1)];
+      const int dx = t % 3 - 1, dy = t / 3 - 1;
+      const bool ok = (dx < 0 ? xm : (dx > 0 ? xp : true)) && (dy < 0 ? ym : (dy > 0 ? yp : true));
+      const f2 c = C[(long long)t * d.N];
+      const f2 x = col[d.n + (ok ? dx + d.nx * dy : 0)];
       sv.x -= c.x * x.x - c.y * x.y;
       sv.y -= c.x * x.y + c.y * x.x;
     }
