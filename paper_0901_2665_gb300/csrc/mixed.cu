@@ -14,7 +14,12 @@
 // Solve: forward/backward sweeps in complex64 (TF32 products, fp32
 // accumulation) give a correction d = M~^{-1} R; FP64 iterative refinement
 // Q_e += d, R = RHS - (Z_e B - A) Q_e repeats until ||R||/||RHS|| <= ir_tol
-// for every node.
+// for every node (the first residual in FP64, the later ones updated by the
+// last correction in double-float).
+//
+// Launch: all Ne nodes in every kernel (grid z = node).  Without kernel
+// timing, a factorisation and a pair of sweeps whose launch sequence was
+// seen before on the same work space are replayed from CUDA graphs.
 #include <cuda.h>
 
 #include <algorithm>
