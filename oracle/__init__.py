@@ -16,11 +16,14 @@ from .feast_oracle import (  # noqa: F401
     contour_points,
     dense_generalized_eigh,
     feast,
+    feast_hermitian,
     filter_value,
     gauss_legendre,
     inertia_count,
     norm1,
     quadrature_subspace,
+    quadrature_subspace_hermitian,
     rayleigh_ritz,
+    rayleigh_ritz_hermitian,
     residuals,
 )

@@ -278,6 +278,85 @@ def feast(op, lmin: float, lmax: float, M0: int, Ne: int, Y: np.ndarray,
 
 
 # ----------------------------------------------------------------------------
+# Complex Hermitian A (Sec. III.A, Eqs. 10 and 12)
+# ----------------------------------------------------------------------------
+
+def quadrature_subspace_hermitian(A: sp.csr_matrix, B: sp.csr_matrix, RHS: np.ndarray,
+                                  lmin: float, lmax: float, Ne: int, n: int, nb: int,
+                                  factors=None):
+    """Eq. 12: Q = -sum_e (w_e r / 4) (e^{i theta_e} G(Z_e) + e^{-i theta_e}
+    G^dagger(Z_e)) RHS, with G(Z) = (Z B - A)^{-1} and, A being Hermitian,
+    G^dagger(Z) = G(conj Z) (Sec. III.A); each node solves at Z_e and at its
+    conjugate, accumulated in the order e = 1..Ne.  ``factors`` caches the
+    2 Ne factorisations.  Returns (Q, factors)."""
+    _, w, theta, Z, r = contour_points(lmin, lmax, Ne)
+    if factors is None:
+        factors = [(block_tridiag_factor((Z[e] * B - A).astype(np.complex128), n, nb),
+                    block_tridiag_factor((np.conj(Z[e]) * B - A).astype(np.complex128), n, nb))
+                   for e in range(Ne)]
+    Q = np.zeros(RHS.shape, dtype=np.complex128)
+    for e in range(Ne):
+        Ge = factors[e][0].solve(RHS.astype(np.complex128))
+        Gd = factors[e][1].solve(RHS.astype(np.complex128))
+        Q = Q - (w[e] * r / 4.0) * (np.exp(1j * theta[e]) * Ge + np.exp(-1j * theta[e]) * Gd)
+    return Q, factors
+
+
+def rayleigh_ritz_hermitian(Q: np.ndarray, A: sp.csr_matrix, B: sp.csr_matrix):
+    """Steps 3-5 for complex Q: A_Q = Q^H A Q, B_Q = Q^H B Q (Hermitian), the
+    Hermitian-definite pencil by LAPACK (hegvd), X = Q Phi; the same
+    definiteness test as the real case."""
+    AQ = Q.conj().T @ (A @ Q)
+    BQ = Q.conj().T @ (B @ Q)
+    AQ = 0.5 * (AQ + AQ.conj().T)   # Hermitian in exact arithmetic
+    BQ = 0.5 * (BQ + BQ.conj().T)
+    d = np.linalg.eigvalsh(BQ)
+    if not (d[0] > 1e-14 * d[-1]):
+        raise BQNotSPD(f"B_Q eigenvalue ratio {d[0] / d[-1]:.3e}")
+    eps, Phi = sla.eigh(AQ, BQ)
+    return eps, Q @ Phi, AQ, BQ
+
+
+def feast_hermitian(op, lmin: float, lmax: float, M0: int, Ne: int, Y: np.ndarray,
+                    tol: float = 1e-12, max_loops: int = 20) -> FeastResult:
+    """FEAST for a complex Hermitian A (``op.A27`` complex) and a real s.p.d.
+    B: the loop of ``feast`` with Y, Q, X and Phi complex and the contour sum
+    of Eq. 12 in step 2 (Sec. III.B, the changes listed for Hermitian A)."""
+    nx, ny, nz = op.nx, op.ny, op.nz
+    n, nb = nx * ny, nz
+    A = assemble(op.A27, nx, ny, nz)
+    B = assemble(op.B27, nx, ny, nz)
+    Ycur = np.array(Y, dtype=np.complex128)
+    factors = None
+    prev_trace, prev_count = None, None
+    traces, changes = [], []
+    converged = False
+    for loop in range(1, max_loops + 1):
+        RHS = B @ Ycur
+        Q, factors = quadrature_subspace_hermitian(A, B, RHS, lmin, lmax, Ne, n, nb, factors)
+        eps, X, _, _ = rayleigh_ritz_hermitian(Q, A, B)
+        inside = (eps >= lmin) & (eps <= lmax)
+        count = int(inside.sum())
+        trace = float(eps[inside].sum())
+        scale = float(np.abs(eps[inside]).sum())
+        traces.append(trace)
+        if prev_trace is not None:
+            change = abs(trace - prev_trace) / scale if scale > 0 else 0.0
+            changes.append(change)
+            if count == prev_count and change <= tol:
+                converged = True
+        Ycur = X
+        if converged:
+            break
+        prev_trace, prev_count = trace, count
+    order = np.concatenate([np.flatnonzero(inside), np.flatnonzero(~inside)])
+    lam = eps[order]
+    X = X[:, order]
+    r1, rp = residuals(A, B, lam, X)
+    return FeastResult(lam, X, r1, rp, count, loop, converged, traces, changes)
+
+
+# ----------------------------------------------------------------------------
 # Independent checks used to pin the oracle
 # ----------------------------------------------------------------------------
 

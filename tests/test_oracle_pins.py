@@ -333,3 +333,107 @@ def test_bf16_rounding_nearest_even():
     assert r[1] == 1.0                                             # 1 + 2^-8 is a tie: even is 1.0
     assert r[2] == 1.0 + 2 ** -7                                   # above the tie rounds up
     assert r[3] == -2.5
+
+
+# ---------------------------------------------------------------- Hermitian A (Eqs. 10, 12)
+
+def _tiny_hermitian(flux=0.4, gauge_seed=None, gauge_B=False):
+    real = workloads.q1_operator(5, 4, 6, workloads.gaussian_potential(3, 17, 5, 4, 6))
+    return real, workloads.peierls_operator(real, flux=flux, gauge_seed=gauge_seed, gauge_B=gauge_B)
+
+
+def test_peierls_operator_is_hermitian():
+    _, op = _tiny_hermitian(flux=0.4, gauge_seed=3)
+    A = oracle.assemble(op.A27, op.nx, op.ny, op.nz).toarray()
+    assert np.abs(A.imag).max() > 1e-3                      # genuinely complex
+    assert np.abs(A - A.conj().T).max() < 1e-15 * np.abs(A).max()
+
+
+def test_hermitian_quadrature_matches_spectral_form():
+    """Eq. 12 on a tiny Hermitian pencil equals Q = X f(Lambda) X^H RHS with
+    the real filter f of Eq. 15 (G(Z) = X (Z - Lambda)^{-1} X^H, and the two
+    terms of Eq. 12 add to twice the real part)."""
+    _, op = _tiny_hermitian()
+    A = oracle.assemble(op.A27, op.nx, op.ny, op.nz)
+    B = oracle.assemble(op.B27, op.nx, op.ny, op.nz)
+    lam, X = sla.eigh(A.toarray(), B.toarray())
+    lmin, lmax = lam[1] - 0.3, 0.5 * (lam[6] + lam[7])
+    rhs = workloads.random_Y_complex(op.N, 3, 41)
+    Q, _ = oracle.quadrature_subspace_hermitian(A, B, rhs, lmin, lmax, 8, op.n, op.nz)
+    f = oracle.filter_value(lam, lmin, lmax, 8)
+    Qref = X @ (f[:, None] * (X.conj().T @ rhs))
+    assert np.abs(Q - Qref).max() / np.abs(Qref).max() < 1e-12
+
+
+def test_hermitian_formula_reduces_to_the_real_one():
+    """For real A and real Y, Eq. 12 gives the real subspace of Eq. 15."""
+    real, op = _tiny_hermitian(flux=0.0)
+    A = oracle.assemble(op.A27, op.nx, op.ny, op.nz)
+    Ar = oracle.assemble(real.A27, real.nx, real.ny, real.nz)
+    B = oracle.assemble(op.B27, op.nx, op.ny, op.nz)
+    lam = oracle.dense_generalized_eigh(real)[0]
+    lmin, lmax = lam[0] - 0.5, 0.5 * (lam[5] + lam[6])
+    rhs = np.random.default_rng(43).standard_normal((op.N, 4))
+    Qh, _ = oracle.quadrature_subspace_hermitian(A, B, rhs, lmin, lmax, 8, op.n, op.nz)
+    Qr, _ = oracle.quadrature_subspace(Ar, B, rhs, lmin, lmax, 8, op.n, op.nz)
+    assert np.abs(Qh.imag).max() < 1e-13 * np.abs(Qr).max()
+    assert np.abs(Qh.real - Qr).max() < 1e-12 * np.abs(Qr).max()
+
+
+def test_feast_hermitian_matches_dense_pencil():
+    """A uniform field (flux 0.4 per plaquette) and a potential: the Hermitian
+    loop finds the eigenvalues of the dense Hermitian pencil to 1e-12 with
+    B-orthonormal eigenvectors (X^H B X = I) and residuals <= 1e-10."""
+    _, op = _tiny_hermitian(flux=0.4)
+    A = oracle.assemble(op.A27, op.nx, op.ny, op.nz)
+    B = oracle.assemble(op.B27, op.nx, op.ny, op.nz)
+    lam = sla.eigh(A.toarray(), B.toarray(), eigvals_only=True)
+    M = 6
+    lmin, lmax = lam[0] - 0.5 * (lam[M] - lam[M - 1]), 0.5 * (lam[M - 1] + lam[M])
+    res = oracle.feast_hermitian(op, lmin, lmax, 10, 8, workloads.random_Y_complex(op.N, 10, 1001), tol=1e-12)
+    assert res.converged and res.m_found == M
+    assert np.allclose(res.lam[:M], lam[:M], rtol=1e-12, atol=0)
+    X = res.X[:, :M]
+    assert np.abs(X.conj().T @ (B @ X) - np.eye(M)).max() < 1e-12
+    assert res.resid[:M].max() < 1e-10
+
+
+def test_feast_hermitian_is_gauge_invariant():
+    """A pure gauge transformation D^H (A, B) D, D = diag(exp(i chi)), leaves
+    the spectrum unchanged: the Hermitian loop on the transformed pencil finds
+    the eigenvalues of the real pencil (closed interval as for the real loop)."""
+    real, op = _tiny_hermitian(flux=0.0, gauge_seed=5, gauge_B=True)
+    lam = oracle.dense_generalized_eigh(real)[0]
+    M = 6
+    lmin, lmax = lam[0] - 0.5 * (lam[M] - lam[M - 1]), 0.5 * (lam[M - 1] + lam[M])
+    res = oracle.feast_hermitian(op, lmin, lmax, 10, 8, workloads.random_Y_complex(op.N, 10, 1002), tol=1e-12)
+    assert res.converged and res.m_found == M
+    assert np.allclose(res.lam[:M], lam[:M], rtol=1e-12, atol=0)
+
+
+def test_hermitian_pin_catches_planted_mistakes():
+    """Each plausible slip in Eq. 12 breaks the spectral-form pin: the G^dagger
+    term dropped (and the first doubled), the weight 1/4 read as 1/2, the
+    conjugate node replaced by Z_e itself."""
+    _, op = _tiny_hermitian()
+    A = oracle.assemble(op.A27, op.nx, op.ny, op.nz)
+    B = oracle.assemble(op.B27, op.nx, op.ny, op.nz)
+    lam, X = sla.eigh(A.toarray(), B.toarray())
+    lmin, lmax = lam[1] - 0.3, 0.5 * (lam[6] + lam[7])
+    rhs = workloads.random_Y_complex(op.N, 2, 47)
+    f = oracle.filter_value(lam, lmin, lmax, 8)
+    Qref = X @ (f[:, None] * (X.conj().T @ rhs))
+    _, w, theta, Z, r = oracle.contour_points(lmin, lmax, 8)
+
+    def solve(z):
+        return sla.solve((z * B - A).toarray(), rhs)
+
+    wrong = {
+        "no adjoint term": sum(-(w[e] * r / 2.0) * np.exp(1j * theta[e]) * solve(Z[e]) for e in range(8)),
+        "weight 1/2": sum(-(w[e] * r / 2.0) * (np.exp(1j * theta[e]) * solve(Z[e])
+                                               + np.exp(-1j * theta[e]) * solve(np.conj(Z[e]))) for e in range(8)),
+        "Z for conj Z": sum(-(w[e] * r / 4.0) * (np.exp(1j * theta[e]) + np.exp(-1j * theta[e])) * solve(Z[e])
+                            for e in range(8)),
+    }
+    for name, Q in wrong.items():
+        assert np.abs(Q - Qref).max() / np.abs(Qref).max() > 1e-3, name

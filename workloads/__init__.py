@@ -179,6 +179,42 @@ def q1_operator(nx: int, ny: int, nz: int, potential: Potential | None = None) -
     return Operator(nx, ny, nz, np.ascontiguousarray(A27), np.ascontiguousarray(B27))
 
 
+def peierls_operator(op: Operator, flux: float = 0.0, gauge_seed: int | None = None,
+                     gauge_B: bool = False) -> Operator:
+    """A Hermitian operator from a real one: every coupling A_ij (i != j) gets
+    the phase exp(i phi_ij) with phi_ji = -phi_ij, so that A_ji = conj(A_ij).
+    phi_ij = flux * (x_i + x_j)/2 * (y_j - y_i) in grid units (a uniform field
+    along z in the Landau gauge) plus chi_j - chi_i for a seeded uniform chi in
+    [0, 2 pi) when gauge_seed is given.  With gauge_B the couplings of B get
+    the gauge part exp(i (chi_j - chi_i)) too: the pencil is then D^H (A, B) D
+    for D = diag(exp(i chi)) (at flux 0), with the eigenvalues of (A, B).
+    A27 (and then B27) is complex128."""
+    nx, ny, nz = op.nx, op.ny, op.nz
+    ix, iy, iz = grid_index(nx, ny, nz)
+    N = op.N
+    chi = np.zeros(N)
+    if gauge_seed is not None:
+        chi = 2.0 * np.pi * np.random.default_rng(gauge_seed).random(N)
+    idx = np.arange(N, dtype=np.int64)
+    A27 = np.zeros((27, N), dtype=np.complex128)
+    B27 = np.zeros((27, N), dtype=np.complex128)
+    for s, (dx, dy, dz) in enumerate(STENCIL_OFFSETS):
+        valid = ((ix + dx >= 0) & (ix + dx < nx) & (iy + dy >= 0) & (iy + dy < ny)
+                 & (iz + dz >= 0) & (iz + dz < nz))
+        j = np.where(valid, idx + dx + nx * (dy + ny * dz), idx)
+        phi = flux * (ix + 0.5 * dx) * dy + chi[j] - chi
+        A27[s] = np.where(valid, op.A27[s] * np.exp(1j * phi), 0.0)
+        if gauge_B:
+            B27[s] = np.where(valid, op.B27[s] * np.exp(1j * (chi[j] - chi)), 0.0)
+    return Operator(nx, ny, nz, np.ascontiguousarray(A27), B27 if gauge_B else op.B27.copy())
+
+
+def random_Y_complex(N: int, M0: int, seed: int) -> np.ndarray:
+    """Complex start block: real part random_Y(seed), imaginary part
+    random_Y(seed + 1) (the same counter-based generator)."""
+    return random_Y(N, M0, seed) + 1j * random_Y(N, M0, seed + 1)
+
+
 def decouple_layers(op: Operator, cut_layers) -> Operator:
     """Zero the couplings across the z-interfaces just below each layer in
     ``cut_layers``: the matrices become block diagonal with one block per slab
