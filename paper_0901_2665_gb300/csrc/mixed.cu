@@ -158,9 +158,10 @@ __device__ __forceinline__ f2 f2inv_fast(f2 a) {
 // pivot's row and column publish them to shared memory (double-buffered by
 // pivot parity), and the holder of the next pivot publishes its reciprocal,
 // so that one block barrier per pivot suffices and the reciprocal is formed
-// once.  Every thread applies the rank-1 update to its eight entries; the
-// pivot row (two warps) and the pivot column (one lane in eight warps) are
-// then overwritten.  The 64 pivots are the kernel's critical path.
+// once.  Every thread applies the rank-1 update to its eight entries, the
+// pivot column through the same FMAs (its entries are cleared when published
+// and the multiplier there is -1/p); the pivot row (two warps) is then
+// overwritten.  The 64 pivots are the kernel's critical path.
 constexpr int kPinvThreads = 512;
 constexpr int kPinvGroups = kPinvThreads / kPanel;   // row groups
 constexpr int kPinvRows = kPanel / kPinvGroups;      // rows per thread
@@ -207,9 +208,14 @@ __global__ void __launch_bounds__(kPinvThreads) k_mx_pinv(Dims d, int layer, int
         invb[buf] = good ? f2inv_fast(x) : f2{0.f, 0.f};
       }
     }
+    // the column's holders publish it and clear their entries: the next
+    // pivot's update then leaves P[i, kn] / p there (see below)
     if (j == kn)
 #pragma unroll
-      for (int a = 0; a < kPinvRows; ++a) colb[buf][g + kPinvGroups * a] = v[a];
+      for (int a = 0; a < kPinvRows; ++a) {
+        colb[buf][g + kPinvGroups * a] = v[a];
+        v[a] = f2{0.f, 0.f};
+      }
   };
   publish(0, 0);
   __syncthreads();
@@ -218,19 +224,18 @@ __global__ void __launch_bounds__(kPinvThreads) k_mx_pinv(Dims d, int layer, int
     const int b = k & 1;
     const f2 inv = invb[b];
     const f2 rki = f2mul(rowb[b][j], inv);   // P[k, j] / p
-    // rank-1 update of every entry: P[i, j] -= P[i, k] P[k, j] / p
+    // rank-1 update of every entry: P[i, j] -= P[i, k] P[k, j] / p.  On the
+    // pivot column (entries cleared at publication) the multiplier -1/p makes
+    // the same two FMAs leave P[i, k] / p, without a divergent branch.
+    const f2 r = (j == k) ? f2{-inv.x, -inv.y} : rki;
 #pragma unroll
     for (int a = 0; a < kPinvRows; ++a) {
       const f2 c = colb[b][g + kPinvGroups * a];
-      v[a].x = fmaf(-c.x, rki.x, v[a].x);
-      v[a].x = fmaf(c.y, rki.y, v[a].x);
-      v[a].y = fmaf(-c.x, rki.y, v[a].y);
-      v[a].y = fmaf(-c.y, rki.x, v[a].y);
+      v[a].x = fmaf(-c.x, r.x, v[a].x);
+      v[a].x = fmaf(c.y, r.y, v[a].x);
+      v[a].y = fmaf(-c.x, r.y, v[a].y);
+      v[a].y = fmaf(-c.y, r.x, v[a].y);
     }
-    // pivot column: P[i, k] = P[i, k] / p
-    if (j == k)
-#pragma unroll
-      for (int a = 0; a < kPinvRows; ++a) v[a] = f2mul(colb[b][g + kPinvGroups * a], inv);
     // pivot row: P[k, j] = P[k, j] / p, and P[k, k] = -1 / p
     if (g == k % kPinvGroups) {
       const f2 x = (j == k) ? f2{-inv.x, -inv.y} : rki;
