@@ -8,6 +8,7 @@ tiny inputs, Sylvester inertia and the k-fold multiplicity construction of
 Sec. IV.B.
 """
 
+import json
 import math
 import os
 
@@ -201,6 +202,27 @@ def test_inertia_count_matches_dense_eigenvalues():
     lam = oracle.dense_generalized_eigh(op)[0]
     for sigma in (lam[0] - 1.0, 0.5 * (lam[3] + lam[4]), 0.5 * (lam[40] + lam[41]), lam[-1] + 1):
         assert oracle.inertia_count(op, sigma) == int((lam < sigma).sum())
+
+
+def test_full_size_brackets_are_consistent(intervals):
+    """The stored brackets of sampled eigenvalues of the 32 x 32 x 400
+    workload (bisection on the inertia count above) are tight, ordered, inside
+    the certified interval and inside the coarser brackets stored with it,
+    and their end counts straddle their index."""
+    with open(os.path.join(GOLDEN, "fullsize_brackets.json")) as f:
+        fb = json.load(f)
+    iv = intervals[fb["key"]]
+    coarse = iv["brackets"]
+    prev = -math.inf
+    for k in sorted(fb["brackets"], key=int):
+        b = fb["brackets"][k]
+        assert 0 < b["hi"] - b["lo"] <= fb["rel_width"] * abs(b["hi"]) <= 1e-11 * abs(b["hi"])
+        assert b["nu_lo"] <= int(k) - 1 < int(k) <= b["nu_hi"]
+        assert iv["lmin"] <= b["lo"] and b["hi"] <= iv["lmax"] and b["lo"] >= prev
+        if k in coarse:
+            assert coarse[k][0] <= b["lo"] and b["hi"] <= coarse[k][1]
+        prev = b["hi"]
+    assert {"1", str(iv["M"])} <= set(fb["brackets"])
 
 
 def test_k_copies_give_k_fold_multiplicity():
