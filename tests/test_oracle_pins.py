@@ -4,8 +4,10 @@ Each test checks the oracle against something other than itself: the paper's
 printed Gauss-Legendre table (Fig. 2 caption), exactness of Gauss quadrature,
 closed forms of the contour filter, the V = 0 tensor-product spectrum, the
 spectral form of Q from a dense pencil eigendecomposition, LAPACK/SuperLU on
-tiny inputs, Sylvester inertia and the k-fold multiplicity construction of
-Sec. IV.B.
+tiny inputs, a Jacobi generalized eigensolver written from the mathematics
+(oracle/jacobi.py, itself pinned to closed forms), hand-computed residuals and
+norms (Table I caption), Sylvester inertia and the k-fold multiplicity
+construction of Sec. IV.B.
 """
 
 import json
@@ -140,18 +142,195 @@ def test_quadrature_matches_spectral_form():
 # ---------------------------------------------------------------- steps 3-5
 
 def test_rayleigh_ritz_2x2_closed_form():
-    """A 2x2 reduced problem: eigenvalues of B^{-1}A from the characteristic
-    polynomial det(A - eps B) = 0 written out by hand."""
-    AQ = np.array([[2.0, 1.0], [1.0, 3.0]])
-    BQ = np.array([[2.0, 0.5], [0.5, 1.0]])
-    a = np.linalg.det(BQ)
-    b = -(AQ[0, 0] * BQ[1, 1] + AQ[1, 1] * BQ[0, 0] - 2 * AQ[0, 1] * BQ[0, 1])
-    c = np.linalg.det(AQ)
-    disc = math.sqrt(b * b - 4 * a * c)
-    roots = sorted([(-b - disc) / (2 * a), (-b + disc) / (2 * a)])
-    eps, Phi = sla.eigh(AQ, BQ)
-    assert np.allclose(eps, roots, rtol=1e-14)
-    assert np.allclose(Phi.T @ BQ @ Phi, np.eye(2), atol=1e-14)
+    """Steps 3-5 of the oracle on a 2 x 2 pencil with an invertible,
+    non-orthogonal Q.  A full-rank Q makes A_Q, B_Q congruent to A, B (Eq. 7),
+    so the Ritz values are the pencil's eigenvalues: by hand,
+    det(A - e B) = (2 - 2e)(3 - e) - (1 - e/2)^2 = 1.75 e^2 - 7 e + 5, with
+    roots (7 -+ sqrt(14)) / 3.5.  X = Q Phi must be B-orthonormal (Eq. 9) and
+    satisfy A X = B X diag(eps) exactly (Eq. 2)."""
+    import scipy.sparse as sp
+    A = np.array([[2.0, 1.0], [1.0, 3.0]])
+    B = np.array([[2.0, 0.5], [0.5, 1.0]])
+    Q = np.array([[1.0, 2.0], [0.5, -1.0]])
+    roots = np.array([(7.0 - math.sqrt(14.0)) / 3.5, (7.0 + math.sqrt(14.0)) / 3.5])
+    eps, X, AQ, BQ = oracle.rayleigh_ritz(Q, sp.csr_matrix(A), sp.csr_matrix(B))
+    assert np.allclose(eps, roots, rtol=1e-14, atol=0)
+    assert np.abs(X.T @ B @ X - np.eye(2)).max() < 1e-14
+    assert np.abs(A @ X - B @ X * eps[None, :]).max() < 1e-14
+    # a plausible slip, B_Q = Q^T Q (B dropped from Eq. 7), breaks the pin
+    wrong = np.sort(np.real(np.linalg.eigvals(np.linalg.solve(Q.T @ Q, Q.T @ A @ Q))))
+    assert np.abs(wrong - roots).max() > 1e-2
+
+
+def test_reduced_eigensolve_matches_jacobi():
+    """The oracle's step 4 (LAPACK sygvd inside rayleigh_ritz) against the
+    Jacobi solver written from the mathematics, on the A_Q, B_Q that
+    rayleigh_ritz itself forms from a tiny Q1 pencil and a random block."""
+    import scipy.sparse as sp  # noqa: F401
+    op = workloads.q1_operator(4, 3, 5, workloads.gaussian_potential(3, 21, 4, 3, 5))
+    A = oracle.assemble(op.A27, 4, 3, 5)
+    B = oracle.assemble(op.B27, 4, 3, 5)
+    Q = np.random.default_rng(8).standard_normal((op.N, 12))
+    eps, X, AQ, BQ = oracle.rayleigh_ritz(Q, A, B)
+    ej, Pj = oracle.jacobi_generalized_eigh(AQ, BQ)
+    assert np.abs(eps - ej).max() <= 1e-12 * np.abs(ej).max()
+    # same Ritz vectors up to sign (the eigenvalues here are simple)
+    Xj = Q @ Pj
+    for c in range(12):
+        s = np.sign(Xj[:, c] @ (B @ X[:, c]))
+        assert np.abs(s * Xj[:, c] - X[:, c]).max() <= 1e-9 * np.abs(X[:, c]).max()
+
+
+# ---------------------------------------------------------------- Jacobi (independent eigensolver)
+
+def test_jacobi_2x2_closed_form():
+    """A symmetric 2 x 2 matrix [[a, b], [b, c]] has the eigenvalues
+    (a + c)/2 -+ sqrt(((a - c)/2)^2 + b^2)."""
+    for a, b, c in [(2.0, 1.0, -3.0), (1.0, 1e-9, 1.0), (5.0, -4.0, 5.0), (0.0, 2.0, 0.0)]:
+        w, V = oracle.jacobi_symmetric(np.array([[a, b], [b, c]]))
+        d = math.sqrt(((a - c) / 2) ** 2 + b * b)
+        assert np.allclose(w, [(a + c) / 2 - d, (a + c) / 2 + d], rtol=1e-15, atol=1e-15)
+        assert np.abs(V.T @ V - np.eye(2)).max() < 1e-15
+
+
+def test_jacobi_generalized_v0_closed_form():
+    """The Jacobi solver on the assembled V = 0 pencil reproduces the
+    tensor-product closed form, with B-orthonormal eigenvectors."""
+    for (nx, ny, nz) in [(3, 4, 5), (2, 3, 7)]:
+        op = workloads.q1_operator(nx, ny, nz)
+        A = oracle.assemble(op.A27, nx, ny, nz).toarray()
+        B = oracle.assemble(op.B27, nx, ny, nz).toarray()
+        eps, Phi = oracle.jacobi_generalized_eigh(A, B)
+        cf = oracle.closed_form_eigenvalues_v0(nx, ny, nz)
+        assert np.allclose(eps, cf, rtol=1e-12, atol=0)
+        assert np.abs(Phi.T @ B @ Phi - np.eye(op.N)).max() < 1e-12
+        assert np.abs(A @ Phi - B @ Phi * eps[None, :]).max() < 1e-12 * np.abs(A).max()
+
+
+def test_jacobi_generalized_matches_lapack_dense_pencil():
+    """Jacobi and LAPACK (the oracle's dense reference) on pencils with a
+    potential: eigenvalue by eigenvalue to 1e-12."""
+    for (nx, ny, nz, G, seed) in [(5, 4, 6, 3, 17), (3, 3, 8, 4, 2)]:
+        op = workloads.q1_operator(nx, ny, nz, workloads.gaussian_potential(G, seed, nx, ny, nz))
+        A = oracle.assemble(op.A27, nx, ny, nz).toarray()
+        B = oracle.assemble(op.B27, nx, ny, nz).toarray()
+        ej, _ = oracle.jacobi_generalized_eigh(A, B)
+        el = oracle.dense_generalized_eigh(op)[0]
+        assert np.allclose(ej, el, rtol=1e-12, atol=0)
+
+
+def test_feast_matches_jacobi_on_tiny_pencil():
+    """The whole oracle loop (Fig. 2) against the from-scratch Jacobi
+    eigensolve of the dense pencil: the M lowest eigenvalues to 1e-12, the
+    eigenvectors through their B-projectors (all simple here)."""
+    op = workloads.q1_operator(5, 4, 6, workloads.gaussian_potential(3, 17, 5, 4, 6))
+    A = oracle.assemble(op.A27, 5, 4, 6)
+    B = oracle.assemble(op.B27, 5, 4, 6)
+    ej, Pj = oracle.jacobi_generalized_eigh(A.toarray(), B.toarray())
+    M = 7
+    lmin, lmax = ej[0] - 0.5 * (ej[M] - ej[M - 1]), 0.5 * (ej[M - 1] + ej[M])
+    res = oracle.feast(op, lmin, lmax, 12, 8, workloads.random_Y(op.N, 12, 5), tol=1e-12)
+    assert res.converged and res.m_found == M
+    assert np.allclose(res.lam[:M], ej[:M], rtol=1e-12, atol=0)
+    for c in range(M):
+        x, xj = res.X[:, c], Pj[:, c]
+        assert np.abs(x * (xj @ (B @ x)) - xj * (xj @ (B @ xj))).max() <= 1e-9 * np.abs(xj).max()
+
+
+def test_jacobi_pins_catch_planted_mistakes(monkeypatch):
+    """A wrong rotation -- the sign of s flipped, or tau with its sign
+    reversed -- no longer annihilates a_pq: the 2 x 2 closed form fails or the
+    sweeps never end."""
+    import oracle.jacobi as jac
+    S = np.array([[2.0, 1.0], [1.0, -3.0]])
+    d = math.sqrt(2.5 ** 2 + 1.0)
+    want = [-0.5 - d, -0.5 + d]
+    orig = jac.rotation
+
+    def flipped(app, aqq, apq):
+        c, s = orig(app, aqq, apq)
+        return c, -s
+
+    def tau_reversed(app, aqq, apq):
+        return orig(aqq, app, apq)
+
+    for bad in (flipped, tau_reversed):
+        monkeypatch.setattr(jac, "rotation", bad)
+        try:
+            w, _ = jac.jacobi_symmetric(S, max_sweeps=20)
+            assert not np.allclose(w, want, rtol=1e-12), bad.__name__
+        except jac.JacobiNoConvergence:
+            pass
+    monkeypatch.setattr(jac, "rotation", orig)
+    w, _ = jac.jacobi_symmetric(S, max_sweeps=20)
+    assert np.allclose(w, want, rtol=1e-14)
+
+
+# ---------------------------------------------------------------- residuals (Table I caption)
+
+def test_norm1_closed_forms():
+    """||M||_1 = largest absolute column sum: 6 for [[1, -2], [3, 4]] (its
+    infinity norm is 7, its 2-norm 5.12); and for the Q1 operator at V = 0,
+    A = K/2 has the interior column 8h/3 in absolute sum (centre 4h/3, 12
+    edge neighbours -h/12, 8 corners -h/24, faces 0)."""
+    import scipy.sparse as sp
+    assert oracle.norm1(sp.csr_matrix(np.array([[1.0, -2.0], [3.0, 4.0]]))) == 6.0
+    for g in [(3, 3, 3), (4, 5, 6), (7, 3, 4)]:
+        op = workloads.q1_operator(*g)
+        h = 1.0 / (g[0] + 1)
+        assert abs(oracle.norm1(oracle.assemble(op.A27, *g)) - 8.0 * h / 3.0) < 1e-15
+
+
+def _resid_case():
+    import scipy.sparse as sp
+    A = sp.csr_matrix(np.array([[3.0, -1.0, 0.0], [-1.0, 2.0, -1.0], [0.0, -1.0, 2.0]]))
+    B = sp.csr_matrix(np.diag([2.0, 1.0, 1.0]))
+    X = np.array([[1.0, 1.0, 1.0], [0.0, 1.0, -1.0], [0.0, 0.0, 2.0]])
+    lam = np.array([1.0, 2.0, 0.5])
+    # by hand, ||A||_1 = 4 (columns 4, 4, 3):
+    #   x = (1, 0, 0),  l = 1:   A x - l B x = (1, -1, 0),      ||.||_1 = 2,    ||x||_1 = 1, ||A x||_1 = 4
+    #   x = (1, 1, 0),  l = 2:   A x - l B x = (-2, -1, -1),    ||.||_1 = 4,    ||x||_1 = 2, ||A x||_1 = 4
+    #   x = (1, -1, 2), l = 1/2: A x - l B x = (3, -4.5, 4),    ||.||_1 = 11.5, ||x||_1 = 4, ||A x||_1 = 14
+    want = np.array([2.0 / 4.0, 4.0 / 8.0, 11.5 / 16.0])
+    want_paper = np.array([2.0 / 4.0, 4.0 / 4.0, 11.5 / 14.0])
+    return A, B, X, lam, want, want_paper
+
+
+def test_residuals_hand_computed():
+    """Both residual forms on a 3 x 3 pencil with planted non-eigenvectors."""
+    A, B, X, lam, want, want_paper = _resid_case()
+    r1, rp = oracle.residuals(A, B, lam, X)
+    assert np.allclose(r1, want, rtol=1e-15, atol=0)
+    assert np.allclose(rp, want_paper, rtol=1e-15, atol=0)
+    # invariant under scaling of x
+    r1s, rps = oracle.residuals(A, B, lam, X * np.array([3.0, -0.25, 7.0])[None, :])
+    assert np.allclose(r1s, want, rtol=1e-15) and np.allclose(rps, want_paper, rtol=1e-15)
+
+
+def test_residual_pins_catch_planted_mistakes(monkeypatch):
+    """Plausible slips in the residual formulas each miss the hand values:
+    the 2-norm for ||x||, the 2-norm or Frobenius norm for ||A||, B dropped,
+    the two denominators swapped."""
+    import numpy.linalg as la
+    import oracle.feast_oracle as fo
+    A, B, X, lam, want, want_paper = _resid_case()
+    Ad = A.toarray()
+    # the oracle with ||A||_1 replaced by the 2-norm / Frobenius norm
+    for bad_norm in (lambda M: float(la.norm(M.toarray(), 2)), lambda M: float(la.norm(M.toarray(), "fro"))):
+        monkeypatch.setattr(fo, "norm1", bad_norm)
+        r1, _ = fo.residuals(A, B, lam, X)
+        assert not np.allclose(r1, want, rtol=1e-6)
+    monkeypatch.setattr(fo, "norm1", oracle.norm1)
+    R = Ad @ X - (B.toarray() @ X) * lam[None, :]
+    rn = np.abs(R).sum(axis=0)
+    # ||x||_2 in place of ||x||_1
+    assert not np.allclose(rn / (4.0 * la.norm(X, axis=0)), want, rtol=1e-6)
+    # B dropped: A x - l x
+    rn_noB = np.abs(Ad @ X - X * lam[None, :]).sum(axis=0)
+    assert not np.allclose(rn_noB / (4.0 * np.abs(X).sum(axis=0)), want, rtol=1e-6)
+    # denominators swapped between the two forms
+    assert not np.allclose(rn / np.abs(Ad @ X).sum(axis=0), want, rtol=1e-6)
+    assert not np.allclose(rn / (4.0 * np.abs(X).sum(axis=0)), want_paper, rtol=1e-6)
 
 
 # ---------------------------------------------------------------- full loop
