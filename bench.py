@@ -103,6 +103,8 @@ def parse():
                          "ne_sweep: contour node counts 4/8/16 (Table III); warm_sequence: a potential changed in "
                          "small steps, each solve started from the previous subspace (Sec. IV.C)")
     ap.add_argument("--skip-fp64", action="store_true", help="do not time the plain FP64 GPU path")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed solves of the plain FP64 GPU path")
+    ap.add_argument("--fp64-warmup", type=int, default=1, help="untimed solves of the plain FP64 GPU path")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--profile-timed", action="store_true",
                     help="time kernel classes inside the timed steps (default: in one extra step after them)")
@@ -170,8 +172,10 @@ def oracle_sample(layers: int, loops: int) -> dict:
     scale = wl.Ne * nb / layers
     full_s = scale * (t_fact + loops * t_solve) + loops * t_rr
     del rhs_full
+    # fraction of a full solve's estimated time that the sample measured
+    frac = (t_fact + t_solve + t_rr) / full_s
     return dict(value=iv["M"] / full_s, full_s=full_s, sample_s=t4 - t0 - (t3 - t2), t_fact=t_fact,
-                t_solve=t_solve, t_rr=t_rr, layers=layers, loops=loops)
+                t_solve=t_solve, t_rr=t_rr, layers=layers, loops=loops, sample_fraction=frac)
 
 
 def run_cpu_sample(layers: int, loops: int) -> dict:
@@ -434,18 +438,30 @@ def run_ours(args):
         e2e = {"value": e2e_total / t_e2e, "unit": UNIT, "steps": args.e2e_steps,
                "h2d_bytes_per_step": 2 * 27 * N * 8, "d2h_bytes_per_step": N * M0 * 8 + 2 * M0 * 8}
 
-    # ---- plain FP64 GPU path, one solve (the comparison baseline)
+    # ---- plain FP64 GPU path (the comparison baseline), timed like the
+    # headline: warm-up solves on the same handle first, kernel timing off,
+    # CUDA events on the stream around each timed solve
     fp64 = None
     if not args.skip_fp64 and args.precision == "mixed" and rank0:
-        h64 = F.Handle(precision=F.FEAST_PREC_FP64, seed=Y_SEED, stream=stream.cuda_stream, profile=True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r64 = h64.feast_solve(dop, iv["lmin"], iv["lmax"], M0, Ne, wl.tol, None, lam, X, resid, allow=())
-        torch.cuda.synchronize()
-        t64 = time.perf_counter() - t0
-        fp64 = {"value": r64.m_found / t64 if r64.info.resid_max <= 1e-10 else 0.0, "unit": UNIT, "steps": 1,
-                "ms_per_step": t64 * 1e3, "loops": r64.loops, "resid_max": r64.info.resid_max,
-                "block_lu_tflops": r64.info.factor_flops / (r64.info.t_factor_ms * 1e-3) / 1e12}
+        h64 = F.Handle(precision=F.FEAST_PREC_FP64, seed=Y_SEED, stream=stream.cuda_stream)
+        for _ in range(args.fp64_warmup):
+            h64.feast_solve(dop, iv["lmin"], iv["lmax"], M0, Ne, wl.tol, None, lam, X, resid, allow=())
+        times, r64 = [], None
+        for _ in range(args.fp64_steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r64 = h64.feast_solve(dop, iv["lmin"], iv["lmax"], M0, Ne, wl.tol, None, lam, X, resid, allow=())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        t64 = statistics.median(times) * 1e-3
+        fp64 = {"value": r64.m_found / t64 if r64.info.resid_max <= 1e-10 else 0.0, "unit": UNIT,
+                "steps": args.fp64_steps, "warmup": args.fp64_warmup, "ms_per_step": t64 * 1e3,
+                "ms_each": [round(t, 1) for t in times], "loops": r64.loops, "resid_max": r64.info.resid_max,
+                "block_lu_tflops": r64.info.factor_flops / (r64.info.t_factor_ms * 1e-3) / 1e12,
+                "factor_ms": r64.info.t_factor_ms, "timing": "median of the timed solves, after warm-up, no "
+                                                             "kernel instrumentation"}
         h64.close()
 
     if not rank0:
@@ -739,28 +755,44 @@ def run_warm_sequence(args):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, on the host cores.  A
+    full oracle solve of this workload takes about a quarter of an hour, so
+    each step times a bounded sample of it (see oracle_sample) and the line
+    reports the measured sample time per step; the eigenpairs/s value is the
+    certified pair count over the full-solve time extrapolated from the
+    sample, and the line says so."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
     cores = os.cpu_count() or 1
     runs = []
+    t_steps = []
     for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         res = run_cpu_sample(args.sample_layers, args.loops)
         if i >= args.warmup:
             runs.append(res)
-    full = sum(r["full_s"] for r in runs)
-    value = 100 * len(runs) / full
+            t_steps.append(time.perf_counter() - t0)
+    iv = load_interval()
+    full = statistics.median(r["full_s"] for r in runs)
+    value = iv["M"] / full
+    frac = runs[-1]["sample_fraction"]
     cb = cpu_baseline_obj(dict(runs[-1], value=value, cores=cores))
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": full / len(runs) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * sum(t_steps) / len(t_steps), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "Q1 FE 32x32x400 (N=409600, 400 layers of 1024), 32 Gaussians seed 0, "
                                    "lowest 100 eigenpairs, M0=128, Ne=8, tol 1e-12",
                        "precision": "f64 (CPU oracle)", "parallelism": "host cores"},
+            "value_kind": "extrapolated: certified pair count / full-solve time estimated from the timed sample",
+            "step_kind": "one bounded sample of a solve (ms_per_step is the measured time of a sample step, "
+                         "process start included)",
+            "sample_fraction": frac, "full_solve_s_est": full,
+            "pairs_certified": iv["M"], "m_found": None,
+            "sample_s_per_step": sum(r["sample_s"] for r in runs) / len(runs),
             "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                                        "d2h_bytes_per_step": 0},
-            "sample_s_per_step": sum(r["sample_s"] for r in runs) / len(runs)}
+                                        "d2h_bytes_per_step": 0}}
 
 
 def main():

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <cstddef>
+#include <mutex>
 
 namespace feast {
 
@@ -61,5 +62,34 @@ struct Grid {
 };
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Set-up that the CUDA runtime keeps per device (kernel attributes such as
+// the dynamic shared-memory opt-in, occupancy probes): run once for each
+// device ordinal, with that device current, and remember the result.  A
+// process may drive several GPUs; a process-wide flag would leave every
+// device but the first without the set-up.
+constexpr int kMaxDevices = 64;
+template <class T>
+struct PerDevice {
+  std::mutex mu;
+  bool done[kMaxDevices] = {};
+  T value[kMaxDevices] = {};
+  // f() -> T runs on the first call for the current device; fail is returned
+  // when the device ordinal cannot be read.
+  template <class F>
+  T get(F&& f, T fail) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+      cudaGetLastError();
+      return fail;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done[dev]) {
+      value[dev] = f();
+      done[dev] = true;
+    }
+    return value[dev];
+  }
+};
 
 }  // namespace feast

@@ -140,13 +140,14 @@ cudaError_t gemm_bf16(cudaStream_t s, const bf16* A, int a_rows, const bf16* Bm,
       !feast::make_map_2d(&tb, Bm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, K, b_rows, K, kBN))
     return cudaErrorInvalidValue;
   constexpr size_t smem = feast::tc::Smem<kBN, 4>::kBytes;
-  static bool attr = false;   // set under the handle's single-threaded use
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(feast::tc::k_tc_gemm<kBN, 4, Epi, 1>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static feast::PerDevice<cudaError_t> attr;   // the opt-in is per device
+  if (const cudaError_t e = attr.get(
+          [] {
+            return cudaFuncSetAttribute(feast::tc::k_tc_gemm<kBN, 4, Epi, 1>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          },
+          cudaErrorInvalidDevice))
+    return e;
   feast::tc::Geom geo{0, 0, 0, 0, (K + 63) / 64};
   feast::tc::k_tc_gemm<kBN, 4, Epi, 1><<<dim3(n_tiles, m_tiles, 1), feast::tc::kThreads, smem, s>>>(ta, tb, geo, epi,
                                                                                                   status);

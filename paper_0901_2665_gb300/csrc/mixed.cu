@@ -924,18 +924,18 @@ bool make_map(CUtensorMap* map, const float* base, long long inner, long long ro
   return make_map_2d(map, base, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, inner, rows, ld, box_rows);
 }
 
-// Shared-memory attribute of a GEMM instantiation, set once per process (and
+// Shared-memory attribute of a GEMM instantiation, set once per device (and
 // before any stream capture: it is not a stream operation).
 template <int BN, int STAGES, class Epi>
 cudaError_t tc_attr() {
   constexpr size_t smem = tc::smem_bytes<BN, STAGES, Epi>();
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    attr_err =
-        cudaFuncSetAttribute(tc::k_tc_gemm<BN, STAGES, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  });
-  return attr_err;
+  static PerDevice<cudaError_t> attr;
+  return attr.get(
+      [] {
+        return cudaFuncSetAttribute(tc::k_tc_gemm<BN, STAGES, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+      },
+      cudaErrorInvalidDevice);
 }
 
 template <int BN, int STAGES, class Epi>
@@ -1436,11 +1436,17 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
   if (shape_changed) cudaMemsetAsync(w.bufs[B_BEMB], 0, bemb, s);
   const dim3 rgrid(cdiv(d.N, kResRows), Ne);
   const long long nblk = rgrid.x;
-  static std::once_flag res_once;
-  std::call_once(res_once, [] {
-    cudaFuncSetAttribute(k_mx_residual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResSmem);
-    cudaFuncSetAttribute(k_mx_residual_inc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResSmem);
-  });
+  static PerDevice<cudaError_t> res_attr;
+  if (res_attr.get(
+          [] {
+            cudaError_t e = cudaFuncSetAttribute(k_mx_residual, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kResSmem);
+            if (e == cudaSuccess)
+              e = cudaFuncSetAttribute(k_mx_residual_inc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResSmem);
+            return e;
+          },
+          cudaErrorInvalidDevice) != cudaSuccess)
+    return "refinement residual attribute rejected";
   if (!ensure(w, B_PART, sizeof(double) * 2 * (size_t)Ne * nblk, s)) return "out of device memory";
   if (!ensure(w, B_REL, sizeof(double) * Ne, s)) return "out of device memory";
   if (!ensure(w, B_ACTIVE, sizeof(int) * Ne, s)) return "out of device memory";

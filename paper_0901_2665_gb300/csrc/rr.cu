@@ -751,9 +751,9 @@ void dgemm_tall(cudaStream_t s, long long N, int m, int k, const double* Q, cons
 // co-schedule such a cluster (a non-portable size), else 8; 0 when neither
 // launches.
 int reduced_eig_cluster_size(int m) {
-  static std::once_flag once;
-  static int size16 = 0, size8 = 0;
-  std::call_once(once, [] {
+  static PerDevice<int> probe;   // per device: 16, else 8, else 0
+  const int size = probe.get([] {
+    int size16 = 0, size8 = 0;
     cudaFuncSetAttribute(k_reduced_eig_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)cl_smem_bytes(128, 8));
     cudaFuncSetAttribute(k_reduced_eig_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -774,9 +774,10 @@ int reduced_eig_cluster_size(int m) {
         (cl == 16 ? size16 : size8) = cl;
       cudaGetLastError();
     }
-  });
+    return size16 ? size16 : size8;
+  }, 0);
   if (m < kClMinM) return 0;
-  return size16 ? size16 : size8;
+  return size;
 }
 
 void reduced_eig(cudaStream_t s, int m, const double* AQ, const double* BQ, double* eps, double* Phi,
@@ -802,8 +803,9 @@ void reduced_eig(cudaStream_t s, int m, const double* AQ, const double* BQ, doub
   }
   const size_t smem = sizeof(double) * ((size_t)m * (m + 1) + 2 * (m / 2 + 2) + 2 * m) +
                       sizeof(int) * (2 * (m / 2 + 2) + 1);
-  static std::once_flag once;
-  std::call_once(once, [] { cudaFuncSetAttribute(k_reduced_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); });
+  static PerDevice<cudaError_t> attr;
+  attr.get([] { return cudaFuncSetAttribute(k_reduced_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); },
+           cudaErrorInvalidDevice);
   k_reduced_eig<<<1, 1024, smem, s>>>(m, AQ, BQ, eps, Phi, work, status);
   prof::count_launch();
 }

@@ -92,3 +92,69 @@ def test_batched_reports_failing_instance():
     assert st == F.FEAST_ERR_BQ_NOT_SPD
     assert list(sts) == [F.FEAST_OK, F.FEAST_OK, F.FEAST_ERR_BQ_NOT_SPD]
     assert "instance 2" in h.last_error()
+
+
+# instances of the 64-instance workload (workloads.batch_instances): the
+# largest (32x32x378, N = 387,072), and 24x24 / 16x16 / 24x24 ones with
+# M0 = 128, 128, 32; the last two also have the oracle's own converged
+# eigenvalues stored (oracle_eigenvalues.json)
+BATCH_SUBSET = [16, 7, 46, 45]
+
+
+def test_batch64_subset_matches_oracle():
+    """A seeded subset of the 64-instance batched workload through one
+    feast_solve_batched call on the mixed path: every count against the
+    oracle's inertia certificate nu(lmax) - nu(lmin) = M, every residual
+    recomputed by the oracle's sparse product, B-orthonormality, and the
+    eigenvalues element by element against the oracle's FEAST where it has
+    been run to convergence."""
+    import json
+    import os
+
+    import paper_0901_2665_gb300 as F
+
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    with open(os.path.join(golden, "batch_intervals.json")) as f:
+        ivs = json.load(f)
+    with open(os.path.join(golden, "oracle_eigenvalues.json")) as f:
+        gold = json.load(f)
+    allinst = workloads.batch_instances(64)
+    keep, ops, lo, hi, m0s, lams, Xs, res, hostops = [], [], [], [], [], [], [], [], []
+    for i in BATCH_SUBSET:
+        bi, iv = allinst[i], ivs[str(i)]
+        op = bi.operator()
+        A = torch.from_numpy(op.A27).cuda()
+        B = torch.from_numpy(op.B27).cuda()
+        keep += [A, B]
+        hostops.append(op)
+        ops.append(F.make_operator(op.nx, op.ny, op.nz, A, B))
+        lo.append(iv["lmin"])
+        hi.append(iv["lmax"])
+        m0s.append(bi.M0)
+        lams.append(torch.zeros(bi.M0, dtype=torch.float64, device="cuda"))
+        Xs.append(torch.zeros((bi.M0, op.N), dtype=torch.float64, device="cuda"))
+        res.append(torch.zeros(bi.M0, dtype=torch.float64, device="cuda"))
+    h = F.Handle(precision=F.FEAST_PREC_MIXED)
+    st, mf, lp, sts = h.feast_solve_batched(ops, lo, hi, m0s, 8, 1e-12, None, lams, Xs, res, workers=0)
+    assert st == F.FEAST_OK and (sts == 0).all()
+    compared = 0
+    for j, i in enumerate(BATCH_SUBSET):
+        iv, op = ivs[str(i)], hostops[j]
+        M = iv["M"]
+        assert mf[j] == M == iv["inertia_lmax"] - iv["inertia_lmin"], i
+        lam = lams[j].cpu().numpy()[:M]
+        X = back(Xs[j])[:, :M]
+        assert np.all(np.diff(lam) >= 0) and lam[0] >= iv["lmin"] and lam[-1] <= iv["lmax"]
+        Am = oracle.assemble(op.A27, op.nx, op.ny, op.nz)
+        Bm = oracle.assemble(op.B27, op.nx, op.ny, op.nz)
+        r1, _ = oracle.residuals(Am, Bm, lam, X)
+        assert r1.max() <= 1e-10, (i, r1.max())
+        assert np.abs(res[j].cpu().numpy()[:M] - r1).max() <= 1e-14, i
+        assert np.abs(X.T @ (Bm @ X) - np.eye(M)).max() <= 1e-9, i
+        g = gold.get(f"batch/{i}")
+        if g is not None:
+            ref = np.array(g["lam"])
+            assert g["m_found"] == M
+            assert np.abs(lam - ref).max() <= 1e-10 * np.abs(ref).max(), i
+            compared += 1
+    assert compared == 2

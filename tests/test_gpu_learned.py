@@ -129,7 +129,9 @@ def test_trained_network_saves_a_loop_on_held_out_instances():
     """The committed network (trained on 2000 converged instances of the
     24x24x100 family) starts FEAST on held-out instances whose intervals the
     oracle certified: same eigenvalues and residual gate as the random start,
-    one refinement loop fewer at trace tolerance 1e-10."""
+    one refinement loop fewer at trace tolerance 1e-10, and the eigenvalues
+    of the learned start equal the oracle's converged FEAST (stored for one
+    instance) to 1e-10."""
     import json
     import os
 
@@ -138,9 +140,12 @@ def test_trained_network_saves_a_loop_on_held_out_instances():
 
     with open(os.path.join(os.path.dirname(__file__), "golden", "learned_intervals.json")) as f:
         ivs = json.load(f)
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_eigenvalues.json")) as f:
+        gold = json.load(f)
     assert ivs
     net = L.load_weights()
     h = F.Handle(precision=F.FEAST_PREC_MIXED)
+    compared = 0
     for key in sorted(ivs):
         iv = ivs[key]
         op = L.operator(iv["seed"])
@@ -158,3 +163,11 @@ def test_trained_network_saves_a_loop_on_held_out_instances():
         assert np.abs(lam1 - lam0).max() <= 1e-10 * np.abs(lam0).max(), key
         assert r0.info.resid_max <= 1e-10 and r1.info.resid_max <= 1e-10, key
         assert r1.loops < r0.loops, (key, r0.loops, r1.loops)
+        g = gold.get(f"learned/{iv['seed']}")
+        if g is not None:
+            # the learned start's eigenvalues against the oracle's own FEAST
+            ref = np.array(g["lam"])
+            assert g["m_found"] == iv["M"]
+            assert np.abs(lam1 - ref).max() <= 1e-10 * np.abs(ref).max(), key
+            compared += 1
+    assert compared >= 1

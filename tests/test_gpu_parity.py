@@ -159,6 +159,46 @@ def _compare_feast(res_gpu_lam, X_gpu, m_gpu, loops_gpu, ref, op, M):
         i = j
 
 
+@pytest.mark.parametrize("nx,ny,nz,G,seed", GRIDS)
+@pytest.mark.parametrize("k", [1, 7, 40])
+def test_residuals_match_oracle_elementwise(nx, ny, nz, G, seed, k):
+    """Both residual forms of the Table I caption, column by column, against
+    the oracle's on the same seeded pairs (random vectors, so every residual is
+    O(1) and its relative rounding error ~1e-15)."""
+    op = workloads.q1_operator(nx, ny, nz, workloads.gaussian_potential(G, seed, nx, ny, nz))
+    rng = np.random.default_rng(100 + seed)
+    X = rng.standard_normal((op.N, k))
+    lam = rng.uniform(5.0, 60.0, k)
+    dop, keep = dev_op(op)
+    r1 = torch.full((k,), np.nan, dtype=torch.float64, device="cuda")
+    rp = torch.full((k,), np.nan, dtype=torch.float64, device="cuda")
+    F().Handle().feast_residuals(dop, cm(lam), cm(X), k, r1, rp)
+    A = oracle.assemble(op.A27, nx, ny, nz)
+    B = oracle.assemble(op.B27, nx, ny, nz)
+    ref1, refp = oracle.residuals(A, B, lam, X)
+    assert np.all(np.abs(r1.cpu().numpy() - ref1) <= 1e-12 * ref1)
+    assert np.all(np.abs(rp.cpu().numpy() - refp) <= 1e-12 * refp)
+
+
+def test_residuals_of_converged_pairs_match_oracle():
+    """Converged eigenpairs of the oracle's loop: the residuals are rounding
+    noise (~1e-16), so the two computations must agree to a small multiple of
+    the unit roundoff in the normalised units of each form."""
+    wl = workloads.WORKLOADS["q1_10x10x20_fp64"]
+    op = wl.operator(4)
+    lam_d, Xd = oracle.dense_generalized_eigh(op)
+    k = 12
+    lam, X = lam_d[:k], Xd[:, :k]
+    dop, keep = dev_op(op)
+    r1 = torch.zeros(k, dtype=torch.float64, device="cuda")
+    rp = torch.zeros(k, dtype=torch.float64, device="cuda")
+    F().Handle().feast_residuals(dop, cm(lam), cm(X), k, r1, rp)
+    ref1, refp = oracle.residuals(oracle.assemble(op.A27, 10, 10, 20), oracle.assemble(op.B27, 10, 10, 20), lam, X)
+    assert ref1.max() < 1e-13 and refp.max() < 1e-13
+    assert np.abs(r1.cpu().numpy() - ref1).max() <= 2e-15
+    assert np.abs(rp.cpu().numpy() - refp).max() <= 2e-14
+
+
 @pytest.mark.parametrize("key,seed,zero", [("q1_10x10x20/v0", 0, True)] +
                          [(f"q1_10x10x20/seed{s}", s, False) for s in range(5)])
 def test_feast_solve_fp64_matches_oracle(intervals, key, seed, zero):
@@ -176,10 +216,13 @@ def test_feast_solve_fp64_matches_oracle(intervals, key, seed, zero):
     _compare_feast(lam.cpu().numpy(), back(X), r.m_found, r.loops, ref, op, iv["M"])
     assert resid.cpu().numpy()[:iv["M"]].max() <= 1e-10
     assert r.info.resid_max <= 1e-10
-    # residuals of the GPU eigenpairs recomputed by the oracle
+    # residuals of the GPU eigenpairs recomputed by the oracle; the solve's own
+    # residual output agrees with them pair by pair (both are rounding noise
+    # here, so the agreement is absolute in the normalised units)
     r1, _ = oracle.residuals(oracle.assemble(op.A27, 10, 10, 20), oracle.assemble(op.B27, 10, 10, 20),
                              lam.cpu().numpy(), back(X))
     assert r1[:iv["M"]].max() <= 1e-10
+    assert np.abs(resid.cpu().numpy()[:iv["M"]] - r1[:iv["M"]]).max() <= 2e-15
     if zero:
         cf = oracle.closed_form_eigenvalues_v0(10, 10, 20)
         assert np.abs(lam.cpu().numpy()[:iv["M"]] - cf[:iv["M"]]).max() <= 1e-10 * cf[iv["M"] - 1]

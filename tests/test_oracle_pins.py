@@ -638,3 +638,23 @@ def test_hermitian_pin_catches_planted_mistakes():
     }
     for name, Q in wrong.items():
         assert np.abs(Q - Qref).max() / np.abs(Qref).max() > 1e-3, name
+
+
+def test_stored_oracle_eigenvalues_are_consistent():
+    """The stored converged oracle runs (make_oracle_eigenvalues.py) lie inside
+    their certified intervals, ascending, with the certified count, residuals
+    <= 1e-10 and the first loop never the last (Fig. 2 step 6)."""
+    with open(os.path.join(GOLDEN, "oracle_eigenvalues.json")) as f:
+        gold = json.load(f)
+    with open(os.path.join(GOLDEN, "batch_intervals.json")) as f:
+        bivs = json.load(f)
+    with open(os.path.join(GOLDEN, "learned_intervals.json")) as f:
+        livs = json.load(f)
+    assert {"batch/45", "batch/46", "learned/10000"} <= set(gold)
+    for key, g in gold.items():
+        kind, ident = key.split("/")
+        iv = (bivs if kind == "batch" else livs)[ident]
+        lam = np.array(g["lam"])
+        assert g["m_found"] == len(lam) == iv["M"] == iv["inertia_lmax"] - iv["inertia_lmin"]
+        assert np.all(np.diff(lam) >= 0) and iv["lmin"] <= lam[0] and lam[-1] <= iv["lmax"]
+        assert g["resid_max"] <= 1e-10 and g["loops"] >= 2

@@ -2,7 +2,7 @@
 eigenpairs, M0 = 128, Ne = 8) solved on the mixed path exactly as the
 benchmark times it: one handle on the current stream, the library's seeded
 random start, three solves so that the third replays its factorisation and
-sweeps from CUDA graphs.
+sweeps from CUDA graphs; and once on the plain FP64 path.
 
 The oracle cannot run FEAST at this size within a test, so the results are
 checked against what it computes one by one, and against properties that
@@ -38,7 +38,7 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 KEY, NAME, START_SEED = "q1_32x32x400/seed0", "q1_32x32x400_fp64", 1000
 
 
-def _solve_mixed(op, lmin, lmax, M0, Ne, tol, solves):
+def _solve(op, lmin, lmax, M0, Ne, tol, solves, precision="mixed"):
     """Solve `solves` times on one handle (the benchmark's form); returns the
     last result with lambda (M0,), X (N x M0) and the reported residuals."""
     import paper_0901_2665_gb300 as F
@@ -50,7 +50,8 @@ def _solve_mixed(op, lmin, lmax, M0, Ne, tol, solves):
     X = torch.zeros((M0, op.N), dtype=torch.float64, device="cuda")
     resid = torch.zeros(M0, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    h = F.Handle(precision=F.FEAST_PREC_MIXED, seed=START_SEED, stream=stream.cuda_stream)
+    prec = F.FEAST_PREC_MIXED if precision == "mixed" else F.FEAST_PREC_FP64
+    h = F.Handle(precision=prec, seed=START_SEED, stream=stream.cuda_stream)
     for _ in range(solves):
         r = h.feast_solve(dop, lmin, lmax, M0, Ne, tol, None, lam, X, resid, allow=())
     torch.cuda.synchronize()
@@ -78,8 +79,29 @@ def test_full_size_workload_as_benchmarked(intervals):
         brackets = json.load(f)["brackets"]
     op = wl.operator(0)
     M = iv["M"]
-    r, lam, X, resid = _solve_mixed(op, iv["lmin"], iv["lmax"], wl.M0, wl.Ne, wl.tol, 3)
+    r, lam, X, resid = _solve(op, iv["lmin"], iv["lmax"], wl.M0, wl.Ne, wl.tol, 3)
     assert r.info.sweep_graphs > 0
+    assert r.m_found == M == iv["inertia_lmax"] - iv["inertia_lmin"]
+    assert r.info.resid_max <= 1e-10
+    lg = lam[:M]
+    for k, b in brackets.items():
+        x = lg[int(k) - 1]
+        assert b["lo"] - 1e-10 * abs(x) <= x <= b["hi"] + 1e-10 * abs(x), (k, x, b)
+    _check_pairs(op, iv["lmin"], iv["lmax"], lg, X[:, :M], resid[:M])
+
+
+def test_full_size_workload_plain_fp64_path(intervals):
+    """The plain FP64 path (complex128 block factors and solves, the baseline
+    the other forms are compared with) on the same full-size workload, with
+    the same oracle checks: count against the inertia certificate, the
+    bracketed eigenvalues, every residual and B-orthonormality."""
+    wl = workloads.WORKLOADS[NAME]
+    iv = intervals[KEY]
+    with open(os.path.join(GOLDEN, "fullsize_brackets.json")) as f:
+        brackets = json.load(f)["brackets"]
+    op = wl.operator(0)
+    M = iv["M"]
+    r, lam, X, resid = _solve(op, iv["lmin"], iv["lmax"], wl.M0, wl.Ne, wl.tol, 1, precision="fp64")
     assert r.m_found == M == iv["inertia_lmax"] - iv["inertia_lmin"]
     assert r.info.resid_max <= 1e-10
     lg = lam[:M]
@@ -101,7 +123,7 @@ def test_full_size_zero_potential_matches_closed_form():
     lmax = 0.5 * (cf[M - 1] + cf[M])
     lmin = cf[0] - 0.5 * (cf[M] - cf[M - 1])
     assert int(((cf >= lmin) & (cf <= lmax)).sum()) == M
-    r, lam, X, resid = _solve_mixed(op, lmin, lmax, wl.M0, wl.Ne, wl.tol, 1)
+    r, lam, X, resid = _solve(op, lmin, lmax, wl.M0, wl.Ne, wl.tol, 1)
     assert r.m_found == M
     assert np.abs(lam[:M] - cf[:M]).max() <= 1e-10 * np.abs(cf[:M]).max()
     _check_pairs(op, lmin, lmax, lam[:M], X[:, :M], resid[:M])
