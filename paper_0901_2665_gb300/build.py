@@ -56,8 +56,11 @@ def _compile(src: str, force: bool, extra) -> str:
 
 
 def build(force: bool = False, verbose_ptxas: bool = False) -> str:
+    """Compiles the library; FEAST_NVCC_FLAGS (environment, space separated)
+    adds nvcc flags, e.g. -D tuning constants of the kernels."""
     os.makedirs(BUILD, exist_ok=True)
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    extra += os.environ.get("FEAST_NVCC_FLAGS", "").split()
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, force, extra), srcs))

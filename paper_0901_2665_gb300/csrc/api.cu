@@ -154,13 +154,13 @@ struct feast_handle {
   // factor and node buffers
   DevBuf F, T1, T, L, Pinv, G, Tmp, Zd, coefd, status;
   // loop buffers
-  DevBuf RHS, Q, AQf, BQf, Xb, Yb, Xout, part, AQ, BQ, eps, Phi, work, norms, normA, lam_d, perm_d, resid_d,
+  DevBuf RHS, Q, Qp, AQf, BQf, Xb, Yb, Xout, part, AQ, BQ, eps, Phi, work, norms, normA, lam_d, perm_d, resid_d,
       residp_d;
   MixedWork mixed;
   cudaEvent_t ev[8] = {};
 
   void release_all() {
-    for (DevBuf* b : {&opA, &opB, &F, &T1, &T, &L, &Pinv, &G, &Tmp, &Zd, &coefd, &status, &RHS, &Q, &AQf, &BQf,
+    for (DevBuf* b : {&opA, &opB, &F, &T1, &T, &L, &Pinv, &G, &Tmp, &Zd, &coefd, &status, &RHS, &Q, &Qp, &AQf, &BQf,
                       &Xb, &Yb, &Xout, &part, &AQ, &BQ, &eps, &Phi, &work, &norms, &normA, &lam_d, &perm_d,
                       &resid_d, &residp_d})
       b->release();
@@ -258,18 +258,25 @@ void factor_nodes(feast_handle* h, const OpView& op, int Ne, int precision) {
   }
 }
 
-// Solve the Ne node systems for RHS (N x k real) into G (Ne x N x k complex).
-void solve_nodes(feast_handle* h, const OpView& op, int Ne, int precision, const double* RHS, cplx* G, int k,
-                 double ir_tol) {
+// Solve the Ne node systems for RHS (N x k real).  G (nullable on the mixed
+// path): receives the node solutions (Ne x N x k complex).  Qp (nullable):
+// receives the node shares Re{coef_e Q_e} of the quadrature sum (Eq. 15),
+// folded in by the backward sweeps.
+void solve_nodes(feast_handle* h, const OpView& op, int Ne, int precision, const double* RHS, cplx* G, double* Qp,
+                 int k, double ir_tol) {
   const int n = op.g.n();
   if (precision == FEAST_PREC_FP64) {
     h->Tmp.ensure(sizeof(cplx) * (size_t)Ne * n * k, "solve scratch");
+    if (!G) {   // the FP64 sweeps keep their layer solutions in G
+      h->G.ensure(sizeof(cplx) * (size_t)Ne * op.g.N() * k, "node solutions");
+      G = h->G.as<cplx>();
+    }
     solve_fp64(h->stream, op.g, Ne, h->Zd.as<cplx>(), op.A27, op.B27, h->F.as<cplx>(), RHS, G, h->Tmp.as<cplx>(),
-               k);
+               k, Qp, h->coefd.as<cplx>());
   } else {
     MixedSolveStats st;
-    const char* msg = mixed_solve(h->stream, op.g, Ne, h->Zd.as<cplx>(), op.A27, op.B27, h->mixed, RHS, G, k,
-                                  ir_tol, h->opt.ir_max, &st, h->status.as<int>());
+    const char* msg = mixed_solve(h->stream, op.g, Ne, h->Zd.as<cplx>(), op.A27, op.B27, h->mixed, RHS, G, Qp,
+                                  h->coefd.as<cplx>(), k, ir_tol, h->opt.ir_max, &st, h->status.as<int>());
     if (msg) fail(FEAST_ERR_CUDA, msg);
     h->info.ir_steps_max = std::max(h->info.ir_steps_max, st.steps_max);
     if (ir_tol <= h->opt.ir_tol) h->info.ir_resid_max = std::max(h->info.ir_resid_max, st.resid_max);
@@ -418,7 +425,7 @@ feast_status feast_node_solve(feast_handle* h, const feast_operator* op, double 
     h->info.ir_resid_max = 0.0;
     factor_nodes(h, v, 1, precision);
     check_status(h);
-    solve_nodes(h, v, 1, precision, RHS, reinterpret_cast<cplx*>(Qe), k, h->opt.ir_tol);
+    solve_nodes(h, v, 1, precision, RHS, reinterpret_cast<cplx*>(Qe), nullptr, k, h->opt.ir_tol);
     check_status(h);
   });
 }
@@ -437,9 +444,9 @@ feast_status feast_quadrature(feast_handle* h, const feast_operator* op, double 
     h->info.ir_resid_max = 0.0;
     factor_nodes(h, v, Ne, precision);
     check_status(h);
-    h->G.ensure(sizeof(cplx) * (size_t)Ne * N * k, "node solutions");
-    solve_nodes(h, v, Ne, precision, RHS, h->G.as<cplx>(), k, h->opt.ir_tol);
-    quadrature_sum(h->stream, N, k, Ne, h->coefd.as<cplx>(), h->G.as<cplx>(), N * k, Q);
+    h->Qp.ensure(sizeof(double) * (size_t)Ne * N * k, "quadrature shares");
+    solve_nodes(h, v, Ne, precision, RHS, nullptr, h->Qp.as<double>(), k, h->opt.ir_tol);
+    quadrature_sum(h->stream, N, k, Ne, h->Qp.as<double>(), N * k, Q);
     check_status(h);
   });
 }
@@ -524,7 +531,7 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
     h->Xb.ensure(blk, "X");
     h->Yb.ensure(blk, "Y");
     h->Xout.ensure(blk, "X out");
-    h->G.ensure(sizeof(cplx) * (size_t)Ne * N * M0, "node solutions");
+    h->Qp.ensure(sizeof(double) * (size_t)Ne * N * M0, "quadrature shares");
     h->eps.ensure(sizeof(double) * M0, "eps");
     h->lam_d.ensure(sizeof(double) * M0, "lambda");
     h->perm_d.ensure(sizeof(int) * M0, "perm");
@@ -555,8 +562,8 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
       if (h->opt.ir_early && !Y0 && prec == FEAST_PREC_MIXED && loop <= 2)
         ir_loop = std::max(ir_loop, loop == 1 ? 1e-5 : 1e-8);
       const bool exact_loop = ir_loop <= h->opt.ir_tol;
-      solve_nodes(h, v, Ne, prec, h->RHS.as<double>(), h->G.as<cplx>(), M0, ir_loop);
-      quadrature_sum(s, N, M0, Ne, h->coefd.as<cplx>(), h->G.as<cplx>(), N * M0, h->Q.as<double>());
+      solve_nodes(h, v, Ne, prec, h->RHS.as<double>(), nullptr, h->Qp.as<double>(), M0, ir_loop);
+      quadrature_sum(s, N, M0, Ne, h->Qp.as<double>(), N * M0, h->Q.as<double>());
       ck(cudaEventRecord(h->ev[3], s), "event");
       // steps 3-5: Rayleigh-Ritz
       rayleigh_ritz_dev(h, v, h->Q.as<double>(), M0, h->eps.as<double>(), h->Xb.as<double>(), nullptr, nullptr);
@@ -648,11 +655,11 @@ static double instance_bytes(const feast_operator& op, int M0, int Ne, int preci
   const double N = (double)op.nx * op.ny * op.nz, n = (double)op.nx * op.ny;
   const double ldF = std::ceil(2.0 * n / 32.0) * 32.0;
   const double blk = 8.0 * N * M0;
-  double b = 16.0 * N * M0 * Ne + 12.0 * blk + 2.0 * 27.0 * N * 8.0;
+  double b = 8.0 * N * M0 * Ne + 12.0 * blk + 2.0 * 27.0 * N * 8.0;   // quadrature shares, loop blocks, operator
   if (precision == FEAST_PREC_MIXED)
-    b += 4.0 * Ne * op.nz * n * ldF + 8.0 * Ne * 27.0 * N + 2.0 * 8.0 * N * M0 * Ne + 4.0 * Ne * 3.0 * n * ldF;
+    b += 4.0 * Ne * op.nz * n * ldF + 8.0 * Ne * 27.0 * N + 3.0 * 8.0 * N * M0 * Ne + 4.0 * Ne * 3.0 * n * ldF;
   else
-    b += 16.0 * Ne * op.nz * n * n + 16.0 * Ne * n * n;
+    b += 16.0 * Ne * op.nz * n * n + 16.0 * Ne * n * n + 16.0 * N * M0 * Ne;
   return b * 1.05 + 64.0 * 1024 * 1024;
 }
 

@@ -235,11 +235,14 @@ __global__ void __launch_bounds__(256) k_sweep_update(cplx* __restrict__ Sall, l
   }
 }
 
-// ---- C = alpha * S X, S n x n (symmetric, row-major), X, C n x k col-major
+// ---- C = alpha * S X, S n x n (symmetric, row-major), X, C n x k col-major.
+// With qp set (the backward sweep) each entry c of C is also folded into the
+// node's share of the quadrature sum (Eq. 15): qp[e*sQ + m*ldq + p] = Re{coef_e c}.
 __global__ void __launch_bounds__(256) k_zgemm_sym(int n, int k, double alpha, const cplx* __restrict__ Sall,
                                                    long long sS, const cplx* __restrict__ Xall, long long ldx,
                                                    long long sX, cplx* __restrict__ Call, long long ldc,
-                                                   long long sC) {
+                                                   long long sC, double* __restrict__ qp, long long sQ,
+                                                   long long ldq, const cplx* __restrict__ coef) {
   constexpr int BM = 64, BN = 32, BK = 16;
   __shared__ cplx As[BK][BM];
   __shared__ cplx Bs[BK][BN];
@@ -277,6 +280,7 @@ __global__ void __launch_bounds__(256) k_zgemm_sym(int n, int k, double alpha, c
     __syncthreads();
   }
   cplx* C = Call + e * sC;
+  const cplx ce = qp ? coef[e] : cplx{0.0, 0.0};
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int p = p0 + ty + 16 * r;
@@ -285,7 +289,9 @@ __global__ void __launch_bounds__(256) k_zgemm_sym(int n, int k, double alpha, c
     for (int c = 0; c < 2; ++c) {
       const int m = m0 + tx + 16 * c;
       if (m >= k) continue;
-      C[(long long)m * ldc + p] = cplx{alpha * acc[r][c].re, alpha * acc[r][c].im};
+      const cplx v{alpha * acc[r][c].re, alpha * acc[r][c].im};
+      C[(long long)m * ldc + p] = v;
+      if (qp) qp[e * sQ + (long long)m * ldq + p] = ce.re * v.re - ce.im * v.im;
     }
   }
 }
@@ -293,9 +299,10 @@ __global__ void __launch_bounds__(256) k_zgemm_sym(int n, int k, double alpha, c
 }  // namespace
 
 void zgemm_sym(cudaStream_t s, int n, int k, int Ne, double alpha, const cplx* S, long long sS, const cplx* X,
-               long long ldx, long long sX, cplx* C, long long ldc, long long sC) {
+               long long ldx, long long sX, cplx* C, long long ldc, long long sC, double* qp, long long sQ,
+               long long ldq, const cplx* coef) {
   dim3 grid(cdiv(k, 32), cdiv(n, 64), Ne);
-  k_zgemm_sym<<<grid, 256, 0, s>>>(n, k, alpha, S, sS, X, ldx, sX, C, ldc, sC);
+  k_zgemm_sym<<<grid, 256, 0, s>>>(n, k, alpha, S, sS, X, ldx, sX, C, ldc, sC, qp, sQ, ldq, coef);
   prof::count_launch();
 }
 
@@ -325,7 +332,7 @@ void factor_fp64(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A2
 }
 
 void solve_fp64(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
-                const cplx* F, const double* RHS, cplx* G, cplx* Tmp, int k) {
+                const cplx* F, const double* RHS, cplx* G, cplx* Tmp, int k, double* Qp, const cplx* coef) {
   const int n = g.n(), nb = g.nz;
   const long long N = g.N();
   const long long nn = (long long)n * n;
@@ -341,7 +348,8 @@ void solve_fp64(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27
   // backward sweep (x_i overwrites g_i)
   for (int i = nb - 1; i >= 0; --i) {
     couple_backward(s, g, i, Ne, Z, A27, B27, G, sG, Tmp, sT, k);
-    zgemm_sym(s, n, k, Ne, -1.0, F + (long long)i * nn, sF, Tmp, n, sT, G + (long long)i * n, N, sG);
+    zgemm_sym(s, n, k, Ne, -1.0, F + (long long)i * nn, sF, Tmp, n, sT, G + (long long)i * n, N, sG,
+              Qp ? Qp + (long long)i * n : nullptr, sG, N, coef);
   }
 }
 

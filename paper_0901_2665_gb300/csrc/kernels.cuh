@@ -24,9 +24,10 @@ void couple_forward(cudaStream_t s, Grid g, int layer, int Ne, const cplx* Z, co
 // backward: Tmp_e = G_e[layer i] - U_i G_e[layer i+1]    (U_i = M[i, i+1])
 void couple_backward(cudaStream_t s, Grid g, int layer, int Ne, const cplx* Z, const double* A27,
                      const double* B27, const cplx* G, long long sG, cplx* Tmp, long long sT, int k);
-// Q = sum_e Re(coef_e G_e) summed in node order (Eq. 15 with coef_e = -(w_e/2) r e^{i theta_e}).
-void quadrature_sum(cudaStream_t s, long long N, int k, int Ne, const cplx* coef, const cplx* G,
-                    long long sG, double* Q);
+// Q = sum_e Qp_e in node order e = 1..Ne (Eq. 15): Qp holds the node shares
+// Re{coef_e Q_e}, coef_e = -(w_e/2) r e^{i theta_e}, written by the backward
+// sweeps (node stride sQ); Q: N x k.
+void quadrature_sum(cudaStream_t s, long long N, int k, int Ne, const double* Qp, long long sQ, double* Q);
 // Copy a real RHS into complex G (imaginary part 0) for rows [0, n) of every node.
 void rhs_to_complex(cudaStream_t s, long long rows, int k, int Ne, const double* RHS, long long ldr,
                     cplx* G, long long ldg, long long sG);
@@ -45,11 +46,16 @@ struct Fp64Work {
 void factor_fp64(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
                  const Fp64Work& w);
 // C_e = alpha * S_e X_e for symmetric n x n S (row-major), X, C: n x k complex col-major.
+// qp (nullable): qp_e[m*ldq + p] = Re{coef_e C_e[p, m]} (node stride sQ).
 void zgemm_sym(cudaStream_t s, int n, int k, int Ne, double alpha, const cplx* S, long long sS,
-               const cplx* X, long long ldx, long long sX, cplx* C, long long ldc, long long sC);
+               const cplx* X, long long ldx, long long sX, cplx* C, long long ldc, long long sC,
+               double* qp = nullptr, long long sQ = 0, long long ldq = 0, const cplx* coef = nullptr);
 // Solve M_e G_e = RHS for all nodes with the FP64 factors; G: Ne x (N x k complex).
+// Qp (nullable): the node shares Re{coef_e G_e} of Eq. 15 (Ne x N x k real),
+// written by the backward sweep's products.
 void solve_fp64(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
-                const cplx* F, const double* RHS, cplx* G, cplx* Tmp, int k);
+                const cplx* F, const double* RHS, cplx* G, cplx* Tmp, int k, double* Qp = nullptr,
+                const cplx* coef = nullptr);
 
 // ---------------------------------------------------------------- rr.cu
 // out (k1 x k2, col-major, ld k1) = X^T Y, X: N x k1, Y: N x k2 (col-major, ld N).

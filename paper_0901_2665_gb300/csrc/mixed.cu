@@ -255,6 +255,113 @@ __global__ void __launch_bounds__(kPinvThreads) k_mx_pinv(Dims d, int layer, int
   if (tid == 0 && bad) atomicExch(status, (int)DEV_PIVOT);
 }
 
+// The same Gauss-Jordan sweep with fewer, fuller threads: thread t holds
+// column j = t % 64 of the RPT consecutive rows h RPT + a (a < RPT),
+// h = t / 64, so a CTA has 64 * (64 / RPT) threads.  Per pivot a thread reads
+// the pivot's reciprocal, its own entry of the pivot row and the RPT entries
+// of the pivot column that its rows need (a warp-wide broadcast, two complex
+// values per 16-byte load), and applies RPT complex FMAs; the per-pivot
+// overhead (barrier, reciprocal, selects) is shared by 2 RPT FMAs instead of
+// 8.  The pivot loop is unrolled within a row block so that every register
+// index is a compile-time constant.  Arithmetic and publication order are
+// those of k_mx_pinv.
+template <int RPT>
+__global__ void __launch_bounds__(kPanel * (kPanel / RPT)) k_mx_pinv_cols(Dims d, int layer, int k0, int bw,
+                                                                         const float* __restrict__ F,
+                                                                         f2* __restrict__ PinvOut, int* status) {
+  constexpr int H = kPanel / RPT;   // row blocks
+  static_assert(RPT % 2 == 0 && kPanel % RPT == 0, "rows per thread");
+  __shared__ __align__(16) f2 rowb[2][kPanel];   // row k of P before pivot k
+  __shared__ __align__(16) f2 colb[2][kPanel];   // column k of P before pivot k
+  __shared__ f2 invb[2];                         // 1 / P[k, k] before pivot k
+  __shared__ int bad;
+  const int e = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int j = tid % kPanel, h = tid / kPanel;
+  const int n = d.n;
+  const float* Fl = F + ((long long)e * 2 + (layer & 1)) * n * d.ldF;
+  if (tid == 0) bad = 0;
+  f2 v[RPT];
+#pragma unroll
+  for (int a = 0; a < RPT; ++a) {
+    const int i = h * RPT + a;
+    f2 x{(i == j) ? 1.f : 0.f, 0.f};
+    if (i < bw && j < bw) {
+      const float* row = Fl + (long long)(k0 + i) * d.ldF;
+      x = f2{row[k0 + j], row[n + k0 + j]};
+    }
+    v[a] = x;
+  }
+  __syncthreads();   // `bad` initialised
+  // publish pivot kn = hb RPT + idx (idx a compile-time constant after
+  // unrolling): its row from the row block hb, its reciprocal from its
+  // holder, its column (cleared afterwards, see k_mx_pinv) from column kn
+  auto publish = [&](int hb, int idx, int kn, int buf) {
+    if (h == hb) {
+      const f2 x = v[idx];
+      rowb[buf][j] = x;
+      if (j == kn) {
+        const float mag = fabsf(x.x) + fabsf(x.y);
+        const bool good = mag > 0.f && isfinite(mag);
+        if (!good) bad = 1;
+        invb[buf] = good ? f2inv_fast(x) : f2{0.f, 0.f};
+      }
+    }
+    if (j == kn) {
+#pragma unroll
+      for (int a = 0; a < RPT; a += 2) {
+        *reinterpret_cast<float4*>(&colb[buf][h * RPT + a]) = make_float4(v[a].x, v[a].y, v[a + 1].x, v[a + 1].y);
+        v[a] = f2{0.f, 0.f};
+        v[a + 1] = f2{0.f, 0.f};
+      }
+    }
+  };
+  publish(0, 0, 0, 0);
+  __syncthreads();
+#pragma unroll 1
+  for (int hk = 0; hk < H; ++hk) {
+#pragma unroll
+    for (int kk = 0; kk < RPT; ++kk) {
+      const int k = hk * RPT + kk;
+      const int b = k & 1;
+      const f2 inv = invb[b];
+      const f2 rki = f2mul(rowb[b][j], inv);   // P[k, j] / p
+      const f2 r = (j == k) ? f2{-inv.x, -inv.y} : rki;
+#pragma unroll
+      for (int a = 0; a < RPT; a += 2) {
+        const float4 c2 = *reinterpret_cast<const float4*>(&colb[b][h * RPT + a]);
+        v[a].x = fmaf(-c2.x, r.x, v[a].x);
+        v[a].x = fmaf(c2.y, r.y, v[a].x);
+        v[a].y = fmaf(-c2.x, r.y, v[a].y);
+        v[a].y = fmaf(-c2.y, r.x, v[a].y);
+        v[a + 1].x = fmaf(-c2.z, r.x, v[a + 1].x);
+        v[a + 1].x = fmaf(c2.w, r.y, v[a + 1].x);
+        v[a + 1].y = fmaf(-c2.z, r.y, v[a + 1].y);
+        v[a + 1].y = fmaf(-c2.w, r.x, v[a + 1].y);
+      }
+      // pivot row: P[k, j] = P[k, j] / p, and P[k, k] = -1 / p
+      if (h == hk) v[kk] = (j == k) ? f2{-inv.x, -inv.y} : rki;
+      if (k + 1 < kPanel) {
+        if (kk + 1 < RPT) publish(hk, kk + 1, k + 1, b ^ 1);
+        else publish(hk + 1, 0, k + 1, b ^ 1);
+      }
+      __syncthreads();
+    }
+  }
+  // P holds -S[K,K]^{-1}
+#pragma unroll
+  for (int a = 0; a < RPT; ++a) {
+    const int i = h * RPT + a;
+    PinvOut[(long long)e * kPanel * kPanel + i * kPanel + j] = f2{-v[a].x, -v[a].y};
+  }
+  if (tid == 0 && bad) atomicExch(status, (int)DEV_PIVOT);
+}
+
+#ifndef FEAST_PINV_RPT
+#define FEAST_PINV_RPT 32
+#endif
+constexpr int kPinvRpt = FEAST_PINV_RPT;   // rows per thread of the panel inverse
+
 // For panel K and this CTA's kRowsPerPanelCta rows i:  T[i, :] = S[i, K] Pinv  and
 // L[i, :] = S[i, K], written as the TF32-rounded GEMM operands
 // Aop = [Tr | Ti] (row i) and Bop (embedded L, rows in blocks of 64 complex
@@ -560,15 +667,27 @@ struct SweepEpiTma {
 
 // Solve product: out[m*ldo + p] = alpha * (S' g)[p, m] (complex64); lanes are
 // consecutive rows p, so the stores of a warp are contiguous.
+// With qp set (the backward sweep of feast_solve / feast_quadrature) the
+// epilogue also folds the layer's solution x into the node's share of the
+// quadrature sum (Eq. 15):  qp[m*ldq + p] (= or +=) Re{coef_e x}  in FP64,
+// coef_e = -(w_e/2) r e^{i theta_e}.  x of the first solve is Q_e itself and
+// x of each refinement step is its correction, so after the last step the
+// node's share is Re{coef_e Q_e}, without Q_e ever being stored.
 template <int CB>
 struct SolveEpi {
   f2* out;
   long long sOut, ldo;
   int n, k;
   float alpha;
+  double* qp = nullptr;        // per-node quadrature partials (row offset of the layer applied)
+  long long sQ = 0, ldq = 0;   // node stride, column stride
+  const cplx* coef = nullptr;  // Ne quadrature coefficients
+  int qfirst = 0;              // 1: store (first solve), 0: accumulate (refinement)
   __device__ void operator()(int e, int tm, int tn, int row, uint32_t taddr, int, uint8_t*) const {
     const int p = tm * tc::kBlockM + row;
     f2* o = out + e * sOut;
+    cplx ce{0.0, 0.0};
+    if (qp) ce = coef[e];
 #pragma unroll 1
     for (int c0 = 0; c0 < CB; c0 += 16) {
       float re[16], im[16];
@@ -578,7 +697,15 @@ struct SolveEpi {
 #pragma unroll
       for (int t = 0; t < 16; ++t) {
         const int m = tn * CB + c0 + t;
-        if (c0 + t < CB && m < k) o[(long long)m * ldo + p] = f2{alpha * re[t], alpha * im[t]};
+        if (c0 + t < CB && m < k) {
+          const f2 x{alpha * re[t], alpha * im[t]};
+          o[(long long)m * ldo + p] = x;
+          if (qp) {
+            double* q = qp + e * sQ + (long long)m * ldq + p;
+            const double v = ce.re * (double)x.x - ce.im * (double)x.y;
+            *q = qfirst ? v : *q + v;
+          }
+        }
       }
     }
   }
@@ -686,11 +813,15 @@ __global__ void k_mx_accumulate(long long total, int first, const f2* __restrict
 }
 
 constexpr int kResRows = 128;      // grid rows per block
+// Refinement targets at or above this take their first residual in
+// double-float as well (its error, ~1e-12 of ||RHS||, is far below them).
+constexpr double kFFirstTol = 1e-9;
 constexpr int kResThreads = 256;   // two columns in flight per row
 constexpr size_t kResSmem = sizeof(cplx) * 27 * kResRows;
 
 // R_e = RHS - (Z_e B - A) Q_e in FP64 (108 FP64 FMAs per complex entry, the
-// only FP64 arithmetic of the kernel): the block's 128 rows keep their 27
+// only FP64 arithmetic of the kernel) for the first solve's Q_e, which is its
+// complex64 sweep output exactly: the block's 128 rows keep their 27
 // complex coefficients in shared memory while the threads sweep the columns.
 // Stores R in FP64 (R64, the start of the incremental residuals) and as
 // complex64 (the next correction's right-hand side), and per-block partial
@@ -699,7 +830,7 @@ __global__ void __launch_bounds__(kResThreads) k_mx_residual(Dims d, const cplx*
                                                              const double* __restrict__ A27,
                                                              const double* __restrict__ B27,
                                                              const double* __restrict__ RHS,
-                                                             const cplx* __restrict__ Q, f2* __restrict__ Rc,
+                                                             const f2* __restrict__ Q, f2* __restrict__ Rc,
                                                              cplx* __restrict__ R64, double* __restrict__ partial,
                                                              const int* __restrict__ active) {
   extern __shared__ cplx rsm[];
@@ -739,13 +870,14 @@ __global__ void __launch_bounds__(kResThreads) k_mx_residual(Dims d, const cplx*
     }
     const long long sG = d.N * d.k;
     for (int m = tid / kResRows; m < d.k; m += kResThreads / kResRows) {
-      const cplx* q = Q + e * sG + (long long)m * d.N + i;
+      const f2* q = Q + e * sG + (long long)m * d.N + i;
       const double b = RHS[(long long)m * d.N + i];
       double are = b, aim = 0.0;
 #pragma unroll
       for (int s = 0; s < 27; ++s) {
         const cplx c = rsm[s * kResRows + r];
-        const cplx v = q[off[s]];
+        const f2 v32 = q[off[s]];
+        const cplx v{(double)v32.x, (double)v32.y};
         are = fma(-c.re, v.re, are);
         are = fma(c.im, v.im, are);
         aim = fma(-c.re, v.im, aim);
@@ -799,14 +931,21 @@ __device__ __forceinline__ void ff_axpy(float ch, float cl, float v, float& sh, 
 
 // R64 <- R64 - (Z_e B - A) delta, Rc <- complex64(R64), partial |R|^2 per block
 // (the |RHS|^2 partials of the first residual are kept).
+// kFirst: the first residual of a solve whose target is loose (>= 1e-9
+// relative): R64 starts from RHS instead, delta is the first solution Q_e,
+// and the |RHS|^2 partials are written.  The product's error, ~2^-48 kappa
+// ||Q_e|| (kappa ~ 300 here), is then far below the target.
+template <bool kFirst>
 __global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, const cplx* __restrict__ Z,
                                                                  const double* __restrict__ A27,
                                                                  const double* __restrict__ B27,
                                                                  const f2* __restrict__ delta, f2* __restrict__ Rc,
                                                                  cplx* __restrict__ R64, double* __restrict__ partial,
-                                                                 const int* __restrict__ active) {
+                                                                 const int* __restrict__ active,
+                                                                 const double* __restrict__ RHS) {
   extern __shared__ float4 csm[];   // per (slot, row): Re c hi/lo, Im c hi/lo
   __shared__ double red[kResThreads];
+  __shared__ double redb[kFirst ? kResThreads : 1];
   const int e = blockIdx.y;
   const int tid = threadIdx.x;
   if (!active[e]) return;
@@ -833,7 +972,7 @@ __global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, cons
   __syncthreads();
   const int r = tid % kResRows;
   const long long i = i0 + r;
-  double rr = 0.0;
+  double rr = 0.0, bb = 0.0;
   if (i < d.N) {
     const int ix = (int)(i % d.nx), iy = (int)((i / d.nx) % d.ny), iz = (int)(i / d.n);
     // neighbour validity per axis; an absent neighbour has a zero coefficient
@@ -869,7 +1008,14 @@ __global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, cons
       }
       {
         const long long at = e * sG + (long long)m * d.N + i;
-        cplx R = R64[at];
+        cplx R;
+        if constexpr (kFirst) {
+          const double b = RHS[(long long)m * d.N + i];
+          R = cplx{b, 0.0};
+          bb += b * b;
+        } else {
+          R = R64[at];
+        }
         R.re -= (double)ah + (double)al;
         R.im -= (double)bh + (double)bl;
         R64[at] = R;
@@ -878,7 +1024,14 @@ __global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, cons
       }
       if (two) {
         const long long at = e * sG + (long long)(m + kGroups) * d.N + i;
-        cplx R = R64[at];
+        cplx R;
+        if constexpr (kFirst) {
+          const double b = RHS[(long long)(m + kGroups) * d.N + i];
+          R = cplx{b, 0.0};
+          bb += b * b;
+        } else {
+          R = R64[at];
+        }
         R.re -= (double)ch + (double)cl;
         R.im -= (double)eh + (double)el;
         R64[at] = R;
@@ -888,12 +1041,19 @@ __global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, cons
     }
   }
   red[tid] = rr;
+  if constexpr (kFirst) redb[tid] = bb;
   __syncthreads();
   for (int w = kResThreads / 2; w > 0; w >>= 1) {
-    if (tid < w) red[tid] += red[tid + w];
+    if (tid < w) {
+      red[tid] += red[tid + w];
+      if constexpr (kFirst) redb[tid] += redb[tid + w];
+    }
     __syncthreads();
   }
-  if (tid == 0) partial[((long long)e * gridDim.x + blockIdx.x) * 2] = red[0];
+  if (tid == 0) {
+    partial[((long long)e * gridDim.x + blockIdx.x) * 2] = red[0];
+    if constexpr (kFirst) partial[((long long)e * gridDim.x + blockIdx.x) * 2 + 1] = redb[0];
+  }
 }
 
 // rel[e] = sqrt(sum |R|^2 / sum |RHS|^2), blocks summed in order
@@ -1083,7 +1243,7 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
       const int k0 = kp * kPanel, bw = std::min(kPanel, d.n - k0), q = kp & 1;
       prof::begin(st, prof::PINV);
       prof::add_work(prof::PINV, 8.0 * kPanel * kPanel * kPanel * Ne);
-      k_mx_pinv<<<Ne, kPinvThreads, 0, st>>>(d, layer, k0, bw, F, Pv[q], status);
+      k_mx_pinv_cols<kPinvRpt><<<Ne, kPanel * (kPanel / kPinvRpt), 0, st>>>(d, layer, k0, bw, F, Pv[q], status);
       prof::end(st, prof::PINV);
       prof::begin(st, prof::PANEL_T);
       prof::add_work(prof::PANEL_T, 8.0 * d.n * kPanel * kPanel * Ne);
@@ -1211,9 +1371,20 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
 
 namespace {
 
+// Where the backward sweep folds its solutions into the quadrature sum
+// (Eq. 15): per-node partials qp (N x k, node stride N k), the coefficients,
+// and whether this sweep stores (the first solve) or accumulates (a
+// refinement step).  qp == nullptr: no folding.
+struct QuadOut {
+  double* qp;
+  const cplx* coef;
+  int first;
+};
+
 template <int CB>
 const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const double* A27, const double* B27,
-                         MixedWork& w, const double* Rreal, const f2* Rc, const NodeList& nl, int* status) {
+                         MixedWork& w, const double* Rreal, const f2* Rc, const NodeList& nl, const QuadOut& qo,
+                         int* status) {
   float* F = buf<float>(w, B_F);
   f2* Gc = buf<f2>(w, B_GC);
   f2* Tout = buf<f2>(w, B_TOUT);
@@ -1259,6 +1430,13 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     k_mx_couple_bwd<<<cgrid, 128, 0, s>>>(d, i, Cf, Gc, Bemb, nl);
     prof::end(s, prof::COUPLE);
     SolveEpi<CB> epi{Gc + (long long)i * d.n, d.N * d.k, d.N, d.n, d.k, -1.0f};
+    if (qo.qp) {
+      epi.qp = qo.qp + (long long)i * d.n;
+      epi.sQ = d.N * d.k;
+      epi.ldq = d.N;
+      epi.coef = qo.coef;
+      epi.qfirst = qo.first;
+    }
     tc::Geom geo = geo0;
     geo.a_row0 = i * d.n;
     prof::begin(s, prof::SOLVE_GEMM);
@@ -1333,12 +1511,13 @@ int tuned_cb(cudaStream_t s, const Dims& d, MixedWork& w, int* status) {
 }
 
 const char* solve_direct(cudaStream_t s, const Dims& d, const cplx* Z, const double* A27, const double* B27,
-                         MixedWork& w, const double* Rreal, const f2* Rc, const NodeList& nl, int* status) {
+                         MixedWork& w, const double* Rreal, const f2* Rc, const NodeList& nl, const QuadOut& qo,
+                         int* status) {
   switch (d.CB) {
-    case 8: return solve_sweeps<8>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
-    case 16: return solve_sweeps<16>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
-    case 32: return solve_sweeps<32>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
-    default: return solve_sweeps<64>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+    case 8: return solve_sweeps<8>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
+    case 16: return solve_sweeps<16>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
+    case 32: return solve_sweeps<32>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
+    default: return solve_sweeps<64>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
   }
 }
 
@@ -1348,7 +1527,7 @@ const char* solve_direct(cudaStream_t s, const Dims& d, const cplx* Z, const dou
 // back to direct launches.
 const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const double* A27, const double* B27,
                        MixedWork& w, const double* Rreal, const f2* Rc, const std::vector<int>& active,
-                       MixedSolveStats* stats, int* status) {
+                       const QuadOut& qo, MixedSolveStats* stats, int* status) {
   NodeList nl{0, 0ULL};
   for (int e = 0; e < d.Ne; ++e)
     if (active[e]) {
@@ -1356,7 +1535,7 @@ const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const doubl
       ++nl.count;
     }
   if (nl.count == 0) return nullptr;
-  if (prof::enabled() || !w.use_graphs) return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+  if (prof::enabled() || !w.use_graphs) return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
   const unsigned long long key[kSweepKey] = {
       (unsigned long long)d.nx | ((unsigned long long)d.ny << 20) | ((unsigned long long)d.nz << 40),
       (unsigned long long)d.k | ((unsigned long long)d.CB << 20) | ((unsigned long long)d.Ne << 40),
@@ -1365,7 +1544,9 @@ const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const doubl
       (unsigned long long)(uintptr_t)A27, (unsigned long long)(uintptr_t)B27, (unsigned long long)(uintptr_t)status,
       (unsigned long long)(uintptr_t)w.bufs[B_F], (unsigned long long)(uintptr_t)w.bufs[B_GC],
       (unsigned long long)(uintptr_t)w.bufs[B_TOUT], (unsigned long long)(uintptr_t)w.bufs[B_BEMB],
-      (unsigned long long)(uintptr_t)w.bufs[B_CF], (unsigned long long)d.ldF, 1ULL};
+      (unsigned long long)(uintptr_t)w.bufs[B_CF], (unsigned long long)d.ldF, 1ULL,
+      (unsigned long long)(uintptr_t)qo.qp, (unsigned long long)(uintptr_t)qo.coef, (unsigned long long)qo.first,
+      0ULL};
   SweepGraphCache& gc = w.graphs;
   ++gc.clock;
   for (int g = 0; g < kSweepGraphs; ++g) {
@@ -1382,17 +1563,17 @@ const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const doubl
   if (!seen) {
     std::memcpy(gc.seen[gc.seen_next], key, sizeof(key));
     gc.seen_next = (gc.seen_next + 1) % kSweepGraphs;
-    return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+    return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
   }
   // second sighting: capture
   cudaGraph_t graph = nullptr;
   cudaStream_t cs = capture_stream(w);
   if (!cs || cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
-    return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+    return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
   }
   const long long launches0 = prof::launches();
-  const char* msg = solve_direct(cs, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+  const char* msg = solve_direct(cs, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
   const cudaError_t end = cudaStreamEndCapture(cs, &graph);
   cudaGraphExec_t exec = nullptr;
   if (msg || end != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
@@ -1400,7 +1581,7 @@ const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const doubl
     cudaGetLastError();
     prof::count_launch(launches0 - prof::launches());   // nothing of the capture ran
     if (msg) return msg;
-    return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+    return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
   }
   cudaGraphDestroy(graph);
   int slot = 0;
@@ -1418,8 +1599,8 @@ const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const doubl
 }  // namespace
 
 const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
-                        MixedWork& w, const double* RHS, cplx* G, int k, double ir_tol, int ir_max,
-                        MixedSolveStats* stats, int* status) {
+                        MixedWork& w, const double* RHS, cplx* G, double* Qp, const cplx* coef, int k, double ir_tol,
+                        int ir_max, MixedSolveStats* stats, int* status) {
   Dims d = make_dims(g, Ne, k);
   if (w.nz_factored != d.nz || w.ne_factored != Ne) return "mixed solve called without matching factors";
   const long long sG = d.N * k;
@@ -1442,7 +1623,11 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
             cudaError_t e = cudaFuncSetAttribute(k_mx_residual, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)kResSmem);
             if (e == cudaSuccess)
-              e = cudaFuncSetAttribute(k_mx_residual_inc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResSmem);
+              e = cudaFuncSetAttribute(k_mx_residual_inc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kResSmem);
+            if (e == cudaSuccess)
+              e = cudaFuncSetAttribute(k_mx_residual_inc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kResSmem);
             return e;
           },
           cudaErrorInvalidDevice) != cudaSuccess)
@@ -1456,19 +1641,30 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
   std::vector<double> rel(Ne, 0.0), final_rel(Ne, 0.0);
   const int acc_blocks = (int)std::min<long long>(4096, (sG + 255) / 256);
   // first solve: Q_e = M~^{-1} RHS
-  if (const char* m = solve_once(s, d, Z, A27, B27, w, RHS, nullptr, active, stats, status)) return m;
-  k_mx_accumulate<<<dim3(acc_blocks, Ne), 256, 0, s>>>(sG, 1, buf<f2>(w, B_GC), G, buf<int>(w, B_ACTIVE));
-  prof::count_launch();
+  if (const char* m = solve_once(s, d, Z, A27, B27, w, RHS, nullptr, active, QuadOut{Qp, coef, 1}, stats, status))
+    return m;
+  if (G) {
+    k_mx_accumulate<<<dim3(acc_blocks, Ne), 256, 0, s>>>(sG, 1, buf<f2>(w, B_GC), G, buf<int>(w, B_ACTIVE));
+    prof::count_launch();
+  }
   int steps = 0;
   for (;;) {
     {
       int nact = 0;
       for (int e = 0; e < Ne; ++e) nact += active[e];
-      if (steps == 0) {
+      if (steps == 0 && ir_tol >= kFFirstTol) {
+        // a loose target: the first residual in double-float from Q_e too
+        prof::begin(s, prof::FF_RESIDUAL);
+        prof::add_work(prof::FF_RESIDUAL, 216.0 * (double)d.N * k * nact);
+        k_mx_residual_inc<true><<<rgrid, kResThreads, kResSmem, s>>>(
+            d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<cplx>(w, B_R64), buf<double>(w, B_PART),
+            buf<int>(w, B_ACTIVE), RHS);
+        prof::end(s, prof::FF_RESIDUAL);
+      } else if (steps == 0) {
         // the first residual in FP64 from Q_e itself
         prof::begin(s, prof::RESIDUAL);
         prof::add_work(prof::RESIDUAL, 216.0 * (double)d.N * k * nact);   // 108 FP64 FMAs per complex entry
-        k_mx_residual<<<rgrid, kResThreads, kResSmem, s>>>(d, Z, A27, B27, RHS, G, buf<f2>(w, B_RC),
+        k_mx_residual<<<rgrid, kResThreads, kResSmem, s>>>(d, Z, A27, B27, RHS, buf<f2>(w, B_GC), buf<f2>(w, B_RC),
                                                            buf<cplx>(w, B_R64), buf<double>(w, B_PART),
                                                            buf<int>(w, B_ACTIVE));
         prof::end(s, prof::RESIDUAL);
@@ -1476,9 +1672,9 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
         // later residuals move by the last correction, in double-float
         prof::begin(s, prof::FF_RESIDUAL);
         prof::add_work(prof::FF_RESIDUAL, 216.0 * (double)d.N * k * nact);
-        k_mx_residual_inc<<<rgrid, kResThreads, kResSmem, s>>>(d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC),
-                                                               buf<cplx>(w, B_R64), buf<double>(w, B_PART),
-                                                               buf<int>(w, B_ACTIVE));
+        k_mx_residual_inc<false><<<rgrid, kResThreads, kResSmem, s>>>(
+            d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<cplx>(w, B_R64), buf<double>(w, B_PART),
+            buf<int>(w, B_ACTIVE), nullptr);
         prof::end(s, prof::FF_RESIDUAL);
       }
     }
@@ -1501,10 +1697,13 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
     if (steps >= ir_max) return "iterative refinement did not reach the tolerance";
     cudaMemcpyAsync(w.bufs[B_ACTIVE], active.data(), sizeof(int) * Ne, cudaMemcpyHostToDevice, s);
     // only the unconverged nodes are swept again
-    if (const char* m = solve_once(s, d, Z, A27, B27, w, nullptr, buf<f2>(w, B_RC), active, stats, status))
+    if (const char* m = solve_once(s, d, Z, A27, B27, w, nullptr, buf<f2>(w, B_RC), active, QuadOut{Qp, coef, 0},
+                                   stats, status))
       return m;
-    k_mx_accumulate<<<dim3(acc_blocks, Ne), 256, 0, s>>>(sG, 0, buf<f2>(w, B_GC), G, buf<int>(w, B_ACTIVE));
-    prof::count_launch();
+    if (G) {
+      k_mx_accumulate<<<dim3(acc_blocks, Ne), 256, 0, s>>>(sG, 0, buf<f2>(w, B_GC), G, buf<int>(w, B_ACTIVE));
+      prof::count_launch();
+    }
     ++steps;
   }
   if (stats) {

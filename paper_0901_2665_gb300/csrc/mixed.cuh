@@ -19,7 +19,7 @@ struct MixedSolveStats {
 // key is captured the second time it is seen (a capture and instantiation
 // cost more than one direct run, so one-off shapes stay direct).
 constexpr int kSweepGraphs = 8;
-constexpr int kSweepKey = 16;
+constexpr int kSweepKey = 20;
 struct SweepGraphCache {
   cudaGraphExec_t exec[kSweepGraphs] = {};
   unsigned long long key[kSweepGraphs][kSweepKey] = {};
@@ -50,8 +50,12 @@ struct MixedWork {
 // Both return nullptr on success, else a static error message.
 const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
                          MixedWork& w, int* status);
+// Solves (Z_e B - A) Q_e = RHS for every node e to the refinement tolerance.
+// G (nullable): receives Q_e (Ne x N x k complex128).  Qp (nullable):
+// receives the node shares Re{coef_e Q_e} of the quadrature sum (Eq. 15,
+// Ne x N x k real), accumulated in the backward-sweep epilogue.
 const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
-                        MixedWork& w, const double* RHS, cplx* G, int k, double ir_tol, int ir_max,
-                        MixedSolveStats* stats, int* status);
+                        MixedWork& w, const double* RHS, cplx* G, double* Qp, const cplx* coef, int k, double ir_tol,
+                        int ir_max, MixedSolveStats* stats, int* status);
 
 }  // namespace feast

@@ -155,17 +155,14 @@ __global__ void __launch_bounds__(256) k_couple_backward(Grid g, int layer, cons
   }
 }
 
-__global__ void k_quadrature_sum(long long N, int k, int Ne, const cplx* __restrict__ coef,
-                                 const cplx* __restrict__ G, long long sG, double* __restrict__ Q) {
-  const long long total = N * k;
+// Q[t] = sum_e Qp[e][t], nodes in order e = 1..Ne (a fixed summation order,
+// so the result does not depend on the launch schedule).
+__global__ void k_quadrature_node_sum(long long total, int Ne, const double* __restrict__ Qp, long long sQ,
+                                 double* __restrict__ Q) {
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     double acc = 0.0;
-    for (int e = 0; e < Ne; ++e) {
-      const cplx v = G[e * sG + t];
-      const cplx c = coef[e];
-      acc += c.re * v.re - c.im * v.im;
-    }
+    for (int e = 0; e < Ne; ++e) acc += Qp[e * sQ + t];
     Q[t] = acc;
   }
 }
@@ -225,11 +222,10 @@ void couple_backward(cudaStream_t s, Grid g, int layer, int Ne, const cplx* Z, c
   prof::count_launch();
 }
 
-void quadrature_sum(cudaStream_t s, long long N, int k, int Ne, const cplx* coef, const cplx* G,
-                    long long sG, double* Q) {
+void quadrature_sum(cudaStream_t s, long long N, int k, int Ne, const double* Qp, long long sQ, double* Q) {
   long long total = N * k;
   if (total == 0) return;
-  k_quadrature_sum<<<grid1d(total, 256), 256, 0, s>>>(N, k, Ne, coef, G, sG, Q);
+  k_quadrature_node_sum<<<grid1d(total, 256), 256, 0, s>>>(total, Ne, Qp, sQ, Q);
   prof::count_launch();
 }
 
