@@ -92,7 +92,17 @@ typedef struct {
                          target of loop 1 to 1e-5 and of loop 2 to 1e-8 (never below ir_tol); a
                          loop with a loosened target never ends the iteration.  0, or a given
                          start block: ir_tol in every loop. */
+  int inner_solver;   /* FEAST_INNER_DIRECT (default): the node systems are factorised once and
+                         solved by block elimination (precision selects FP64 or mixed).
+                         FEAST_INNER_COCG: no factorisation; every node system is solved by the
+                         Jacobi-preconditioned conjugate orthogonal CG method (FP64) to the
+                         relative residual inner_tol per column -- the inexact iterative inner
+                         solves of Sec. IV.C; precision and the ir_* options are then unused. */
+  double inner_tol;   /* COCG: relative residual ||r||_2 / ||b||_2 of each column (default 1e-3) */
+  int inner_max_iter; /* COCG: iteration cap (default 5000); reaching it fails the solve (FEAST_ERR_NO_CONVERGENCE) */
 } feast_options;
+
+enum { FEAST_INNER_DIRECT = 0, FEAST_INNER_COCG = 1 };
 
 /* Per-solve diagnostics, valid after feast_solve (also after a failing one). */
 #define FEAST_KERNEL_CLASSES 12
@@ -125,6 +135,8 @@ typedef struct {
                                a TF32 product counts once) */
   long long sweep_graphs;   /* MIXED: forward/backward sweep pairs replayed from captured CUDA graphs
                                (0 with options.profile, which times the kernels one by one) */
+  int inner_iters_max;      /* COCG: most iterations of one loop's node solves */
+  double inner_rel_max;     /* COCG: largest final relative residual of a column */
 } feast_info;
 
 /* Fills *opt with the defaults listed above. */

@@ -42,6 +42,8 @@ STATUS_NAMES = {v: k for k, v in globals().items() if k.startswith("FEAST_ERR_")
 
 FEAST_PREC_FP64 = 0
 FEAST_PREC_MIXED = 1
+FEAST_INNER_DIRECT = 0
+FEAST_INNER_COCG = 1
 
 EXPORTED = [
     "feast_default_options", "feast_init", "feast_destroy", "feast_last_error", "feast_get_info",
@@ -60,7 +62,8 @@ class feast_operator(ctypes.Structure):
 class feast_options(ctypes.Structure):
     _fields_ = [("max_loops", ctypes.c_int), ("precision", ctypes.c_int), ("ir_tol", ctypes.c_double),
                 ("ir_max", ctypes.c_int), ("seed", ctypes.c_uint64), ("profile", ctypes.c_int),
-                ("ir_early", ctypes.c_int)]
+                ("ir_early", ctypes.c_int), ("inner_solver", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("inner_max_iter", ctypes.c_int)]
 
 
 KERNEL_CLASS_SLOTS = 12   # FEAST_KERNEL_CLASSES
@@ -77,7 +80,8 @@ class feast_info(ctypes.Structure):
                 ("kernel_ms", ctypes.c_double * KERNEL_CLASS_SLOTS),
                 ("kernel_launches", ctypes.c_longlong * KERNEL_CLASS_SLOTS),
                 ("kernel_flops", ctypes.c_double * KERNEL_CLASS_SLOTS),
-                ("sweep_graphs", ctypes.c_longlong)]
+                ("sweep_graphs", ctypes.c_longlong), ("inner_iters_max", ctypes.c_int),
+                ("inner_rel_max", ctypes.c_double)]
 
 
 KERNEL_CLASSES = ["sweep_gemm", "solve_gemm", "panel_inverse", "panel_product", "schur", "solve_coupling",
@@ -181,11 +185,13 @@ class Handle:
     """Owns one feast_handle (feast_init / feast_destroy)."""
 
     def __init__(self, precision: int = FEAST_PREC_FP64, max_loops: int = 20, ir_tol: float = 1e-12,
-                 ir_max: int = 30, seed: int = 1000, stream=None, profile: bool = False, ir_early: bool = True):
+                 ir_max: int = 30, seed: int = 1000, stream=None, profile: bool = False, ir_early: bool = True,
+                 inner_solver: int = FEAST_INNER_DIRECT, inner_tol: float = 1e-3, inner_max_iter: int = 5000):
         opt = default_options()
         opt.precision, opt.max_loops, opt.ir_tol, opt.ir_max, opt.seed = precision, max_loops, ir_tol, ir_max, seed
         opt.profile = 1 if profile else 0
         opt.ir_early = 1 if ir_early else 0
+        opt.inner_solver, opt.inner_tol, opt.inner_max_iter = inner_solver, inner_tol, inner_max_iter
         self._h = _vp()
         st = _lib.feast_init(ctypes.byref(self._h), ctypes.byref(opt), stream if stream is not None else _current_stream())
         if st != FEAST_OK:

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/feast.h"
+#include "iterative.cuh"
 #include "kernels.cuh"
 #include "mixed.cuh"
 #include "prof.cuh"
@@ -152,7 +153,7 @@ struct feast_handle {
   // operator copies (when the caller passes host arrays)
   DevBuf opA, opB;
   // factor and node buffers
-  DevBuf F, T1, T, L, Pinv, G, Tmp, Zd, coefd, status;
+  DevBuf F, T1, T, L, Pinv, G, Tmp, Zd, coefd, status, cgw;
   // loop buffers
   DevBuf RHS, Q, Qp, AQf, BQf, Xb, Yb, Xout, part, AQ, BQ, eps, Phi, work, norms, normA, lam_d, perm_d, resid_d,
       residp_d;
@@ -160,7 +161,8 @@ struct feast_handle {
   cudaEvent_t ev[8] = {};
 
   void release_all() {
-    for (DevBuf* b : {&opA, &opB, &F, &T1, &T, &L, &Pinv, &G, &Tmp, &Zd, &coefd, &status, &RHS, &Q, &Qp, &AQf, &BQf,
+    for (DevBuf* b : {&opA, &opB, &F, &T1, &T, &L, &Pinv, &G, &Tmp, &Zd, &coefd, &status, &cgw, &RHS, &Q, &Qp, &AQf,
+                      &BQf,
                       &Xb, &Yb, &Xout, &part, &AQ, &BQ, &eps, &Phi, &work, &norms, &normA, &lam_d, &perm_d,
                       &resid_d, &residp_d})
       b->release();
@@ -242,6 +244,7 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 void factor_nodes(feast_handle* h, const OpView& op, int Ne, int precision) {
   const int n = op.g.n(), nb = op.g.nz;
   const long long nn = (long long)n * n;
+  if (h->opt.inner_solver == FEAST_INNER_COCG) return;   // iterative inner solves: nothing to factor
   if (precision == FEAST_PREC_FP64) {
     h->F.ensure(sizeof(cplx) * (size_t)Ne * nb * nn, "factors");
     h->T1.ensure(sizeof(cplx) * (size_t)Ne * nn, "schur scratch");
@@ -265,6 +268,23 @@ void factor_nodes(feast_handle* h, const OpView& op, int Ne, int precision) {
 void solve_nodes(feast_handle* h, const OpView& op, int Ne, int precision, const double* RHS, cplx* G, double* Qp,
                  int k, double ir_tol) {
   const int n = op.g.n();
+  if (h->opt.inner_solver == FEAST_INNER_COCG) {
+    // iterative inner solves (Sec. IV.C); the node shares are formed from
+    // the solutions by quadrature_from_solutions instead
+    if (!G) fail(FEAST_ERR_ARG, "iterative inner solves need the solution buffer");
+    h->cgw.ensure(cocg_work_bytes(op.g, Ne, k), "iterative solver work space");
+    CocgStats st;
+    const char* msg = cocg_solve(h->stream, op.g, Ne, h->Zd.as<cplx>(), op.A27, op.B27, RHS, G, k, h->opt.inner_tol,
+                                 h->opt.inner_max_iter, h->cgw.p, h->status.as<int>(), &st);
+    h->info.inner_iters_max = std::max(h->info.inner_iters_max, st.iterations);
+    h->info.inner_rel_max = std::max(h->info.inner_rel_max, st.rel_max);
+    if (msg) {
+      int dst = 0;
+      cudaMemcpy(&dst, h->status.p, sizeof(int), cudaMemcpyDeviceToHost);
+      fail(dst == DEV_PIVOT ? FEAST_ERR_PIVOT : FEAST_ERR_NO_CONVERGENCE, msg);
+    }
+    return;
+  }
   if (precision == FEAST_PREC_FP64) {
     h->Tmp.ensure(sizeof(cplx) * (size_t)Ne * n * k, "solve scratch");
     if (!G) {   // the FP64 sweeps keep their layer solutions in G
@@ -282,6 +302,22 @@ void solve_nodes(feast_handle* h, const OpView& op, int Ne, int precision, const
     if (ir_tol <= h->opt.ir_tol) h->info.ir_resid_max = std::max(h->info.ir_resid_max, st.resid_max);
     h->info.sweep_graphs += st.graph_sweeps;
   }
+}
+
+// Fig. 2 step 2 in full: the Ne node solves of RHS and the quadrature sum
+// Q (Eq. 15), N x k.
+void node_solves_and_quadrature(feast_handle* h, const OpView& op, int Ne, int precision, const double* RHS, int k,
+                                double ir_tol, double* Q) {
+  const long long N = op.g.N();
+  if (h->opt.inner_solver == FEAST_INNER_COCG) {
+    h->G.ensure(sizeof(cplx) * (size_t)Ne * N * k, "node solutions");
+    solve_nodes(h, op, Ne, precision, RHS, h->G.as<cplx>(), nullptr, k, ir_tol);
+    quadrature_from_solutions(h->stream, N, k, Ne, h->coefd.as<cplx>(), h->G.as<cplx>(), Q);
+    return;
+  }
+  h->Qp.ensure(sizeof(double) * (size_t)Ne * N * k, "quadrature shares");
+  solve_nodes(h, op, Ne, precision, RHS, nullptr, h->Qp.as<double>(), k, ir_tol);
+  quadrature_sum(h->stream, N, k, Ne, h->Qp.as<double>(), N * k, Q);
 }
 
 void upload_contour(feast_handle* h, const Contour& ct) {
@@ -340,6 +376,9 @@ void feast_default_options(feast_options* opt) {
   opt->ir_early = 1;
   opt->seed = 1000;
   opt->profile = 0;
+  opt->inner_solver = FEAST_INNER_DIRECT;
+  opt->inner_tol = 1e-3;
+  opt->inner_max_iter = 5000;
 }
 
 feast_status feast_init(feast_handle** out, const feast_options* opt, void* cuda_stream) {
@@ -353,6 +392,10 @@ feast_status feast_init(feast_handle** out, const feast_options* opt, void* cuda
     if (h->opt.max_loops < 1 || h->opt.max_loops > 1000) fail(FEAST_ERR_ARG, "max_loops out of range");
     if (h->opt.precision != FEAST_PREC_FP64 && h->opt.precision != FEAST_PREC_MIXED)
       fail(FEAST_ERR_ARG, "unknown precision");
+    if (h->opt.inner_solver != FEAST_INNER_DIRECT && h->opt.inner_solver != FEAST_INNER_COCG)
+      fail(FEAST_ERR_ARG, "unknown inner solver");
+    if (h->opt.inner_solver == FEAST_INNER_COCG && (!(h->opt.inner_tol > 0.0) || h->opt.inner_max_iter < 1))
+      fail(FEAST_ERR_ARG, "inner_tol must be > 0 and inner_max_iter >= 1");
     ck(cudaGetDevice(&h->device), "cudaGetDevice");
     if (h->opt.profile) prof::set_enabled(true);
     for (auto& e : h->ev) ck(cudaEventCreate(&e), "event");
@@ -423,6 +466,8 @@ feast_status feast_node_solve(feast_handle* h, const feast_operator* op, double 
     ck(cudaMemcpyAsync(h->Zd.p, &z, sizeof(cplx), cudaMemcpyHostToDevice, h->stream), "Z");
     h->info.ir_steps_max = 0;
     h->info.ir_resid_max = 0.0;
+    h->info.inner_iters_max = 0;
+    h->info.inner_rel_max = 0.0;
     factor_nodes(h, v, 1, precision);
     check_status(h);
     solve_nodes(h, v, 1, precision, RHS, reinterpret_cast<cplx*>(Qe), nullptr, k, h->opt.ir_tol);
@@ -444,9 +489,7 @@ feast_status feast_quadrature(feast_handle* h, const feast_operator* op, double 
     h->info.ir_resid_max = 0.0;
     factor_nodes(h, v, Ne, precision);
     check_status(h);
-    h->Qp.ensure(sizeof(double) * (size_t)Ne * N * k, "quadrature shares");
-    solve_nodes(h, v, Ne, precision, RHS, nullptr, h->Qp.as<double>(), k, h->opt.ir_tol);
-    quadrature_sum(h->stream, N, k, Ne, h->Qp.as<double>(), N * k, Q);
+    node_solves_and_quadrature(h, v, Ne, precision, RHS, k, h->opt.ir_tol, Q);
     check_status(h);
   });
 }
@@ -522,7 +565,8 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
     ck(cudaEventRecord(h->ev[1], s), "event");
     check_status(h);
     h->info.t_factor_ms = elapsed(h->ev[0], h->ev[1]);
-    h->info.factor_flops = (long long)8 * n * (long long)n * n * v.g.nz * Ne;
+    h->info.factor_flops =
+        h->opt.inner_solver == FEAST_INNER_COCG ? 0 : (long long)8 * n * (long long)n * n * v.g.nz * Ne;
 
     // ---- buffers of the loop
     const size_t blk = sizeof(double) * (size_t)N * M0;
@@ -531,7 +575,6 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
     h->Xb.ensure(blk, "X");
     h->Yb.ensure(blk, "Y");
     h->Xout.ensure(blk, "X out");
-    h->Qp.ensure(sizeof(double) * (size_t)Ne * N * M0, "quadrature shares");
     h->eps.ensure(sizeof(double) * M0, "eps");
     h->lam_d.ensure(sizeof(double) * M0, "lambda");
     h->perm_d.ensure(sizeof(int) * M0, "perm");
@@ -562,8 +605,7 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
       if (h->opt.ir_early && !Y0 && prec == FEAST_PREC_MIXED && loop <= 2)
         ir_loop = std::max(ir_loop, loop == 1 ? 1e-5 : 1e-8);
       const bool exact_loop = ir_loop <= h->opt.ir_tol;
-      solve_nodes(h, v, Ne, prec, h->RHS.as<double>(), nullptr, h->Qp.as<double>(), M0, ir_loop);
-      quadrature_sum(s, N, M0, Ne, h->Qp.as<double>(), N * M0, h->Q.as<double>());
+      node_solves_and_quadrature(h, v, Ne, prec, h->RHS.as<double>(), M0, ir_loop, h->Q.as<double>());
       ck(cudaEventRecord(h->ev[3], s), "event");
       // steps 3-5: Rayleigh-Ritz
       rayleigh_ritz_dev(h, v, h->Q.as<double>(), M0, h->eps.as<double>(), h->Xb.as<double>(), nullptr, nullptr);

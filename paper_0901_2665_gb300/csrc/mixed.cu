@@ -153,120 +153,24 @@ __device__ __forceinline__ f2 f2inv_fast(f2 a) {
 // with the identity when bw < 64), one pivot at a time:
 //   p = P[k,k];  P[i,j] -= P[i,k] P[k,j] / p  (i, j != k);
 //   P[k,j] /= p;  P[i,k] /= p;  P[k,k] = -1/p,
-// after which P = -S[K,K]^{-1}.  Thread t holds column j = t % 64 of rows
-// t / 64 + 8a (a < 8) in registers.  After each pivot the holders of the next
+// after which P = -S[K,K]^{-1}.  After each pivot the holders of the next
 // pivot's row and column publish them to shared memory (double-buffered by
-// pivot parity), and the holder of the next pivot publishes its reciprocal,
-// so that one block barrier per pivot suffices and the reciprocal is formed
-// once.  Every thread applies the rank-1 update to its eight entries, the
-// pivot column through the same FMAs (its entries are cleared when published
-// and the multiplier there is -1/p); the pivot row (two warps) is then
-// overwritten.  The 64 pivots are the kernel's critical path.
-constexpr int kPinvThreads = 512;
-constexpr int kPinvGroups = kPinvThreads / kPanel;   // row groups
-constexpr int kPinvRows = kPanel / kPinvGroups;      // rows per thread
-
-__global__ void __launch_bounds__(kPinvThreads) k_mx_pinv(Dims d, int layer, int k0, int bw,
-                                                          const float* __restrict__ F, f2* __restrict__ PinvOut,
-                                                          int* status) {
-  __shared__ f2 rowb[2][kPanel];   // row k of P before pivot k
-  __shared__ f2 colb[2][kPanel];   // column k of P before pivot k
-  __shared__ f2 invb[2];           // 1 / P[k, k] before pivot k
-  __shared__ int bad;
-  const int e = blockIdx.x;
-  const int tid = threadIdx.x;
-  const int j = tid % kPanel, g = tid / kPanel;   // column, row group (rows g + 8a)
-  const int n = d.n;
-  const float* Fl = F + ((long long)e * 2 + (layer & 1)) * n * d.ldF;
-  if (tid == 0) bad = 0;
-  f2 v[kPinvRows];
-#pragma unroll
-  for (int a = 0; a < kPinvRows; ++a) {
-    const int i = g + kPinvGroups * a;
-    f2 x{(i == j) ? 1.f : 0.f, 0.f};
-    if (i < bw && j < bw) {
-      const float* row = Fl + (long long)(k0 + i) * d.ldF;
-      x = f2{row[k0 + j], row[n + k0 + j]};
-    }
-    v[a] = x;
-  }
-  __syncthreads();   // `bad` initialised
-  // publish pivot kn from this thread's entries (row kn: threads of row group
-  // kn % 8; column kn: threads j == kn; the pivot's holder: its reciprocal)
-  auto publish = [&](int kn, int buf) {
-    const int an = kn / kPinvGroups;
-    if (g == kn % kPinvGroups) {
-      f2 x = v[0];
-#pragma unroll
-      for (int a = 1; a < kPinvRows; ++a)
-        if (a == an) x = v[a];
-      rowb[buf][j] = x;
-      if (j == kn) {
-        const float mag = fabsf(x.x) + fabsf(x.y);
-        const bool good = mag > 0.f && isfinite(mag);
-        if (!good) bad = 1;
-        invb[buf] = good ? f2inv_fast(x) : f2{0.f, 0.f};
-      }
-    }
-    // the column's holders publish it and clear their entries: the next
-    // pivot's update then leaves P[i, kn] / p there (see below)
-    if (j == kn)
-#pragma unroll
-      for (int a = 0; a < kPinvRows; ++a) {
-        colb[buf][g + kPinvGroups * a] = v[a];
-        v[a] = f2{0.f, 0.f};
-      }
-  };
-  publish(0, 0);
-  __syncthreads();
-#pragma unroll 1
-  for (int k = 0; k < kPanel; ++k) {
-    const int b = k & 1;
-    const f2 inv = invb[b];
-    const f2 rki = f2mul(rowb[b][j], inv);   // P[k, j] / p
-    // rank-1 update of every entry: P[i, j] -= P[i, k] P[k, j] / p.  On the
-    // pivot column (entries cleared at publication) the multiplier -1/p makes
-    // the same two FMAs leave P[i, k] / p, without a divergent branch.
-    const f2 r = (j == k) ? f2{-inv.x, -inv.y} : rki;
-#pragma unroll
-    for (int a = 0; a < kPinvRows; ++a) {
-      const f2 c = colb[b][g + kPinvGroups * a];
-      v[a].x = fmaf(-c.x, r.x, v[a].x);
-      v[a].x = fmaf(c.y, r.y, v[a].x);
-      v[a].y = fmaf(-c.x, r.y, v[a].y);
-      v[a].y = fmaf(-c.y, r.x, v[a].y);
-    }
-    // pivot row: P[k, j] = P[k, j] / p, and P[k, k] = -1 / p
-    if (g == k % kPinvGroups) {
-      const f2 x = (j == k) ? f2{-inv.x, -inv.y} : rki;
-#pragma unroll
-      for (int a = 0; a < kPinvRows; ++a)
-        if (a == k / kPinvGroups) v[a] = x;
-    }
-    if (k + 1 < kPanel) publish(k + 1, b ^ 1);
-    __syncthreads();
-  }
-  // P holds -S[K,K]^{-1}
-#pragma unroll
-  for (int a = 0; a < kPinvRows; ++a) {
-    const int i = g + kPinvGroups * a;
-    PinvOut[(long long)e * kPanel * kPanel + i * kPanel + j] = f2{-v[a].x, -v[a].y};
-  }
-  if (tid == 0 && bad) atomicExch(status, (int)DEV_PIVOT);
-}
-
-// The same Gauss-Jordan sweep with fewer, fuller threads: thread t holds
-// column j = t % 64 of the RPT consecutive rows h RPT + a (a < RPT),
-// h = t / 64, so a CTA has 64 * (64 / RPT) threads.  Per pivot a thread reads
-// the pivot's reciprocal, its own entry of the pivot row and the RPT entries
-// of the pivot column that its rows need (a warp-wide broadcast, two complex
-// values per 16-byte load), and applies RPT complex FMAs; the per-pivot
-// overhead (barrier, reciprocal, selects) is shared by 2 RPT FMAs instead of
-// 8.  The pivot loop is unrolled within a row block so that every register
-// index is a compile-time constant.  Arithmetic and publication order are
-// those of k_mx_pinv.
+// pivot parity) and the holder of the next pivot publishes its reciprocal, so
+// one block barrier per pivot suffices and the reciprocal is formed once.
+// Every thread applies the rank-1 update to its entries, the pivot column
+// through the same FMAs (its entries are cleared when published and the
+// multiplier there is -1/p); the pivot row is then overwritten.  The 64 pivots
+// are the kernel's critical path.
+// Layout: thread t holds column j = t % 64 of the RPT consecutive rows
+// h RPT + a (a < RPT), h = t / 64, so a CTA has 64 * (64 / RPT) threads.  Per
+// pivot a thread reads the pivot's reciprocal, its own entry of the pivot row
+// and the RPT entries of the pivot column that its rows need (a warp-wide
+// broadcast, two complex values per 16-byte load), and applies RPT complex
+// FMAs.  The pivot loop is unrolled within a row block so that every register
+// index is a compile-time constant.  RPT = 16 (256 threads) measured fastest:
+// 32 rows per thread leaves one warp per scheduler to hide every latency.
 template <int RPT>
-__global__ void __launch_bounds__(kPanel * (kPanel / RPT)) k_mx_pinv_cols(Dims d, int layer, int k0, int bw,
+__global__ void __launch_bounds__(kPanel * (kPanel / RPT)) k_mx_pinv(Dims d, int layer, int k0, int bw,
                                                                          const float* __restrict__ F,
                                                                          f2* __restrict__ PinvOut, int* status) {
   constexpr int H = kPanel / RPT;   // row blocks
@@ -295,7 +199,7 @@ __global__ void __launch_bounds__(kPanel * (kPanel / RPT)) k_mx_pinv_cols(Dims d
   __syncthreads();   // `bad` initialised
   // publish pivot kn = hb RPT + idx (idx a compile-time constant after
   // unrolling): its row from the row block hb, its reciprocal from its
-  // holder, its column (cleared afterwards, see k_mx_pinv) from column kn
+  // holder, its column (cleared afterwards, as described above) from column kn
   auto publish = [&](int hb, int idx, int kn, int buf) {
     if (h == hb) {
       const f2 x = v[idx];
@@ -357,8 +261,14 @@ __global__ void __launch_bounds__(kPanel * (kPanel / RPT)) k_mx_pinv_cols(Dims d
   if (tid == 0 && bad) atomicExch(status, (int)DEV_PIVOT);
 }
 
+#ifndef FEAST_WIDE_STAGES
+#define FEAST_WIDE_STAGES 1
+#endif
+// pipeline stages of the wide sweep update (1: two CTAs per SM)
+constexpr int kWideStages = FEAST_WIDE_STAGES;
+
 #ifndef FEAST_PINV_RPT
-#define FEAST_PINV_RPT 32
+#define FEAST_PINV_RPT 16
 #endif
 constexpr int kPinvRpt = FEAST_PINV_RPT;   // rows per thread of the panel inverse
 
@@ -690,6 +600,13 @@ struct SolveEpi {
     if (qp) ce = coef[e];
 #pragma unroll 1
     for (int c0 = 0; c0 < CB; c0 += 16) {
+      // the old shares first, as 16 independent loads (a refinement step)
+      double qold[16];
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        const int m = tn * CB + c0 + t;
+        qold[t] = (qp && !qfirst && p < n && c0 + t < CB && m < k) ? qp[e * sQ + (long long)m * ldq + p] : 0.0;
+      }
       float re[16], im[16];
       tc::tmem_ld16(taddr + c0, re);
       tc::tmem_ld16(taddr + CB + c0, im);
@@ -700,11 +617,8 @@ struct SolveEpi {
         if (c0 + t < CB && m < k) {
           const f2 x{alpha * re[t], alpha * im[t]};
           o[(long long)m * ldo + p] = x;
-          if (qp) {
-            double* q = qp + e * sQ + (long long)m * ldq + p;
-            const double v = ce.re * (double)x.x - ce.im * (double)x.y;
-            *q = qfirst ? v : *q + v;
-          }
+          if (qp)
+            qp[e * sQ + (long long)m * ldq + p] = qold[t] + (ce.re * (double)x.x - ce.im * (double)x.y);
         }
       }
     }
@@ -812,6 +726,21 @@ __global__ void k_mx_accumulate(long long total, int first, const f2* __restrict
   }
 }
 
+// fp32 -> fp64 through the bit fields (IEEE 754 binary32 -> binary64:
+// exponent rebiased by 1023 - 127, mantissa shifted by 29), on the integer
+// pipe: the FP64 refinement residual converts 54 values per complex entry,
+// and a float-to-double conversion instruction would take an FP64-pipe slot
+// each.  Exact for zero and normal numbers; an fp32 subnormal (|x| < 2^-126)
+// becomes a signed zero, infinities and NaNs stay infinities and NaNs.
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned ex = (u >> 23) & 0xFFu;
+  const unsigned e64 = ex == 0xFFu ? 0x7FFu : ex + (1023u - 127u);
+  const unsigned hi = (u & 0x80000000u) | (ex ? (e64 << 20) | ((u >> 3) & 0xFFFFFu) : 0u);
+  const unsigned lo = ex ? (u << 29) : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 constexpr int kResRows = 128;      // grid rows per block
 // Refinement targets at or above this take their first residual in
 // double-float as well (its error, ~1e-12 of ||RHS||, is far below them).
@@ -877,7 +806,7 @@ __global__ void __launch_bounds__(kResThreads) k_mx_residual(Dims d, const cplx*
       for (int s = 0; s < 27; ++s) {
         const cplx c = rsm[s * kResRows + r];
         const f2 v32 = q[off[s]];
-        const cplx v{(double)v32.x, (double)v32.y};
+        const cplx v{f32_to_f64(v32.x), f32_to_f64(v32.y)};
         are = fma(-c.re, v.re, are);
         are = fma(c.im, v.im, are);
         aim = fma(-c.re, v.im, aim);
@@ -1243,7 +1172,7 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
       const int k0 = kp * kPanel, bw = std::min(kPanel, d.n - k0), q = kp & 1;
       prof::begin(st, prof::PINV);
       prof::add_work(prof::PINV, 8.0 * kPanel * kPanel * kPanel * Ne);
-      k_mx_pinv_cols<kPinvRpt><<<Ne, kPanel * (kPanel / kPinvRpt), 0, st>>>(d, layer, k0, bw, F, Pv[q], status);
+      k_mx_pinv<kPinvRpt><<<Ne, kPanel * (kPanel / kPinvRpt), 0, st>>>(d, layer, k0, bw, F, Pv[q], status);
       prof::end(st, prof::PINV);
       prof::begin(st, prof::PANEL_T);
       prof::add_work(prof::PANEL_T, 8.0 * d.n * kPanel * kPanel * Ne);
@@ -1277,7 +1206,8 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
         // the narrow update (one column tile, few CTAs, on the critical path)
         // pipelines its K-blocks; the wide one keeps two CTAs per SM instead
         err = count == 1 ? launch_tc<128, 4>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status)
-                         : launch_tc<128, 1>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status);
+                         : launch_tc<128, kWideStages>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi,
+                                                       status);
       } else {
         SweepEpi epi{F + (long long)(layer & 1) * d.n * d.ldF, sF, last ? Fr + (long long)layer * d.n * d.ldF : nullptr,
                      sFr, d.ldF, d.n, k0, bw, Tc[q], Pv[q]};
@@ -1339,7 +1269,7 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
     } else {
       if (w.factor_graph) cudaGraphExecDestroy(w.factor_graph);
       w.factor_graph = nullptr;
-      if (tc_attr<128, 1, SweepEpiTma>() || tc_attr<128, 4, SweepEpiTma>() || tc_attr<128, 2, SweepEpi>())
+      if (tc_attr<128, kWideStages, SweepEpiTma>() || tc_attr<128, 4, SweepEpiTma>() || tc_attr<128, 2, SweepEpi>())
         return "tcgen05 sweep-update attribute rejected";
       cudaGraph_t graph = nullptr;
       cudaGraphExec_t exec = nullptr;

@@ -164,3 +164,96 @@ def test_inexact_inner_solves_still_converge(intervals):
     assert np.abs(lamd.cpu().numpy()[:M] - lam[:M]).max() <= 1e-5 * lam[M - 1]
     assert resid.cpu().numpy()[:M].max() <= 1e-3
 
+
+
+# ---------------------------------------------------------------- iterative inner solves (Sec. IV.C)
+
+def _cocg_handle(tol, **kw):
+    return F().Handle(inner_solver=F().FEAST_INNER_COCG, inner_tol=tol, **kw)
+
+
+@pytest.mark.parametrize("tol", [1e-3, 1e-10])
+def test_cocg_node_solve_meets_its_tolerance(tol):
+    """The iterative inner solver (Jacobi-preconditioned COCG) on a ragged
+    grid, at the node nearest the middle of the contour and the one closest to
+    the real axis: every column's residual ||(Z B - A) q - b||_2 / ||b||_2,
+    recomputed by the oracle's sparse product, meets the tolerance, and q is
+    within (tolerance x condition) of the oracle's direct block solve."""
+    nx, ny, nz = 12, 11, 9
+    op = workloads.q1_operator(nx, ny, nz, workloads.gaussian_potential(5, 4, nx, ny, nz))
+    lam = oracle.closed_form_eigenvalues_v0(nx, ny, nz)
+    lmin, lmax = lam[0] - 3.0, lam[12]
+    _, _, _, Z, _ = oracle.contour_points(lmin, lmax, 8)
+    k = 24
+    RHS = np.random.default_rng(11).standard_normal((op.N, k))
+    A = oracle.assemble(op.A27, nx, ny, nz)
+    B = oracle.assemble(op.B27, nx, ny, nz)
+    dop, keep = dev_op(op)
+    h = _cocg_handle(tol)
+    for z in (Z[0], Z[7]):
+        Qe = torch.zeros((k, op.N), dtype=torch.complex128, device="cuda")
+        info = h.feast_node_solve(dop, complex(z), cm(RHS), Qe, k)
+        assert info.inner_iters_max > 0 and info.inner_rel_max <= tol
+        q = back(Qe)
+        M = (z * B - A).astype(np.complex128)
+        rel = np.linalg.norm(M @ q - RHS, axis=0) / np.linalg.norm(RHS, axis=0)
+        assert rel.max() <= 1.5 * tol, (z, rel.max())
+        ref = oracle.block_tridiag_factor(M, op.n, nz).solve(RHS.astype(np.complex128))
+        assert np.abs(q - ref).max() <= max(3e4 * tol, 1e-12) * np.abs(ref).max()
+
+
+def test_iterative_inner_solves_example_iii(intervals):
+    """Sec. IV.C settings: inner systems solved iteratively to a relative
+    residual of 1e-3, trace tolerance 1e-8.  FEAST still finds every pair of
+    the interval, the eigenvalues to well below the inner tolerance (1e-5
+    relative against the dense pencil) and residuals in the paper's range
+    (<= 1e-3)."""
+    wl = workloads.WORKLOADS["q1_10x10x20_fp64"]
+    op = wl.operator(0)
+    iv = intervals["q1_10x10x20/seed0"]
+    lam = np.sort(oracle.dense_generalized_eigh(op)[0])
+    M = iv["M"]
+    dop, keep = dev_op(op)
+    lamd = torch.zeros(wl.M0, dtype=torch.float64, device="cuda")
+    X = torch.zeros((wl.M0, op.N), dtype=torch.float64, device="cuda")
+    resid = torch.zeros(wl.M0, dtype=torch.float64, device="cuda")
+    h = _cocg_handle(1e-3)
+    r = h.feast_solve(dop, iv["lmin"], iv["lmax"], wl.M0, wl.Ne, 1e-8, None, lamd, X, resid, allow=())
+    assert r.m_found == M and r.info.factor_flops == 0
+    assert 0 < r.info.inner_iters_max < 5000 and r.info.inner_rel_max <= 1e-3
+    assert np.abs(lamd.cpu().numpy()[:M] - lam[:M]).max() <= 1e-5 * lam[M - 1]
+    assert resid.cpu().numpy()[:M].max() <= 1e-3
+    # the residuals the solve reports are the oracle's, pair by pair
+    r1, _ = oracle.residuals(oracle.assemble(op.A27, 10, 10, 20), oracle.assemble(op.B27, 10, 10, 20),
+                             lamd.cpu().numpy()[:M], back(X)[:, :M])
+    assert np.abs(resid.cpu().numpy()[:M] - r1).max() <= 1e-12 * r1.max()
+
+
+def test_iterative_inner_solves_warm_sequence():
+    """Fig. 3 in miniature: a potential changed in small steps, inner systems
+    solved iteratively to 1e-3, trace tolerance 1e-8, each problem started
+    from the previous subspace.  Every problem yields the dense pencil's
+    eigenvalues to 1e-5, and the warm starts need no more loops than the
+    random start of the first problem."""
+    nx, ny, nz, M, M0 = 8, 8, 12, 8, 14
+    base = workloads.gaussian_potential(6, 21, nx, ny, nz)
+    h = _cocg_handle(1e-3)
+    Xprev, loops = None, []
+    for t in range(4):
+        pot = dataclasses.replace(base, amps=base.amps * (1.0 + 0.01 * t))
+        op = workloads.q1_operator(nx, ny, nz, pot)
+        lam = oracle.dense_generalized_eigh(op)[0]
+        if t == 0:
+            lmin, lmax = lam[0] - 0.5 * (lam[M] - lam[M - 1]), 0.5 * (lam[M - 1] + lam[M])
+        m_in = int(((lam >= lmin) & (lam <= lmax)).sum())
+        dop, keep = dev_op(op)
+        lamd = torch.zeros(M0, dtype=torch.float64, device="cuda")
+        X = torch.zeros((M0, op.N), dtype=torch.float64, device="cuda")
+        r = h.feast_solve(dop, lmin, lmax, M0, 8, 1e-8, Xprev, lamd, X, allow=())
+        assert r.m_found == m_in, t
+        got = lamd.cpu().numpy()[:m_in]
+        ref = lam[(lam >= lmin) & (lam <= lmax)]
+        assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), t
+        loops.append(r.loops)
+        Xprev = X.clone()
+    assert max(loops[1:]) <= loops[0], loops
