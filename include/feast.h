@@ -185,6 +185,28 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
                          double* lambda, double* X, double* resid, int* m_found, int* loops);
 
 /*
+ * The eigensolver for a complex Hermitian A (Sec. III.A: A real symmetric or
+ * Hermitian; Sec. III.B, Eqs. 10 and 12), FP64.  op->A27 and op->B27 hold
+ * complex coefficients ([27][N] complex, interleaved (re, im) doubles, the
+ * same slot layout as feast_operator); A must be Hermitian and B Hermitian
+ * positive definite (a real B is passed with zero imaginary parts).  Step 2
+ * solves at the 2 Ne shifts Z_e and conj Z_e (G(conj Z) = G(Z)^dagger) and
+ * accumulates Eq. 12:
+ *   Q = -sum_e (w_e r / 4) (e^{i theta_e} G(Z_e) + e^{-i theta_e} G(conj Z_e)) B Y;
+ * Rayleigh-Ritz uses A_Q = Q^H A Q, B_Q = Q^H B Q and a Hermitian-definite
+ * reduced eigensolve, X = Q Phi with X^H B X = I.
+ *   Y0, X   : N x M0 complex (interleaved), DEVICE; Y0 may be NULL for the
+ *             seeded block Y(row, col) = u(seed, col N + row) + i u(seed + 1, col N + row)
+ *             (u as for feast_solve).
+ *   lambda, resid, m_found, loops: as in feast_solve (host or device).
+ * Requirements: 1 <= M0 <= min(N, 64); 1 <= Ne <= 32; nx*ny <= 4096; the
+ * operator arrays on the device.  Returns as feast_solve does; synchronises.
+ */
+feast_status feast_solve_hermitian(feast_handle* h, const feast_operator* op, double lmin, double lmax, int M0,
+                                   int Ne, double tol, const double* Y0, double* lambda, double* X, double* resid,
+                                   int* m_found, int* loops);
+
+/*
  * Many independent problems (Sec. V, parallelism level (i): independent
  * search intervals or instances) solved concurrently on the handle's GPU.
  * Instance i has operator ops[i], interval [lmin[i], lmax[i]] and subspace

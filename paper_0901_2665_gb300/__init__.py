@@ -47,7 +47,7 @@ FEAST_INNER_COCG = 1
 
 EXPORTED = [
     "feast_default_options", "feast_init", "feast_destroy", "feast_last_error", "feast_get_info",
-    "feast_solve", "feast_contour", "feast_stencil_apply", "feast_node_solve", "feast_quadrature",
+    "feast_solve", "feast_solve_hermitian", "feast_contour", "feast_stencil_apply", "feast_node_solve", "feast_quadrature",
     "feast_reduced_eig", "feast_rayleigh_ritz", "feast_residuals", "feast_reduced_eig_noalloc",
     "feast_solve_batched", "feast_mlp_create", "feast_mlp_destroy", "feast_mlp_set_layer", "feast_mlp_get_layer",
     "feast_mlp_forward", "feast_mlp_train_step", "feast_sine_expand", "feast_sine_project", "feast_predict_Y",
@@ -98,6 +98,8 @@ _lib.feast_last_error.restype = ctypes.c_char_p
 _lib.feast_get_info.argtypes = [_vp, ctypes.POINTER(feast_info)]
 _lib.feast_solve.argtypes = [_vp, ctypes.POINTER(feast_operator), _d, _d, _i, _i, _d, _vp, _vp, _vp, _vp,
                              ctypes.POINTER(_i), ctypes.POINTER(_i)]
+_lib.feast_solve_hermitian.argtypes = [_vp, ctypes.POINTER(feast_operator), _d, _d, _i, _i, _d, _vp, _vp, _vp, _vp,
+                                       ctypes.POINTER(_i), ctypes.POINTER(_i)]
 _lib.feast_contour.argtypes = [_d, _d, _i, _vp, _vp, _vp, _vp, _vp]
 _lib.feast_stencil_apply.argtypes = [_vp, _i, _i, _i, _vp, _vp, _vp, _i]
 _lib.feast_node_solve.argtypes = [_vp, ctypes.POINTER(feast_operator), _d, _d, _vp, _vp, _i, _i]
@@ -227,6 +229,17 @@ class Handle:
         st = _lib.feast_solve(self._h, ctypes.byref(op), float(lmin), float(lmax), int(M0), int(Ne), float(tol),
                               _ptr(Y0), _ptr(lam), _ptr(X), _ptr(resid), ctypes.byref(m), ctypes.byref(loops))
         self._check(st, "feast_solve", allow)
+        return SolveResult(st, m.value, loops.value, self.info())
+
+    def feast_solve_hermitian(self, op: feast_operator, lmin, lmax, M0, Ne, tol, Y0, lam, X, resid=None,
+                              allow=(FEAST_ERR_NO_CONVERGENCE, FEAST_ERR_M0_TOO_SMALL)) -> SolveResult:
+        """op: feast_operator over complex [27][N] A27 and B27 (device);
+        Y0 (or None) and X: complex N x M0 device buffers."""
+        m, loops = ctypes.c_int(0), ctypes.c_int(0)
+        st = _lib.feast_solve_hermitian(self._h, ctypes.byref(op), float(lmin), float(lmax), int(M0), int(Ne),
+                                        float(tol), _ptr(Y0), _ptr(lam), _ptr(X), _ptr(resid), ctypes.byref(m),
+                                        ctypes.byref(loops))
+        self._check(st, "feast_solve_hermitian", allow)
         return SolveResult(st, m.value, loops.value, self.info())
 
     def feast_solve_batched(self, ops, lmin, lmax, M0, Ne, tol, Y0, lam, X, resid=None, workers=0, raise_on_error=True):

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/feast.h"
+#include "hermitian.cuh"
 #include "iterative.cuh"
 #include "kernels.cuh"
 #include "mixed.cuh"
@@ -158,13 +159,16 @@ struct feast_handle {
   DevBuf RHS, Q, Qp, AQf, BQf, Xb, Yb, Xout, part, AQ, BQ, eps, Phi, work, norms, normA, lam_d, perm_d, resid_d,
       residp_d;
   MixedWork mixed;
+  // Hermitian path (complex buffers)
+  DevBuf hF, hG, hTmp, hRHS, hQ, hAQf, hBQf, hX, hY, hXout, hPart, hAQ, hBQ, hPhi, hWork, hZ, hCoef, hEps;
   cudaEvent_t ev[8] = {};
 
   void release_all() {
     for (DevBuf* b : {&opA, &opB, &F, &T1, &T, &L, &Pinv, &G, &Tmp, &Zd, &coefd, &status, &cgw, &RHS, &Q, &Qp, &AQf,
                       &BQf,
                       &Xb, &Yb, &Xout, &part, &AQ, &BQ, &eps, &Phi, &work, &norms, &normA, &lam_d, &perm_d,
-                      &resid_d, &residp_d})
+                      &resid_d, &residp_d, &hF, &hG, &hTmp, &hRHS, &hQ, &hAQf, &hBQf, &hX, &hY, &hXout, &hPart, &hAQ,
+                      &hBQ, &hPhi, &hWork, &hZ, &hCoef, &hEps})
       b->release();
     mixed.release();
   }
@@ -679,6 +683,169 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
     }
     h->info.gpu_launches = prof::launches() - launches0;
     if (h->opt.profile) prof::collect(h->info.kernel_ms, h->info.kernel_launches, h->info.kernel_flops);
+    h->info.t_total_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_wall0).count();
+    if (count >= M0) final_status = FEAST_ERR_M0_TOO_SMALL;
+    else if (!converged) final_status = FEAST_ERR_NO_CONVERGENCE;
+  });
+  if (st != FEAST_OK) return st;
+  if (final_status == FEAST_ERR_M0_TOO_SMALL)
+    h->err = "every Ritz value lies inside the interval: increase M0";
+  else if (final_status == FEAST_ERR_NO_CONVERGENCE)
+    h->err = "trace test not met within max_loops";
+  return final_status;
+}
+
+feast_status feast_solve_hermitian(feast_handle* h, const feast_operator* op, double lmin, double lmax, int M0,
+                                   int Ne, double tol, const double* Y0, double* lambda, double* X, double* resid,
+                                   int* m_found, int* loops) {
+  if (!h) return FEAST_ERR_ARG;
+  feast_status final_status = FEAST_OK;
+  feast_status st = guarded(h, [&] {
+    auto t_wall0 = std::chrono::steady_clock::now();
+    h->info = feast_info{};
+    prof::set_enabled(false);
+    const long long launches0 = prof::launches();
+    if (!(lmin < lmax) || !std::isfinite(lmin) || !std::isfinite(lmax)) fail(FEAST_ERR_ARG, "need lmin < lmax");
+    if (Ne < 1 || Ne > 32) fail(FEAST_ERR_ARG, "Ne must be in [1, 32]");
+    if (!op || !lambda || !X || !m_found || !loops) fail(FEAST_ERR_ARG, "NULL argument");
+    if (!(tol >= 0.0)) fail(FEAST_ERR_ARG, "tol must be >= 0");
+    if (op->nx < 1 || op->ny < 1 || op->nz < 1) fail(FEAST_ERR_ARG, "grid sizes must be >= 1");
+    if (!is_device_ptr(op->A27) || !is_device_ptr(op->B27) || !is_device_ptr(X) || (Y0 && !is_device_ptr(Y0)))
+      fail(FEAST_ERR_ARG, "the Hermitian solve takes device arrays for A27, B27, Y0 and X");
+    const Grid g{op->nx, op->ny, op->nz};
+    if (g.n() > 4096) fail(FEAST_ERR_ARG, "layer size nx*ny must be <= 4096");
+    const long long N = g.N();
+    if (M0 < 1 || M0 > 64 || M0 > N) fail(FEAST_ERR_ARG, "M0 must be in [1, min(N, 64)]");
+    const HermOp o{g, reinterpret_cast<const cplx*>(op->A27), reinterpret_cast<const cplx*>(op->B27)};
+    cudaStream_t s = h->stream;
+    reset_status(h);
+    // the 2 Ne shifts Z_e, conj Z_e and their coefficients in Eq. 12:
+    // -(w_e r / 4) e^{i theta_e} and -(w_e r / 4) e^{-i theta_e}
+    Contour ct = make_contour(lmin, lmax, Ne);
+    const int nodes = 2 * Ne;
+    std::vector<cplx> Zh(nodes), ch(nodes);
+    for (int e = 0; e < Ne; ++e) {
+      const double a = -(ct.w[e] * ct.r / 4.0);
+      Zh[e] = ct.Z[e];
+      Zh[Ne + e] = cplx{ct.Z[e].re, -ct.Z[e].im};
+      ch[e] = cplx{a * std::cos(ct.theta[e]), a * std::sin(ct.theta[e])};
+      ch[Ne + e] = cplx{a * std::cos(ct.theta[e]), -a * std::sin(ct.theta[e])};
+    }
+    h->hZ.ensure(sizeof(cplx) * nodes, "Z");
+    h->hCoef.ensure(sizeof(cplx) * nodes, "coef");
+    ck(cudaMemcpyAsync(h->hZ.p, Zh.data(), sizeof(cplx) * nodes, cudaMemcpyHostToDevice, s), "Z");
+    ck(cudaMemcpyAsync(h->hCoef.p, ch.data(), sizeof(cplx) * nodes, cudaMemcpyHostToDevice, s), "coef");
+    const int n = g.n();
+    const size_t cblk = sizeof(cplx) * (size_t)N * M0;
+    h->hF.ensure(herm_factor_bytes(g, nodes), "Hermitian factors");
+    h->hG.ensure(cblk * nodes, "node solutions");
+    h->hTmp.ensure(sizeof(cplx) * (size_t)nodes * n * M0, "solve scratch");
+    for (DevBuf* b : {&h->hRHS, &h->hQ, &h->hAQf, &h->hBQf, &h->hX, &h->hY, &h->hXout}) b->ensure(cblk, "block");
+    h->hPart.ensure(sizeof(cplx) * herm_gram_elems(N, M0), "gram partials");
+    for (DevBuf* b : {&h->hAQ, &h->hBQ, &h->hPhi}) b->ensure(sizeof(cplx) * M0 * M0, "reduced");
+    h->hWork.ensure(sizeof(cplx) * 3 * M0 * M0, "eig work");
+    h->hEps.ensure(sizeof(double) * M0, "eps");
+    h->lam_d.ensure(sizeof(double) * M0, "lambda");
+    h->perm_d.ensure(sizeof(int) * M0, "perm");
+    h->resid_d.ensure(sizeof(double) * M0, "resid");
+    h->residp_d.ensure(sizeof(double) * M0, "resid paper");
+    h->norms.ensure(sizeof(double) * 3 * M0, "norms");
+    h->normA.ensure(sizeof(double), "normA");
+    cplx* Zd = h->hZ.as<cplx>();
+
+    ck(cudaEventRecord(h->ev[0], s), "event");
+    herm_factor(s, o, nodes, Zd, h->hF.as<cplx>(), h->status.as<int>());
+    ck(cudaEventRecord(h->ev[1], s), "event");
+    check_status(h);
+    h->info.t_factor_ms = elapsed(h->ev[0], h->ev[1]);
+    h->info.factor_flops = (long long)8 * n * (long long)n * n * g.nz * nodes;
+
+    if (Y0)
+      ck(cudaMemcpyAsync(h->hY.p, Y0, cblk, cudaMemcpyDeviceToDevice, s), "copy Y0");
+    else
+      herm_random(s, N, M0, h->opt.seed, h->hY.as<cplx>());
+    std::vector<double> eps(M0);
+    double prev_trace = 0.0, t_solve = 0.0, t_rr = 0.0;
+    int prev_count = -1, count = 0, loop = 0;
+    bool converged = false;
+    for (loop = 1; loop <= h->opt.max_loops; ++loop) {
+      ck(cudaEventRecord(h->ev[2], s), "event");
+      herm_stencil(s, g, o.B27, h->hY.as<cplx>(), h->hRHS.as<cplx>(), M0);   // RHS = B Y
+      herm_solve(s, o, nodes, Zd, h->hF.as<cplx>(), h->hRHS.as<cplx>(), h->hG.as<cplx>(), h->hTmp.as<cplx>(), M0);
+      herm_quadrature(s, N, M0, nodes, h->hCoef.as<cplx>(), h->hG.as<cplx>(), h->hQ.as<cplx>());   // Eq. 12
+      ck(cudaEventRecord(h->ev[3], s), "event");
+      herm_stencil(s, g, o.A27, h->hQ.as<cplx>(), h->hAQf.as<cplx>(), M0);
+      herm_stencil(s, g, o.B27, h->hQ.as<cplx>(), h->hBQf.as<cplx>(), M0);
+      herm_gram(s, N, M0, h->hQ.as<cplx>(), h->hAQf.as<cplx>(), h->hPart.as<cplx>(), h->hAQ.as<cplx>());
+      herm_gram(s, N, M0, h->hQ.as<cplx>(), h->hBQf.as<cplx>(), h->hPart.as<cplx>(), h->hBQ.as<cplx>());
+      herm_reduced_eig(s, M0, h->hAQ.as<cplx>(), h->hBQ.as<cplx>(), h->hEps.as<double>(), h->hPhi.as<cplx>(),
+                       h->hWork.as<cplx>(), h->status.as<int>());
+      herm_gemm_tall(s, N, M0, M0, h->hQ.as<cplx>(), h->hPhi.as<cplx>(), h->hX.as<cplx>());
+      ck(cudaEventRecord(h->ev[4], s), "event");
+      ck(cudaMemcpyAsync(eps.data(), h->hEps.p, sizeof(double) * M0, cudaMemcpyDeviceToHost, s), "eps");
+      check_status(h);
+      t_solve += elapsed(h->ev[2], h->ev[3]);
+      t_rr += elapsed(h->ev[3], h->ev[4]);
+      count = 0;
+      double trace = 0.0, scale = 0.0;
+      for (int j = 0; j < M0; ++j)
+        if (eps[j] >= lmin && eps[j] <= lmax) {
+          ++count;
+          trace += eps[j];
+          scale += std::fabs(eps[j]);
+        }
+      if (loop - 1 < 64) {
+        h->info.trace[loop - 1] = trace;
+        h->info.rel_change[loop - 1] = -1.0;
+      }
+      if (prev_count >= 0) {
+        const double change = scale > 0 ? std::fabs(trace - prev_trace) / scale : 0.0;
+        if (loop - 1 < 64) h->info.rel_change[loop - 1] = change;
+        if (count == prev_count && change <= tol) converged = true;
+      }
+      std::swap(h->hX, h->hY);   // Y = X: the next right-hand side is B X
+      if (converged) break;
+      prev_trace = trace;
+      prev_count = count;
+    }
+    if (loop > h->opt.max_loops) loop = h->opt.max_loops;
+    std::vector<int> perm;
+    for (int j = 0; j < M0; ++j)
+      if (eps[j] >= lmin && eps[j] <= lmax) perm.push_back(j);
+    for (int j = 0; j < M0; ++j)
+      if (!(eps[j] >= lmin && eps[j] <= lmax)) perm.push_back(j);
+    std::vector<double> lam(M0);
+    for (int j = 0; j < M0; ++j) lam[j] = eps[perm[j]];
+    ck(cudaMemcpyAsync(h->perm_d.p, perm.data(), sizeof(int) * M0, cudaMemcpyHostToDevice, s), "perm");
+    ck(cudaMemcpyAsync(h->lam_d.p, lam.data(), sizeof(double) * M0, cudaMemcpyHostToDevice, s), "lambda");
+    herm_permute(s, N, M0, h->perm_d.as<int>(), h->hY.as<cplx>(), h->hXout.as<cplx>());
+    herm_residuals(s, g, o.A27, o.B27, h->lam_d.as<double>(), h->hXout.as<cplx>(), M0, h->hAQf.as<cplx>(),
+                   h->hBQf.as<cplx>(), h->norms.as<double>(), h->normA.as<double>(), h->resid_d.as<double>(),
+                   h->residp_d.as<double>());
+    std::vector<double> r1(M0), rp(M0);
+    ck(cudaMemcpyAsync(r1.data(), h->resid_d.p, sizeof(double) * M0, cudaMemcpyDeviceToHost, s), "resid");
+    ck(cudaMemcpyAsync(rp.data(), h->residp_d.p, sizeof(double) * M0, cudaMemcpyDeviceToHost, s), "resid");
+    ck(cudaMemcpyAsync(X, h->hXout.p, cblk, cudaMemcpyDeviceToDevice, s), "copy X");
+    if (is_device_ptr(lambda))
+      ck(cudaMemcpyAsync(lambda, h->lam_d.p, sizeof(double) * M0, cudaMemcpyDeviceToDevice, s), "copy lambda");
+    if (resid && is_device_ptr(resid))
+      ck(cudaMemcpyAsync(resid, h->resid_d.p, sizeof(double) * M0, cudaMemcpyDeviceToDevice, s), "copy resid");
+    ck(cudaStreamSynchronize(s), "sync");
+    ck(cudaGetLastError(), "kernels");
+    if (!is_device_ptr(lambda)) std::memcpy(lambda, lam.data(), sizeof(double) * M0);
+    if (resid && !is_device_ptr(resid)) std::memcpy(resid, r1.data(), sizeof(double) * M0);
+    *m_found = count;
+    *loops = loop;
+    h->info.loops = loop;
+    h->info.m_found = count;
+    h->info.t_solve_ms = t_solve;
+    h->info.t_rr_ms = t_rr;
+    for (int j = 0; j < count; ++j) {
+      h->info.resid_max = std::max(h->info.resid_max, r1[j]);
+      h->info.resid_paper_max = std::max(h->info.resid_paper_max, rp[j]);
+    }
+    h->info.gpu_launches = prof::launches() - launches0;
     h->info.t_total_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_wall0).count();
     if (count >= M0) final_status = FEAST_ERR_M0_TOO_SMALL;

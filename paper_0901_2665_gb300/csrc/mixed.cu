@@ -593,20 +593,27 @@ struct SolveEpi {
   long long sQ = 0, ldq = 0;   // node stride, column stride
   const cplx* coef = nullptr;  // Ne quadrature coefficients
   int qfirst = 0;              // 1: store (first solve), 0: accumulate (refinement)
-  __device__ void operator()(int e, int tm, int tn, int row, uint32_t taddr, int, uint8_t*) const {
+  // the old shares of this thread's row, loaded while the main loop runs
+  // (a refinement step reads them back)
+  struct Pre {
+    double q[CB];
+  };
+  __device__ void prefetch(int e, int tm, int tn, int row, Pre& pre) const {
+    const int p = tm * tc::kBlockM + row;
+    const bool rd = qp && !qfirst && p < n;
+#pragma unroll
+    for (int t = 0; t < CB; ++t) {
+      const int m = tn * CB + t;
+      pre.q[t] = (rd && m < k) ? qp[e * sQ + (long long)m * ldq + p] : 0.0;
+    }
+  }
+  __device__ void operator()(int e, int tm, int tn, int row, uint32_t taddr, int, uint8_t*, const Pre& pre) const {
     const int p = tm * tc::kBlockM + row;
     f2* o = out + e * sOut;
     cplx ce{0.0, 0.0};
     if (qp) ce = coef[e];
-#pragma unroll 1
-    for (int c0 = 0; c0 < CB; c0 += 16) {
-      // the old shares first, as 16 independent loads (a refinement step)
-      double qold[16];
 #pragma unroll
-      for (int t = 0; t < 16; ++t) {
-        const int m = tn * CB + c0 + t;
-        qold[t] = (qp && !qfirst && p < n && c0 + t < CB && m < k) ? qp[e * sQ + (long long)m * ldq + p] : 0.0;
-      }
+    for (int c0 = 0; c0 < CB; c0 += 16) {
       float re[16], im[16];
       tc::tmem_ld16(taddr + c0, re);
       tc::tmem_ld16(taddr + CB + c0, im);
@@ -618,7 +625,7 @@ struct SolveEpi {
           const f2 x{alpha * re[t], alpha * im[t]};
           o[(long long)m * ldo + p] = x;
           if (qp)
-            qp[e * sQ + (long long)m * ldq + p] = qold[t] + (ce.re * (double)x.x - ce.im * (double)x.y);
+            qp[e * sQ + (long long)m * ldq + p] = pre.q[c0 + t] + (ce.re * (double)x.x - ce.im * (double)x.y);
         }
       }
     }

@@ -232,6 +232,20 @@ struct EpiExtra<E, std::void_t<decltype(E::kExtraSmem)>> {
   static constexpr size_t kBytes = E::kExtraSmem;
 };
 
+// Epilogues may also declare a register block `Pre` and a member
+// prefetch(e, tm, tn, row, Pre&) that the epilogue threads run before they
+// wait for the accumulator (global loads that the epilogue will need, issued
+// while the main loop is under way); the accumulator is then taken through
+// epi(e, tm, tn, row, lane_taddr, ept, stage, pre).
+template <class E, class = void>
+struct EpiPre {
+  static constexpr bool kHas = false;
+};
+template <class E>
+struct EpiPre<E, std::void_t<typename E::Pre>> {
+  static constexpr bool kHas = true;
+};
+
 template <int BN, int STAGES, class Epi>
 constexpr size_t smem_bytes() {
   return Smem<BN, STAGES>::kBytes + (EpiExtra<Epi>::kBytes ? 1024 + EpiExtra<Epi>::kBytes : 0);
@@ -336,6 +350,16 @@ __global__ void __launch_bounds__(kThreads)
     const int row = q * 32 + lane;
     if constexpr (EpiExtra<Epi>::kBytes > 0)
       epi.prologue(e, tm, tn, static_cast<int>(threadIdx.x) - 64, smem + S::kPipeBytes + 1024, status, abort_flag);
+    if constexpr (EpiPre<Epi>::kHas) {
+      typename Epi::Pre pre;
+      epi.prefetch(e, tm, tn, row, pre);
+      mbar_wait(tfull, 0, status, abort_flag);
+      tc_fence_after();
+      epilogue_sync();   // uniform abort decision, as below
+      if (!*abort_flag)
+        epi(e, tm, tn, row, tmem + (static_cast<uint32_t>(q * 32) << 16), static_cast<int>(threadIdx.x) - 64, smem,
+            pre);
+    } else {
     mbar_wait(tfull, 0, status, abort_flag);
     tc_fence_after();
     // one decision for the whole epilogue group: a thread that gave up set
@@ -348,6 +372,7 @@ __global__ void __launch_bounds__(kThreads)
               smem, smem + S::kPipeBytes + 1024, status, abort_flag);
     } else if (!*abort_flag) {
       epi(e, tm, tn, row, tmem + (static_cast<uint32_t>(q * 32) << 16), static_cast<int>(threadIdx.x) - 64, smem);
+    }
     }
   }
   tc_fence_before();
