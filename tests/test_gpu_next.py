@@ -231,15 +231,16 @@ def test_iterative_inner_solves_example_iii(intervals):
 
 def test_iterative_inner_solves_warm_sequence():
     """Fig. 3 in miniature: a potential changed in small steps, inner systems
-    solved iteratively to 1e-3, trace tolerance 1e-8.  Every problem yields
-    the dense pencil's eigenvalues to 1e-5, started from the previous
-    problem's subspace or from a random block; the warm start's first loop is
-    already far closer to the converged trace than a random start's (the
-    loop count itself is noisy here: inexact inner solves perturb the trace
-    near the 1e-8 tolerance from loop to loop)."""
+    solved iteratively (to 1e-4 here; at 1e-3 the inexact solves perturb
+    the trace from loop to loop by about the 1e-8 tolerance on a problem this
+    small, so the loop count turns noisy), trace tolerance 1e-8.  Every
+    problem yields the dense pencil's eigenvalues to 1e-5 from a random start
+    and from the previous problem's subspace; the warm start's first loop is
+    at least ten times closer to the converged trace, and it needs no more
+    loops than the random start."""
     nx, ny, nz, M, M0 = 8, 8, 12, 8, 14
     base = workloads.gaussian_potential(6, 21, nx, ny, nz)
-    h = _cocg_handle(1e-3)
+    h = _cocg_handle(1e-4)
     Xprev = None
     for t in range(4):
         pot = dataclasses.replace(base, amps=base.amps * (1.0 + 0.01 * t))
@@ -251,7 +252,7 @@ def test_iterative_inner_solves_warm_sequence():
         ref = lam[inside]
         m_in = int(inside.sum())
         dop, keep = dev_op(op)
-        first_err = {}
+        first_err, loops, Xout = {}, {}, {}
         for start in ("random", "warm"):
             if start == "warm" and Xprev is None:
                 continue
@@ -262,10 +263,9 @@ def test_iterative_inner_solves_warm_sequence():
             got = lamd.cpu().numpy()[:m_in]
             assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), (t, start)
             first_err[start] = abs(r.info.trace[0] - ref.sum()) / np.abs(ref).sum()
-            if start == "warm":
-                Xwarm = X.clone()
+            loops[start] = r.loops
+            Xout[start] = X.clone()
         if "warm" in first_err:
-            assert first_err["warm"] <= 1e-2 * first_err["random"], (t, first_err)
-            Xprev = Xwarm
-        else:
-            Xprev = X.clone()
+            assert first_err["warm"] <= 0.1 * first_err["random"], (t, first_err)
+            assert loops["warm"] <= loops["random"], (t, loops)
+        Xprev = Xout.get("warm", Xout["random"])
