@@ -866,7 +866,7 @@ static double instance_bytes(const feast_operator& op, int M0, int Ne, int preci
   const double blk = 8.0 * N * M0;
   double b = 8.0 * N * M0 * Ne + 12.0 * blk + 2.0 * 27.0 * N * 8.0;   // quadrature shares, loop blocks, operator
   if (precision == FEAST_PREC_MIXED)
-    b += 4.0 * Ne * op.nz * n * ldF + 8.0 * Ne * 27.0 * N + 3.0 * 8.0 * N * M0 * Ne + 4.0 * Ne * 3.0 * n * ldF;
+    b += 4.0 * Ne * op.nz * n * ldF + 8.0 * Ne * 27.0 * N + 3.0 * 8.0 * N * M0 * Ne + 4.0 * Ne * 6.0 * n * ldF;
   else
     b += 16.0 * Ne * op.nz * n * n + 16.0 * Ne * n * n + 16.0 * N * M0 * Ne;
   return b * 1.05 + 64.0 * 1024 * 1024;

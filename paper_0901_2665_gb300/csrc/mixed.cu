@@ -61,6 +61,7 @@ struct Dims {
   int CB;        // complex columns per solve-GEMM tile
   int nblkCB;    // ceil(k / CB)
   int ldB;       // floats per embedded RHS row
+  int K;         // middle layer of the two-ended elimination (nz - 1: one-ended)
 };
 
 // Cf[e][s][i] = (Z_e B - A)[i, i + off(s)] in complex fp32, 0 outside the grid:
@@ -87,51 +88,82 @@ __device__ __forceinline__ f2 cf_at(const Dims& d, const f2* Cf, int e, int s, l
   return Cf[((long long)e * 27 + s) * d.N + row];
 }
 
+// Two-ended elimination.  The layers 0..k-1 are eliminated upwards from
+// layer 0 (chain 0) while the layers nz-1..k+1 are eliminated downwards from
+// layer nz-1 (chain 1), in the same launches; the middle layer k is then
+// eliminated last with both neighbours' complements (a "twisted" block
+// factorisation: the dependent chain of layer steps halves).  The kernels
+// see 2 Ne virtual nodes: v < Ne is node v on chain 0, v >= Ne node v - Ne on
+// chain 1.  Chain 0's previous layer is layer - 1 (couplings in the dz = -1
+// slots 0..8), chain 1's is layer + 1 (slots 18..26); by the symmetry of
+// M_e, the coupling back to a chain's next layer is the transpose.
+// k = nz - 1 (chain 1 empty) is the plain one-ended elimination.
+struct Chains {
+  int Ne;          // real nodes
+  int layer[2];    // layer of each chain in this step
+  int rplane[2];   // ping-pong plane holding each chain's previous complement
+  int wplane;      // plane written in this step
+};
+__device__ __forceinline__ int chain_of(const Chains& c, int v) { return v >= c.Ne ? 1 : 0; }
+__device__ __forceinline__ int node_of(const Chains& c, int v) { return v >= c.Ne ? v - c.Ne : v; }
+// first stencil slot of the coupling from a chain's layer to its previous layer
+__device__ __forceinline__ int prev_slot(int chain) { return chain ? 18 : 0; }
+
 // ------------------------------------------------------------------ Schur
-// The fp32 working copies of S_i / S'_i live in a two-layer ping-pong buffer
-// F[e][layer & 1]: the recursion only ever needs the previous layer.
-// T1[a, q] = sum_b S'[a, b] C[q, b] (row-split, fp32), C = dz = -1 slots of layer `layer`
-__global__ void __launch_bounds__(256) k_mx_schur1(Dims d, int layer, const f2* __restrict__ Cf,
+// The fp32 working copies of S_i / S'_i live in a two-plane ping-pong buffer
+// F[v][plane] per virtual node: the recursion only ever needs the previous
+// layer of its chain.
+// T1[v][a, q] = sum_b S'[a, b] C[q, b] (row-split, fp32), C = the coupling of
+// the chain's layer to its previous layer (v = blockIdx.z)
+__global__ void __launch_bounds__(256) k_mx_schur1(Dims d, Chains ch, const f2* __restrict__ Cf,
                                                    const float* __restrict__ F, float* __restrict__ T1) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  const int a = blockIdx.y, e = blockIdx.z;
+  const int a = blockIdx.y, v = blockIdx.z;
   if (q >= d.n) return;
-  const long long rowq = (long long)layer * d.n + q;
-  const float* S = F + (((long long)e * 2 + ((layer - 1) & 1)) * d.n + a) * d.ldF;
+  const int c = chain_of(ch, v), e = node_of(ch, v);
+  const long long rowq = (long long)ch.layer[c] * d.n + q;
+  const float* S = F + (((long long)v * 2 + ch.rplane[c]) * d.n + a) * d.ldF;
   f2 acc{0.f, 0.f};
 #pragma unroll
   for (int t = 0; t < 9; ++t) {
     const int b = q + (t % 3 - 1) + d.nx * (t / 3 - 1);
-    const f2 c = cf_at(d, Cf, e, t, rowq);
-    if (c.x != 0.f || c.y != 0.f) f2fma(acc, f2{S[b], S[d.n + b]}, c);
+    const f2 cv = cf_at(d, Cf, e, prev_slot(c) + t, rowq);
+    if (cv.x != 0.f || cv.y != 0.f) f2fma(acc, f2{S[b], S[d.n + b]}, cv);
   }
-  float* out = T1 + ((long long)e * d.n + a) * d.ldF;
+  float* out = T1 + ((long long)v * d.n + a) * d.ldF;
   out[q] = acc.x;
   out[d.n + q] = acc.y;
 }
 
-// S_i[p, q] = D_i[p, q] + sum_a C[p, a] T1[a, q] -> F (layer i)
-__global__ void __launch_bounds__(256) k_mx_schur2(Dims d, int layer, const f2* __restrict__ Cf,
-                                                   const float* __restrict__ T1, float* __restrict__ F) {
+// S[p, q] = D[p, q] + sum_a C[p, a] T1[a, q] -> F (plane wplane of v), with
+// C the coupling of v's layer to its previous layer (has_prev: 0 on a chain's
+// first layer).  middle: v < Ne only; the middle layer takes both chains'
+// contributions, C0 T1[v] + C1 T1[v + Ne] (the second when has_prev1).
+__global__ void __launch_bounds__(256) k_mx_schur2(Dims d, Chains ch, int has_prev, int middle, int has_prev1,
+                                                   const f2* __restrict__ Cf, const float* __restrict__ T1,
+                                                   float* __restrict__ F) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  const int p = blockIdx.y, e = blockIdx.z;
+  const int p = blockIdx.y, v = blockIdx.z;
   if (q >= d.n) return;
-  const long long rowp = (long long)layer * d.n + p;
+  const int c = chain_of(ch, v), e = node_of(ch, v);
+  const long long rowp = (long long)ch.layer[c] * d.n + p;
   const int px = p % d.nx, py = p / d.nx;
   f2 acc{0.f, 0.f};
   const int ddx = (q % d.nx) - px, ddy = (q / d.nx) - py;
   if (ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1) acc = cf_at(d, Cf, e, 9 + (ddy + 1) * 3 + (ddx + 1), rowp);
-  if (layer > 0) {
-    const float* T = T1 + (long long)e * d.n * d.ldF;
+  auto add = [&](int vt, int slot0) {
+    const float* T = T1 + (long long)vt * d.n * d.ldF;
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
-      const f2 c = cf_at(d, Cf, e, t, rowp);
-      if (c.x == 0.f && c.y == 0.f) continue;
+      const f2 cv = cf_at(d, Cf, e, slot0 + t, rowp);
+      if (cv.x == 0.f && cv.y == 0.f) continue;
       const float* Trow = T + (long long)(p + (t % 3 - 1) + d.nx * (t / 3 - 1)) * d.ldF;
-      f2fma(acc, c, f2{Trow[q], Trow[d.n + q]});
+      f2fma(acc, cv, f2{Trow[q], Trow[d.n + q]});
     }
-  }
-  float* out = F + (((long long)e * 2 + (layer & 1)) * d.n + p) * d.ldF;
+  };
+  if (has_prev) add(v, prev_slot(c));
+  if (middle && has_prev1) add(v + ch.Ne, prev_slot(1));
+  float* out = F + (((long long)v * 2 + ch.wplane) * d.n + p) * d.ldF;
   out[q] = acc.x;
   out[d.n + q] = acc.y;
 }
@@ -170,7 +202,7 @@ __device__ __forceinline__ f2 f2inv_fast(f2 a) {
 // index is a compile-time constant.  RPT = 16 (256 threads) measured fastest:
 // 32 rows per thread leaves one warp per scheduler to hide every latency.
 template <int RPT>
-__global__ void __launch_bounds__(kPanel * (kPanel / RPT)) k_mx_pinv(Dims d, int layer, int k0, int bw,
+__global__ void __launch_bounds__(kPanel * (kPanel / RPT)) k_mx_pinv(Dims d, int plane, int k0, int bw,
                                                                          const float* __restrict__ F,
                                                                          f2* __restrict__ PinvOut, int* status) {
   constexpr int H = kPanel / RPT;   // row blocks
@@ -183,7 +215,7 @@ __global__ void __launch_bounds__(kPanel * (kPanel / RPT)) k_mx_pinv(Dims d, int
   const int tid = threadIdx.x;
   const int j = tid % kPanel, h = tid / kPanel;
   const int n = d.n;
-  const float* Fl = F + ((long long)e * 2 + (layer & 1)) * n * d.ldF;
+  const float* Fl = F + ((long long)e * 2 + plane) * n * d.ldF;
   if (tid == 0) bad = 0;
   f2 v[RPT];
 #pragma unroll
@@ -276,7 +308,7 @@ constexpr int kPinvRpt = FEAST_PINV_RPT;   // rows per thread of the panel inver
 // L[i, :] = S[i, K], written as the TF32-rounded GEMM operands
 // Aop = [Tr | Ti] (row i) and Bop (embedded L, rows in blocks of 64 complex
 // columns: 64 rows [Lr, -Li] then 64 rows [Li, Lr]), and in fp32 as Tc.
-__global__ void __launch_bounds__(256) k_mx_panel_T(Dims d, int layer, int k0, int bw, const float* __restrict__ F,
+__global__ void __launch_bounds__(256) k_mx_panel_T(Dims d, int plane, int k0, int bw, const float* __restrict__ F,
                                                     const f2* __restrict__ PinvIn, float* __restrict__ Aop,
                                                     float* __restrict__ Bop, f2* __restrict__ Tc) {
   __shared__ f2 Ps[kPanel][kPanel + 1];
@@ -285,7 +317,7 @@ __global__ void __launch_bounds__(256) k_mx_panel_T(Dims d, int layer, int k0, i
   const int r0 = blockIdx.x * kRowsPerPanelCta;
   const int tid = threadIdx.x;
   const int n = d.n;
-  const float* Fl = F + ((long long)e * 2 + (layer & 1)) * n * d.ldF;
+  const float* Fl = F + ((long long)e * 2 + plane) * n * d.ldF;
   const f2* Pin = PinvIn + (long long)e * kPanel * kPanel;
   for (int t = tid; t < kPanel * kPanel; t += 256) Ps[t / kPanel][t % kPanel] = Pin[t];
   for (int t = tid; t < kRowsPerPanelCta * kPanel; t += 256) {
@@ -345,16 +377,18 @@ constexpr int kStageLd = tc::kBlockM + 1;   // staging row stride (floats): conf
 // The accumulator goes through shared memory (one half, real or imaginary,
 // at a time) so that the read-modify-write of S is coalesced along rows.
 struct SweepEpi {
-  float* F;        // row-split fp32 working copy of the layer being swept, node stride sF floats
+  float* F;        // row-split fp32 working copy of the layer being swept, virtual-node stride sF floats
   long long sF;
-  float* Fr;       // last panel only: TF32-rounded copy of the finished S' (solve operand), node stride sFr
+  float* Fr;       // last panel only: TF32-rounded copies of the finished S' (solve operand), node stride sFr
   long long sFr;
   int ldF, n, k0, bw;
-  const f2* Tc;    // n x 64 per node
-  const f2* Pinv;  // 64 x 64 per node
+  const f2* Tc;    // n x 64 per virtual node
+  const f2* Pinv;  // 64 x 64 per virtual node
+  Chains ch;       // which node and layer virtual node e is
   __device__ void operator()(int e, int tm, int tn, int row, uint32_t taddr, int ept, uint8_t* stage) const {
     float* Sg = reinterpret_cast<float*>(stage);   // 64 columns x kStageLd
     float* Fe = F + e * sF;
+    float* Fre = Fr ? Fr + node_of(ch, e) * sFr + (long long)ch.layer[chain_of(ch, e)] * n * ldF : nullptr;
     const f2* T = Tc + (long long)e * n * kPanel;
     const f2* Pi = Pinv + (long long)e * kPanel * kPanel;
 #pragma unroll 1
@@ -401,7 +435,7 @@ struct SweepEpi {
             val = -(half ? p2.y : p2.x);
           }
           Fe[(long long)i * ldF + half * n + j] = val;
-          if (Fr) Fr[e * sFr + (long long)i * ldF + half * n + j] = tc::to_tf32(val);
+          if (Fre) Fre[(long long)i * ldF + half * n + j] = tc::to_tf32(val);
         }
       }
       tc::epilogue_sync();
@@ -422,10 +456,11 @@ struct SweepEpi {
 struct SweepEpiTma {
   static constexpr size_t kTileBytes = 4 * 16384;
   static constexpr size_t kExtraSmem = kTileBytes + 64;
-  CUtensorMap mapF;    // fp32 working layers: inner 2n, rows n, planes Ne*2
+  CUtensorMap mapF;    // fp32 working layers: inner 2n, rows n, planes 2 per virtual node
   CUtensorMap mapFr;   // TF32 solve copy: inner 2n, rows n, planes Ne*nz
-  int plane;           // layer & 1
-  int layer, nz;
+  int plane;           // working plane of this step
+  Chains ch;           // which node and layer virtual node e is
+  int nz;
   int n, k0, bw;
   int last;            // last panel: also store the TF32 copy
   const f2* Tc;
@@ -567,7 +602,8 @@ struct SweepEpiTma {
       if (ept == 0) {
 #pragma unroll
         for (int b = 0; b < 4; ++b)
-          tc::tma_store_3d(&mapFr, extra + b * 16384, box_x(b, tn), tm * tc::kBlockM, e * nz + layer);
+          tc::tma_store_3d(&mapFr, extra + b * 16384, box_x(b, tn), tm * tc::kBlockM,
+                           node_of(ch, e) * nz + ch.layer[chain_of(ch, e)]);
         tc::bulk_commit();
       }
     }
@@ -589,10 +625,18 @@ struct SolveEpi {
   long long sOut, ldo;
   int n, k;
   float alpha;
-  double* qp = nullptr;        // per-node quadrature partials (row offset of the layer applied)
+  double* qp = nullptr;        // per-node quadrature partials
   long long sQ = 0, ldq = 0;   // node stride, column stride
   const cplx* coef = nullptr;  // Ne quadrature coefficients
   int qfirst = 0;              // 1: store (first solve), 0: accumulate (refinement)
+  // node_rows: out and qp belong to the real node of virtual node e, at the
+  // rows of its chain's layer (the backward sweep); else out is per virtual
+  // node (the forward products)
+  int node_rows = 0;
+  Chains ch{};
+  __device__ long long base(int e, long long stride) const {
+    return node_rows ? node_of(ch, e) * stride + (long long)ch.layer[chain_of(ch, e)] * n : e * stride;
+  }
   // the old shares of this thread's row, loaded while the main loop runs
   // (a refinement step reads them back)
   struct Pre {
@@ -601,17 +645,19 @@ struct SolveEpi {
   __device__ void prefetch(int e, int tm, int tn, int row, Pre& pre) const {
     const int p = tm * tc::kBlockM + row;
     const bool rd = qp && !qfirst && p < n;
+    const double* q = qp ? qp + base(e, sQ) : nullptr;
 #pragma unroll
     for (int t = 0; t < CB; ++t) {
       const int m = tn * CB + t;
-      pre.q[t] = (rd && m < k) ? qp[e * sQ + (long long)m * ldq + p] : 0.0;
+      pre.q[t] = (rd && m < k) ? q[(long long)m * ldq + p] : 0.0;
     }
   }
   __device__ void operator()(int e, int tm, int tn, int row, uint32_t taddr, int, uint8_t*, const Pre& pre) const {
     const int p = tm * tc::kBlockM + row;
-    f2* o = out + e * sOut;
+    f2* o = out + base(e, sOut);
+    double* q = qp ? qp + base(e, sQ) : nullptr;
     cplx ce{0.0, 0.0};
-    if (qp) ce = coef[e];
+    if (qp) ce = coef[node_of(ch, e)];
 #pragma unroll
     for (int c0 = 0; c0 < CB; c0 += 16) {
       float re[16], im[16];
@@ -624,8 +670,7 @@ struct SolveEpi {
         if (c0 + t < CB && m < k) {
           const f2 x{alpha * re[t], alpha * im[t]};
           o[(long long)m * ldo + p] = x;
-          if (qp)
-            qp[e * sQ + (long long)m * ldq + p] = pre.q[c0 + t] + (ce.re * (double)x.x - ce.im * (double)x.y);
+          if (q) q[(long long)m * ldq + p] = pre.q[c0 + t] + (ce.re * (double)x.x - ce.im * (double)x.y);
         }
       }
     }
@@ -653,24 +698,30 @@ __device__ __forceinline__ void write_emb(const Dims& d, float* Bemb, int e, int
   im_row[d.n + p] = tc::to_tf32(g.x);
 }
 
-// forward: g_i = R_i + C_i t (t = S'_{i-1} g_{i-1}; absent for layer 0); one
-// thread per (row p, column m).  R is the real RHS (Rreal) or the complex64
-// residual of node e (Rc).
-__global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, int layer, const f2* __restrict__ Cf,
-                                                       const double* __restrict__ Rreal, const f2* __restrict__ Rc,
-                                                       const f2* __restrict__ Tout, f2* __restrict__ Gc,
-                                                       float* __restrict__ Bemb, NodeList nl) {
+// forward: g = R + C t on a chain's layer, t = S'_prev g_prev the product
+// of the chain's previous step (has_prev: 0 on the chain's first layer);
+// one thread per (row p, column m).  R is the real RHS (Rreal) or the
+// complex64 residual of the node (Rc).  middle (chain-0 virtual nodes only):
+// the middle layer adds both chains' products, C0 Tout[v] + C1 Tout[v + Ne]
+// (the second when has_prev1).  CTA z handles the virtual node of the z-th
+// set bit of nl.mask; g goes to the node's solution column, its embedded
+// copy to the virtual node's GEMM operand.
+__global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, Chains ch, int has_prev, int middle, int has_prev1,
+                                                       const f2* __restrict__ Cf, const double* __restrict__ Rreal,
+                                                       const f2* __restrict__ Rc, const f2* __restrict__ Tout,
+                                                       f2* __restrict__ Gc, float* __restrict__ Bemb, NodeList nl) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int m = blockIdx.y, e = tc::nth_set_bit(nl.mask, (int)blockIdx.z);
+  const int m = blockIdx.y, v = tc::nth_set_bit(nl.mask, (int)blockIdx.z);
   if (p >= d.n) return;
-  const long long row = (long long)layer * d.n + p;
+  const int c = chain_of(ch, v), e = node_of(ch, v);
+  const long long row = (long long)ch.layer[c] * d.n + p;
   const long long sG = d.N * d.k;
   f2 g = Rc ? Rc[e * sG + (long long)m * d.N + row] : f2{(float)Rreal[(long long)m * d.N + row], 0.f};
-  if (layer > 0) {
-    const f2* T = Tout + ((long long)e * d.k + m) * d.n;
-    const f2* C = Cf + (long long)e * 27 * d.N + row;
-    const int px = p % d.nx, py = p / d.nx;
-    const bool xm = px > 0, xp = px + 1 < d.nx, ym = py > 0, yp = py + 1 < d.ny;
+  const int px = p % d.nx, py = p / d.nx;
+  const bool xm = px > 0, xp = px + 1 < d.nx, ym = py > 0, yp = py + 1 < d.ny;
+  auto add = [&](int vt, int slot0) {
+    const f2* T = Tout + ((long long)vt * d.k + m) * d.n;
+    const f2* C = Cf + ((long long)e * 27 + slot0) * d.N + row;
     // branch-free taps: an in-plane neighbour outside the grid has a zero
     // coefficient and is read at offset 0 (the row itself) to stay in bounds
 #pragma unroll
@@ -679,24 +730,33 @@ __global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, int layer, const 
       const bool ok = (dx < 0 ? xm : (dx > 0 ? xp : true)) && (dy < 0 ? ym : (dy > 0 ? yp : true));
       f2fma(g, C[(long long)t * d.N], T[p + (ok ? dx + d.nx * dy : 0)]);
     }
-  }
+  };
+  if (has_prev) add(v, prev_slot(c));
+  if (middle && has_prev1) add(v + ch.Ne, prev_slot(1));
   Gc[e * sG + (long long)m * d.N + row] = g;
-  write_emb(d, Bemb, e, p, m, g);
+  write_emb(d, Bemb, v, p, m, g);
 }
 
-// backward: s_i = g_i - U_i x_{i+1} (U_i = M[i, i+1], empty on the top layer)
-__global__ void __launch_bounds__(128) k_mx_couple_bwd(Dims d, int layer, const f2* __restrict__ Cf,
+// backward: s = g - U x_next on a chain's layer, x_next the solution of the
+// chain's next layer towards the middle (chain 0: layer + 1, coupled through
+// the dz = +1 slots; chain 1: layer - 1, the dz = -1 slots); the embedded s
+// goes to the virtual node's GEMM operand.  A layer without a next one (the
+// last layer of a one-ended elimination) takes s = g.
+__global__ void __launch_bounds__(128) k_mx_couple_bwd(Dims d, Chains ch, const f2* __restrict__ Cf,
                                                        const f2* __restrict__ Gc, float* __restrict__ Bemb,
                                                        NodeList nl) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int m = blockIdx.y, e = tc::nth_set_bit(nl.mask, (int)blockIdx.z);
+  const int m = blockIdx.y, v = tc::nth_set_bit(nl.mask, (int)blockIdx.z);
   if (p >= d.n) return;
+  const int c = chain_of(ch, v), e = node_of(ch, v);
+  const int layer = ch.layer[c], next = c ? layer - 1 : layer + 1;
   const long long row = (long long)layer * d.n + p;
   const long long sG = d.N * d.k;
   const f2* col = Gc + e * sG + (long long)m * d.N + row;
   f2 sv = col[0];
-  if (layer + 1 < d.nz) {
-    const f2* C = Cf + ((long long)e * 27 + 18) * d.N + row;
+  if (next >= 0 && next < d.nz) {
+    const f2* C = Cf + ((long long)e * 27 + prev_slot(1 - c)) * d.N + row;
+    const long long dn = c ? -(long long)d.n : (long long)d.n;
     const int px = p % d.nx, py = p / d.nx;
     const bool xm = px > 0, xp = px + 1 < d.nx, ym = py > 0, yp = py + 1 < d.ny;
     // branch-free taps, as in the forward coupling
@@ -704,13 +764,13 @@ __global__ void __launch_bounds__(128) k_mx_couple_bwd(Dims d, int layer, const 
     for (int t = 0; t < 9; ++t) {
       const int dx = t % 3 - 1, dy = t / 3 - 1;
       const bool ok = (dx < 0 ? xm : (dx > 0 ? xp : true)) && (dy < 0 ? ym : (dy > 0 ? yp : true));
-      const f2 c = C[(long long)t * d.N];
-      const f2 x = col[d.n + (ok ? dx + d.nx * dy : 0)];
-      sv.x -= c.x * x.x - c.y * x.y;
-      sv.y -= c.x * x.y + c.y * x.x;
+      const f2 cv = C[(long long)t * d.N];
+      const f2 x = col[dn + (ok ? dx + d.nx * dy : 0)];
+      sv.x -= cv.x * x.x - cv.y * x.y;
+      sv.y -= cv.x * x.y + cv.y * x.x;
     }
   }
-  write_emb(d, Bemb, e, p, m, sv);
+  write_emb(d, Bemb, v, p, m, sv);
 }
 
 // ------------------------------------------------------------------ refinement
@@ -1094,6 +1154,8 @@ Dims make_dims(Grid g, int Ne, int k, int cb = 0) {
   d.CB = cb > 0 ? cb : (k <= 8 ? 8 : (k <= 16 ? 16 : (k <= 32 ? 32 : 64)));
   d.nblkCB = (k + d.CB - 1) / d.CB;
   d.ldB = d.ldF;
+  // two chains need 2 Ne virtual nodes in the 64-bit node masks of the sweeps
+  d.K = 2 * Ne <= 64 ? d.nz / 2 : d.nz - 1;
   return d;
 }
 
@@ -1126,15 +1188,16 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
                          MixedWork& w, int* status) {
   Dims d = make_dims(g, Ne, 1);
   if (!encode_fn()) return "cuTensorMapEncodeTiled is not available from the driver";
+  const int V = 2 * Ne;   // virtual nodes (two chains)
   const size_t fbytes = sizeof(float) * (size_t)Ne * d.nz * d.n * d.ldF;
   if (!ensure(w, B_F, fbytes, s)) return "out of device memory (mixed factors)";
-  if (!ensure(w, B_FW, sizeof(float) * (size_t)Ne * 2 * d.n * d.ldF, s)) return "out of device memory (working layers)";
-  if (!ensure(w, B_T1, sizeof(float) * (size_t)Ne * d.n * d.ldF, s)) return "out of device memory (schur scratch)";
+  if (!ensure(w, B_FW, sizeof(float) * (size_t)V * 2 * d.n * d.ldF, s)) return "out of device memory (working layers)";
+  if (!ensure(w, B_T1, sizeof(float) * (size_t)V * d.n * d.ldF, s)) return "out of device memory (schur scratch)";
   // panel operands are double-buffered by panel parity (lookahead)
-  const size_t aop_sz = (size_t)Ne * d.n * 2 * kPanel;
-  const size_t bop_sz = (size_t)Ne * d.nblk64 * 128 * 2 * kPanel;
-  const size_t tc_sz = (size_t)Ne * d.n * kPanel;
-  const size_t pinv_sz = (size_t)Ne * kPanel * kPanel;
+  const size_t aop_sz = (size_t)V * d.n * 2 * kPanel;
+  const size_t bop_sz = (size_t)V * d.nblk64 * 128 * 2 * kPanel;
+  const size_t tc_sz = (size_t)V * d.n * kPanel;
+  const size_t pinv_sz = (size_t)V * kPanel * kPanel;
   if (!ensure(w, B_AOP, sizeof(float) * 2 * aop_sz, s, true)) return "out of device memory";
   if (!ensure(w, B_BOP, sizeof(float) * 2 * bop_sz, s, true)) return "out of device memory";
   if (!ensure(w, B_TC, sizeof(f2) * 2 * tc_sz, s)) return "out of device memory";
@@ -1153,8 +1216,9 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
   cudaStream_t s2 = w.side;
   // The row-split padding [2n, ldF) is never read (the tensor maps stop at 2n).
   float* Fr = buf<float>(w, B_F);    // TF32-rounded S'_i of every layer (solve operand)
-  float* F = buf<float>(w, B_FW);    // fp32 working layers (ping-pong)
+  float* F = buf<float>(w, B_FW);    // fp32 working layers (ping-pong per virtual node)
   f2* Cf = buf<f2>(w, B_CF);
+  const int K = d.K, L0 = K, L1 = d.nz - 1 - K;   // middle layer, chain lengths
   // The launches of the factorisation (both streams).  Without kernel timing
   // they are captured once into a CUDA graph (node priorities kept, so the
   // lookahead chain still goes first) and replayed while the shape, the
@@ -1168,23 +1232,24 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
     f2* Pv[2] = {buf<f2>(w, B_PINV), buf<f2>(w, B_PINV) + pinv_sz};
     CUtensorMap tmA[2], tmB[2];
     for (int q = 0; q < 2; ++q) {
-      if (!make_map(&tmA[q], Aop[q], 2 * kPanel, (long long)Ne * d.n, 2 * kPanel, 128)) return "tensor map (Aop) rejected";
-      if (!make_map(&tmB[q], Bop[q], 2 * kPanel, (long long)Ne * d.nblk64 * 128, 2 * kPanel, 128))
+      if (!make_map(&tmA[q], Aop[q], 2 * kPanel, (long long)V * d.n, 2 * kPanel, 128)) return "tensor map (Aop) rejected";
+      if (!make_map(&tmB[q], Bop[q], 2 * kPanel, (long long)V * d.nblk64 * 128, 2 * kPanel, 128))
         return "tensor map (Bop) rejected";
     }
     const long long sF = 2LL * d.n * d.ldF;
     const long long sFr = (long long)d.nz * d.n * d.ldF;
     const int npan = d.nblk64;
-    auto panel = [&](cudaStream_t st, int layer, int kp) {
+    // one panel step of the virtual nodes 0 .. nv-1 (all of them work on plane ch.wplane)
+    auto panel = [&](cudaStream_t st, const Chains& ch, int nv, int kp) {
       const int k0 = kp * kPanel, bw = std::min(kPanel, d.n - k0), q = kp & 1;
       prof::begin(st, prof::PINV);
-      prof::add_work(prof::PINV, 8.0 * kPanel * kPanel * kPanel * Ne);
-      k_mx_pinv<kPinvRpt><<<Ne, kPanel * (kPanel / kPinvRpt), 0, st>>>(d, layer, k0, bw, F, Pv[q], status);
+      prof::add_work(prof::PINV, 8.0 * kPanel * kPanel * kPanel * nv);
+      k_mx_pinv<kPinvRpt><<<nv, kPanel * (kPanel / kPinvRpt), 0, st>>>(d, ch.wplane, k0, bw, F, Pv[q], status);
       prof::end(st, prof::PINV);
       prof::begin(st, prof::PANEL_T);
-      prof::add_work(prof::PANEL_T, 8.0 * d.n * kPanel * kPanel * Ne);
-      k_mx_panel_T<<<dim3(cdiv(d.n, kRowsPerPanelCta), Ne), 256, 0, st>>>(d, layer, k0, bw, F, Pv[q], Aop[q], Bop[q],
-                                                                        Tc[q]);
+      prof::add_work(prof::PANEL_T, 8.0 * d.n * kPanel * kPanel * nv);
+      k_mx_panel_T<<<dim3(cdiv(d.n, kRowsPerPanelCta), nv), 256, 0, st>>>(d, ch.wplane, k0, bw, F, Pv[q], Aop[q],
+                                                                        Bop[q], Tc[q]);
       prof::end(st, prof::PANEL_T);
       prof::count_launch(2);
     };
@@ -1193,62 +1258,83 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
     const bool tma_rmw = d.n % 64 == 0;
     CUtensorMap mapF{}, mapFr{};
     if (tma_rmw) {
-      if (!make_map_3d(&mapF, F, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 2LL * d.n, d.n, 2LL * Ne, d.ldF,
+      if (!make_map_3d(&mapF, F, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 2LL * d.n, d.n, 2LL * V, d.ldF,
                        (long long)d.n * d.ldF, 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) ||
           !make_map_3d(&mapFr, Fr, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 2LL * d.n, d.n, (long long)Ne * d.nz, d.ldF,
                        (long long)d.n * d.ldF, 32, 128, CU_TENSOR_MAP_SWIZZLE_128B))
         return "tensor map (working layers) rejected";
     }
     // trailing update of panel kp over the column tiles [base, base + count) except `skip`
-    auto update = [&](int layer, int kp, int base, int count, int skip) -> cudaError_t {
+    auto update = [&](const Chains& ch, int nv, int kp, int base, int count, int skip) -> cudaError_t {
       const int k0 = kp * kPanel, bw = std::min(kPanel, d.n - k0), q = kp & 1;
       const bool last = kp == npan - 1;
       tc::Geom geo{0, d.n, 0, d.nblk64 * 128, (2 * kPanel) / tc::kBlockK, base, skip};
       const int cls = base > 0 ? prof::SWEEP_NARROW : prof::SWEEP_GEMM;   // the narrow update starts at tile kp+1
       prof::begin(s, cls);
-      prof::add_work(cls, 8.0 * d.n * (64.0 * count) * bw * Ne);
+      prof::add_work(cls, 8.0 * d.n * (64.0 * count) * bw * nv);
       cudaError_t err;
+      const dim3 grid(count, cdiv(d.n, 128), nv);
       if (tma_rmw) {
-        SweepEpiTma epi{mapF, mapFr, layer & 1, layer, d.nz, d.n, k0, bw, last ? 1 : 0, Tc[q], Pv[q]};
+        SweepEpiTma epi{mapF, mapFr, ch.wplane, ch, d.nz, d.n, k0, bw, last ? 1 : 0, Tc[q], Pv[q]};
         // the narrow update (one column tile, few CTAs, on the critical path)
         // pipelines its K-blocks; the wide one keeps two CTAs per SM instead
-        err = count == 1 ? launch_tc<128, 4>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status)
-                         : launch_tc<128, kWideStages>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi,
-                                                       status);
+        err = count == 1 ? launch_tc<128, 4>(s, grid, tmA[q], tmB[q], geo, epi, status)
+                         : launch_tc<128, kWideStages>(s, grid, tmA[q], tmB[q], geo, epi, status);
       } else {
-        SweepEpi epi{F + (long long)(layer & 1) * d.n * d.ldF, sF, last ? Fr + (long long)layer * d.n * d.ldF : nullptr,
-                     sFr, d.ldF, d.n, k0, bw, Tc[q], Pv[q]};
-        err = launch_tc<128, 2>(s, dim3(count, cdiv(d.n, 128), Ne), tmA[q], tmB[q], geo, epi, status);
+        SweepEpi epi{F + (long long)ch.wplane * d.n * d.ldF, sF, last ? Fr : nullptr, sFr, d.ldF, d.n, k0, bw,
+                     Tc[q], Pv[q], ch};
+        err = launch_tc<128, 2>(s, grid, tmA[q], tmB[q], geo, epi, status);
       }
       prof::end(s, cls);
       prof::count_launch();
       return err;
     };
-    for (int layer = 0; layer < d.nz; ++layer) {
-      prof::begin(s, prof::SCHUR);
-      prof::add_work(prof::SCHUR, (layer > 0 ? 144.0 : 0.0) * d.n * (double)d.n * Ne);
-      if (layer > 0)
-        k_mx_schur1<<<dim3(cdiv(d.n, 256), d.n, Ne), 256, 0, s>>>(d, layer, Cf, F, buf<float>(w, B_T1));
-      k_mx_schur2<<<dim3(cdiv(d.n, 256), d.n, Ne), 256, 0, s>>>(d, layer, Cf, buf<float>(w, B_T1), F);
-      prof::end(s, prof::SCHUR);
-      prof::count_launch(layer > 0 ? 2 : 1);
-      panel(s, layer, 0);
+    // the block sweep of the complements of the nv virtual nodes (plane ch.wplane)
+    auto sweep = [&](const Chains& ch, int nv) -> const char* {
+      panel(s, ch, nv, 0);
       for (int kp = 0; kp < npan; ++kp) {
         if (kp + 1 < npan) {
           // narrow update: the next panel's columns first ...
-          if (update(layer, kp, kp + 1, 1, -1) != cudaSuccess) return "tcgen05 sweep-update launch failed";
+          if (update(ch, nv, kp, kp + 1, 1, -1) != cudaSuccess) return "tcgen05 sweep-update launch failed";
           cudaEventRecord(w.ev_narrow, s);
           // ... so its inversion and product overlap the wide update
           cudaStreamWaitEvent(s2, w.ev_narrow, 0);
-          panel(s2, layer, kp + 1);
+          panel(s2, ch, nv, kp + 1);
           cudaEventRecord(w.ev_side, s2);
-          if (npan > 1 && update(layer, kp, 0, npan - 1, kp + 1) != cudaSuccess)
+          if (npan > 1 && update(ch, nv, kp, 0, npan - 1, kp + 1) != cudaSuccess)
             return "tcgen05 sweep-update launch failed";
           cudaStreamWaitEvent(s, w.ev_side, 0);
         } else {
-          if (update(layer, kp, 0, npan, -1) != cudaSuccess) return "tcgen05 sweep-update launch failed";
+          if (update(ch, nv, kp, 0, npan, -1) != cudaSuccess) return "tcgen05 sweep-update launch failed";
         }
       }
+      return nullptr;
+    };
+    const dim3 sgrid(cdiv(d.n, 256), d.n);
+    // both chains, one layer each per step
+    for (int t = 0; t < L0; ++t) {
+      const Chains ch{Ne, {t, d.nz - 1 - t}, {(t + 1) & 1, (t + 1) & 1}, t & 1};
+      const int nv = t < L1 ? V : Ne;
+      prof::begin(s, prof::SCHUR);
+      prof::add_work(prof::SCHUR, (t > 0 ? 144.0 : 0.0) * d.n * (double)d.n * nv);
+      if (t > 0)
+        k_mx_schur1<<<dim3(sgrid.x, sgrid.y, nv), 256, 0, s>>>(d, ch, Cf, F, buf<float>(w, B_T1));
+      k_mx_schur2<<<dim3(sgrid.x, sgrid.y, nv), 256, 0, s>>>(d, ch, t > 0, 0, 0, Cf, buf<float>(w, B_T1), F);
+      prof::end(s, prof::SCHUR);
+      prof::count_launch(t > 0 ? 2 : 1);
+      if (const char* m = sweep(ch, nv)) return m;
+    }
+    // the middle layer with both chains' last complements
+    {
+      const Chains ch{Ne, {K, K}, {(L0 + 1) & 1, (L1 + 1) & 1}, L0 & 1};
+      prof::begin(s, prof::SCHUR);
+      prof::add_work(prof::SCHUR, (L0 > 0 ? 144.0 : 0.0) * (L1 > 0 ? 2.0 : 1.0) * d.n * (double)d.n * Ne);
+      if (L0 > 0)
+        k_mx_schur1<<<dim3(sgrid.x, sgrid.y, L1 > 0 ? V : Ne), 256, 0, s>>>(d, ch, Cf, F, buf<float>(w, B_T1));
+      k_mx_schur2<<<dim3(sgrid.x, sgrid.y, Ne), 256, 0, s>>>(d, ch, L0 > 0, 1, L1 > 0, Cf, buf<float>(w, B_T1), F);
+      prof::end(s, prof::SCHUR);
+      prof::count_launch(L0 > 0 ? 2 : 1);
+      if (const char* m = sweep(ch, Ne)) return m;
     }
     return nullptr;
   };
@@ -1318,6 +1404,10 @@ struct QuadOut {
   int first;
 };
 
+// One pair of sweeps of the two-ended elimination (see Chains): the forward
+// sweep runs up both chains (chain 0 from layer 0, chain 1 from layer nz-1)
+// to the middle layer K, whose solution x_K = -S'_K g_K starts the backward
+// sweep, which then runs out along both chains.  nl: the real nodes swept.
 template <int CB>
 const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const double* A27, const double* B27,
                          MixedWork& w, const double* Rreal, const f2* Rc, const NodeList& nl, const QuadOut& qo,
@@ -1326,62 +1416,87 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
   f2* Gc = buf<f2>(w, B_GC);
   f2* Tout = buf<f2>(w, B_TOUT);
   float* Bemb = buf<float>(w, B_BEMB);
+  const int Ne = d.Ne, V = 2 * Ne;
   CUtensorMap tmF, tmB;
-  if (!make_map(&tmF, F, 2 * d.n, (long long)d.Ne * d.nz * d.n, d.ldF, 128)) return "tensor map (factors) rejected";
-  if (!make_map(&tmB, Bemb, 2 * d.n, (long long)d.Ne * d.nblkCB * 2 * CB, d.ldB, 2 * CB))
+  if (!make_map(&tmF, F, 2 * d.n, (long long)Ne * d.nz * d.n, d.ldF, 128)) return "tensor map (factors) rejected";
+  if (!make_map(&tmB, Bemb, 2 * d.n, (long long)V * d.nblkCB * 2 * CB, d.ldB, 2 * CB))
     return "tensor map (rhs) rejected";
   const int nk = (2 * d.n + tc::kBlockK - 1) / tc::kBlockK;
   const f2* Cf = buf<f2>(w, B_CF);
-  const int nn = nl.count;
-  const dim3 cgrid(cdiv(d.n, 128), d.k, nn);
-  const dim3 ggrid(d.nblkCB, cdiv(d.n, 128), nn);
+  const int K = d.K, L0 = K, L1 = d.nz - 1 - K;
+  // virtual nodes of a step: the swept nodes on chain 0, and on chain 1 while it has layers
+  const NodeList one{nl.count, nl.mask};
+  const NodeList both{2 * nl.count, nl.mask | (nl.mask << Ne)};
   tc::Geom geo0{0, d.nz * d.n, 0, d.nblkCB * 2 * CB, nk};
-  geo0.node_mask = nl.mask;
+  geo0.split = Ne;
   // coupling work is counted in bytes: per entry the right-hand side and the
   // neighbouring solution (8 B each), g (8 B) and its embedded operand copy
   // (16 B), plus the 9 coefficients of each row
-  const double couple_fwd_bytes = (double)nn * d.n * ((double)d.k * 40.0 + 72.0);
-  const double couple_bwd_bytes = (double)nn * d.n * ((double)d.k * 32.0 + 72.0);
-  // forward sweep
-  prof::begin(s, prof::COUPLE);
-  prof::add_work(prof::COUPLE, couple_fwd_bytes);
-  k_mx_couple_fwd<<<cgrid, 128, 0, s>>>(d, 0, Cf, Rreal, Rc, Tout, Gc, Bemb, nl);
-  prof::end(s, prof::COUPLE);
-  for (int i = 1; i < d.nz; ++i) {
-    SolveEpi<CB> epi{Tout, (long long)d.n * d.k, d.n, d.n, d.k, 1.0f};
+  auto couple_bytes = [&](int nv, double per_entry) { return (double)nv * d.n * ((double)d.k * per_entry + 72.0); };
+  auto gemm = [&](const NodeList& vl, int layer0, int layer1, SolveEpi<CB> epi) -> bool {
     tc::Geom geo = geo0;
-    geo.a_row0 = (i - 1) * d.n;
+    geo.node_mask = vl.mask;
+    geo.a_row0 = layer0 * d.n;
+    geo.a_row0_hi = layer1 * d.n;
     prof::begin(s, prof::SOLVE_GEMM);
-    prof::add_work(prof::SOLVE_GEMM, 8.0 * d.n * (double)d.n * d.k * nn);
-    if (launch_tc<2 * CB, 4>(s, ggrid, tmF, tmB, geo, epi, status) != cudaSuccess) return "tcgen05 solve launch failed";
+    prof::add_work(prof::SOLVE_GEMM, 8.0 * d.n * (double)d.n * d.k * vl.count);
+    const bool ok =
+        launch_tc<2 * CB, 4>(s, dim3(d.nblkCB, cdiv(d.n, 128), vl.count), tmF, tmB, geo, epi, status) == cudaSuccess;
     prof::end(s, prof::SOLVE_GEMM);
-    prof::begin(s, prof::COUPLE);
-    prof::add_work(prof::COUPLE, couple_fwd_bytes);
-    k_mx_couple_fwd<<<cgrid, 128, 0, s>>>(d, i, Cf, Rreal, Rc, Tout, Gc, Bemb, nl);
-    prof::end(s, prof::COUPLE);
-  }
-  // backward sweep: x_i overwrites g_i
-  for (int i = d.nz - 1; i >= 0; --i) {
-    prof::begin(s, prof::COUPLE);
-    prof::add_work(prof::COUPLE, couple_bwd_bytes);
-    k_mx_couple_bwd<<<cgrid, 128, 0, s>>>(d, i, Cf, Gc, Bemb, nl);
-    prof::end(s, prof::COUPLE);
-    SolveEpi<CB> epi{Gc + (long long)i * d.n, d.N * d.k, d.N, d.n, d.k, -1.0f};
+    return ok;
+  };
+  // backward products x = -S' s into the nodes' solution columns (and the
+  // quadrature shares)
+  auto back_epi = [&](const Chains& ch) {
+    SolveEpi<CB> epi{Gc, d.N * d.k, d.N, d.n, d.k, -1.0f};
+    epi.node_rows = 1;
+    epi.ch = ch;
     if (qo.qp) {
-      epi.qp = qo.qp + (long long)i * d.n;
+      epi.qp = qo.qp;
       epi.sQ = d.N * d.k;
       epi.ldq = d.N;
       epi.coef = qo.coef;
       epi.qfirst = qo.first;
     }
-    tc::Geom geo = geo0;
-    geo.a_row0 = i * d.n;
-    prof::begin(s, prof::SOLVE_GEMM);
-    prof::add_work(prof::SOLVE_GEMM, 8.0 * d.n * (double)d.n * d.k * nn);
-    if (launch_tc<2 * CB, 4>(s, ggrid, tmF, tmB, geo, epi, status) != cudaSuccess) return "tcgen05 solve launch failed";
-    prof::end(s, prof::SOLVE_GEMM);
+    return epi;
+  };
+  int launches = 0;
+  // forward sweep: g on each chain's layer, then t = S' g for its next layer
+  for (int t = 0; t < L0; ++t) {
+    const Chains ch{Ne, {t, d.nz - 1 - t}, {0, 0}, 0};
+    const NodeList& vl = t < L1 ? both : one;
+    prof::begin(s, prof::COUPLE);
+    prof::add_work(prof::COUPLE, couple_bytes(vl.count, 40.0));
+    k_mx_couple_fwd<<<dim3(cdiv(d.n, 128), d.k, vl.count), 128, 0, s>>>(d, ch, t > 0, 0, 0, Cf, Rreal, Rc, Tout, Gc,
+                                                                         Bemb, vl);
+    prof::end(s, prof::COUPLE);
+    SolveEpi<CB> epi{Tout, (long long)d.n * d.k, d.n, d.n, d.k, 1.0f};
+    if (!gemm(vl, t, d.nz - 1 - t, epi)) return "tcgen05 solve launch failed";
+    launches += 2;
   }
-  prof::count_launch(4 * d.nz - 2 + 2);
+  // the middle layer: both chains' products meet, x_K = -S'_K g_K
+  {
+    const Chains ch{Ne, {K, K}, {0, 0}, 0};
+    prof::begin(s, prof::COUPLE);
+    prof::add_work(prof::COUPLE, couple_bytes(one.count, L1 > 0 ? 48.0 : 40.0));
+    k_mx_couple_fwd<<<dim3(cdiv(d.n, 128), d.k, one.count), 128, 0, s>>>(d, ch, L0 > 0, 1, L1 > 0, Cf, Rreal, Rc,
+                                                                          Tout, Gc, Bemb, one);
+    prof::end(s, prof::COUPLE);
+    if (!gemm(one, K, K, back_epi(ch))) return "tcgen05 solve launch failed";
+    launches += 2;
+  }
+  // backward sweep out along both chains: x overwrites g
+  for (int u = 0; u < L0; ++u) {
+    const Chains ch{Ne, {K - 1 - u, K + 1 + u}, {0, 0}, 0};
+    const NodeList& vl = u < L1 ? both : one;
+    prof::begin(s, prof::COUPLE);
+    prof::add_work(prof::COUPLE, couple_bytes(vl.count, 32.0));
+    k_mx_couple_bwd<<<dim3(cdiv(d.n, 128), d.k, vl.count), 128, 0, s>>>(d, ch, Cf, Gc, Bemb, vl);
+    prof::end(s, prof::COUPLE);
+    if (!gemm(vl, K - 1 - u, K + 1 + u, back_epi(ch))) return "tcgen05 solve launch failed";
+    launches += 2;
+  }
+  prof::count_launch(launches);
   return nullptr;
 }
 
@@ -1490,7 +1605,7 @@ const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const doubl
     if (!gc.exec[g] || std::memcmp(gc.key[g], key, sizeof(key)) != 0) continue;
     gc.used[g] = gc.clock;
     if (cudaGraphLaunch(gc.exec[g], s) != cudaSuccess) return "sweep graph launch failed";
-    prof::count_launch(4 * d.nz);
+    prof::count_launch(4 * d.K + 2);
     if (stats) ++stats->graph_sweeps;
     return nullptr;
   }
@@ -1543,10 +1658,11 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
   const long long sG = d.N * k;
   if (!ensure(w, B_GC, sizeof(f2) * (size_t)Ne * sG, s)) return "out of device memory (node sweeps)";
   if (!ensure(w, B_RC, sizeof(f2) * (size_t)Ne * sG, s)) return "out of device memory (residuals)";
-  if (!ensure(w, B_TOUT, sizeof(f2) * (size_t)Ne * d.n * k, s)) return "out of device memory";
+  // products and embedded right-hand sides are per virtual node (two chains)
+  if (!ensure(w, B_TOUT, sizeof(f2) * (size_t)2 * Ne * d.n * k, s)) return "out of device memory";
   // embedded RHS operand, sized for every tile width (rows of columns >= k
   // stay zero; re-zeroed when the column count changes)
-  const size_t bemb = sizeof(float) * (size_t)Ne * (2 * (size_t)k + 128) * d.ldB;
+  const size_t bemb = sizeof(float) * (size_t)2 * Ne * (2 * (size_t)k + 128) * d.ldB;
   const bool shape_changed = w.sizes[B_BEMB] < bemb || w.bemb_k != k;
   if (!ensure(w, B_BEMB, bemb, s, shape_changed)) return "out of device memory";
   w.bemb_k = k;

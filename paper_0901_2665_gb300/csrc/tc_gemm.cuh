@@ -198,6 +198,11 @@ struct Geom {
   int tn_base = 0;    // first n tile of the launch
   int tn_skip = -1;   // n tile left out (the grid's x covers the others), -1 = none
   unsigned long long node_mask = 0;   // != 0: the batch index of CTA z is the z-th set bit (a compacted batch)
+  // split > 0: batch indices b >= split take their A tile at row
+  // a_row0_hi + (b - split) a_batch (a second set of A rows, e.g. the
+  // other end of a two-ended elimination)
+  int split = 0;
+  int a_row0_hi = 0;
 };
 
 // Position of the z-th set bit (z from 0) of a 64-bit mask.
@@ -301,7 +306,8 @@ __global__ void __launch_bounds__(kThreads)
 
   if (warp == 0) {
     if (lane == 0) {
-      const int ay = geo.a_row0 + e * geo.a_batch + tm * kBlockM;
+      const bool hi = geo.split > 0 && e >= geo.split;
+      const int ay = (hi ? geo.a_row0_hi + (e - geo.split) * geo.a_batch : geo.a_row0 + e * geo.a_batch) + tm * kBlockM;
       const int by = geo.b_row0 + e * geo.b_batch + tn * BN;
       int issued = 0;
       for (int kb = 0; kb < geo.nk; ++kb) {
