@@ -137,6 +137,9 @@ typedef struct {
                                (0 with options.profile, which times the kernels one by one) */
   int inner_iters_max;      /* COCG: most iterations of one loop's node solves */
   double inner_rel_max;     /* COCG: largest final relative residual of a column */
+  int loop_graphs;          /* 1: the refinement loops ran as one CUDA graph with device-side loop
+                               conditions (see feast_solve); t_rr_ms is then -1 and t_solve_ms
+                               covers the whole loop */
 } feast_info;
 
 /* Fills *opt with the defaults listed above. */

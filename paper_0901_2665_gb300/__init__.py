@@ -81,7 +81,7 @@ class feast_info(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong * KERNEL_CLASS_SLOTS),
                 ("kernel_flops", ctypes.c_double * KERNEL_CLASS_SLOTS),
                 ("sweep_graphs", ctypes.c_longlong), ("inner_iters_max", ctypes.c_int),
-                ("inner_rel_max", ctypes.c_double)]
+                ("inner_rel_max", ctypes.c_double), ("loop_graphs", ctypes.c_int)]
 
 
 KERNEL_CLASSES = ["sweep_gemm", "solve_gemm", "panel_inverse", "panel_product", "schur", "solve_coupling",

@@ -157,7 +157,8 @@ struct feast_handle {
   DevBuf F, T1, T, L, Pinv, G, Tmp, Zd, coefd, status, cgw;
   // loop buffers
   DevBuf RHS, Q, Qp, AQf, BQf, Xb, Yb, Xout, part, AQ, BQ, eps, Phi, work, norms, normA, lam_d, perm_d, resid_d,
-      residp_d;
+      residp_d, loopst;
+  long long loop_graph_solves = 0;   // solves whose loop ran as one CUDA graph
   MixedWork mixed;
   // Hermitian path (complex buffers)
   DevBuf hF, hG, hTmp, hRHS, hQ, hAQf, hBQf, hX, hY, hXout, hPart, hAQ, hBQ, hPhi, hWork, hZ, hCoef, hEps;
@@ -167,7 +168,7 @@ struct feast_handle {
     for (DevBuf* b : {&opA, &opB, &F, &T1, &T, &L, &Pinv, &G, &Tmp, &Zd, &coefd, &status, &cgw, &RHS, &Q, &Qp, &AQf,
                       &BQf,
                       &Xb, &Yb, &Xout, &part, &AQ, &BQ, &eps, &Phi, &work, &norms, &normA, &lam_d, &perm_d,
-                      &resid_d, &residp_d, &hF, &hG, &hTmp, &hRHS, &hQ, &hAQf, &hBQf, &hX, &hY, &hXout, &hPart, &hAQ,
+                      &resid_d, &residp_d, &loopst, &hF, &hG, &hTmp, &hRHS, &hQ, &hAQf, &hBQf, &hX, &hY, &hXout, &hPart, &hAQ,
                       &hBQ, &hPhi, &hWork, &hZ, &hCoef, &hEps})
       b->release();
     mixed.release();
@@ -334,8 +335,9 @@ void upload_contour(feast_handle* h, const Contour& ct) {
 
 // Rayleigh-Ritz on Q (device, N x M0): eps (device, M0), X (device, N x M0).
 void rayleigh_ritz_dev(feast_handle* h, const OpView& op, const double* Q, int M0, double* eps, double* X,
-                       double* AQout, double* BQout) {
+                       double* AQout, double* BQout, cudaStream_t st = nullptr) {
   const long long N = op.g.N();
+  cudaStream_t s = st ? st : h->stream;
   h->AQf.ensure(sizeof(double) * N * M0, "AQ full");
   h->BQf.ensure(sizeof(double) * N * M0, "BQ full");
   h->part.ensure(sizeof(double) * gram_partial_elems(N, M0, M0), "gram partials");
@@ -343,14 +345,14 @@ void rayleigh_ritz_dev(feast_handle* h, const OpView& op, const double* Q, int M
   h->BQ.ensure(sizeof(double) * M0 * M0, "B_Q");
   h->Phi.ensure(sizeof(double) * M0 * M0, "Phi");
   h->work.ensure(sizeof(double) * 3 * M0 * M0, "eig work");
-  stencil_apply(h->stream, op.g, op.A27, Q, N, h->AQf.as<double>(), N, M0);
-  stencil_apply(h->stream, op.g, op.B27, Q, N, h->BQf.as<double>(), N, M0);
+  stencil_apply(s, op.g, op.A27, Q, N, h->AQf.as<double>(), N, M0);
+  stencil_apply(s, op.g, op.B27, Q, N, h->BQf.as<double>(), N, M0);
   double* AQ = AQout ? AQout : h->AQ.as<double>();
   double* BQ = BQout ? BQout : h->BQ.as<double>();
-  gram(h->stream, N, M0, M0, Q, h->AQf.as<double>(), h->part.as<double>(), AQ, true);   // Q^T (A Q), A symmetric
-  gram(h->stream, N, M0, M0, Q, h->BQf.as<double>(), h->part.as<double>(), BQ, true);
-  reduced_eig(h->stream, M0, AQ, BQ, eps, h->Phi.as<double>(), h->work.as<double>(), h->status.as<int>());
-  dgemm_tall(h->stream, N, M0, M0, Q, h->Phi.as<double>(), X);
+  gram(s, N, M0, M0, Q, h->AQf.as<double>(), h->part.as<double>(), AQ, true);   // Q^T (A Q), A symmetric
+  gram(s, N, M0, M0, Q, h->BQf.as<double>(), h->part.as<double>(), BQ, true);
+  reduced_eig(s, M0, AQ, BQ, eps, h->Phi.as<double>(), h->work.as<double>(), h->status.as<int>());
+  dgemm_tall(s, N, M0, M0, Q, h->Phi.as<double>(), X);
 }
 
 void residuals_dev(feast_handle* h, const OpView& op, const double* lam, const double* X, int k, double* resid,
@@ -599,15 +601,89 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
     bool converged = false;
     int count = 0, loop = 0;
     double t_solve = 0, t_rr = 0;
-    for (loop = 1; loop <= h->opt.max_loops; ++loop) {
+    const bool early = h->opt.ir_early && !Y0 && prec == FEAST_PREC_MIXED;
+    // ---- the loop as one CUDA graph with device-side conditions (mixed
+    // precision, no kernel timing): steps 2-6 and every refinement decision
+    // stay on the device, and the host reads the final state once
+    bool device_loop = false;
+    if (prec == FEAST_PREC_MIXED && !h->opt.profile && h->mixed.use_graphs &&
+        h->opt.inner_solver == FEAST_INNER_DIRECT) {
+      h->Qp.ensure(sizeof(double) * (size_t)Ne * N * M0, "quadrature shares");
+      h->loopst.ensure(sizeof(LoopState), "loop state");
+      // Rayleigh-Ritz work space, sized before a capture can start
+      h->AQf.ensure(sizeof(double) * N * M0, "AQ full");
+      h->BQf.ensure(sizeof(double) * N * M0, "BQ full");
+      h->part.ensure(sizeof(double) * gram_partial_elems(N, M0, M0), "gram partials");
+      h->AQ.ensure(sizeof(double) * M0 * M0, "A_Q");
+      h->BQ.ensure(sizeof(double) * M0 * M0, "B_Q");
+      h->Phi.ensure(sizeof(double) * M0 * M0, "Phi");
+      h->work.ensure(sizeof(double) * 3 * M0 * M0, "eig work");
+      const LoopParams lp{lmin, lmax, tol, h->opt.ir_tol, early ? 1 : 0, h->opt.max_loops, h->opt.ir_max, M0};
+      LoopHooks hooks;
+      hooks.rhs = [&](cudaStream_t st) {
+        stencil_apply(st, v.g, v.B27, h->Yb.as<double>(), N, h->RHS.as<double>(), N, M0);
+      };
+      hooks.quad_rr = [&](cudaStream_t st) {
+        quadrature_sum(st, N, M0, Ne, h->Qp.as<double>(), N * M0, h->Q.as<double>());
+        rayleigh_ritz_dev(h, v, h->Q.as<double>(), M0, h->eps.as<double>(), h->Xb.as<double>(), nullptr, nullptr, st);
+      };
+      hooks.next_y = [&](cudaStream_t st) { cudaMemcpyAsync(h->Yb.p, h->Xb.p, blk, cudaMemcpyDeviceToDevice, st); };
+      auto bits = [](double x) {
+        unsigned long long u;
+        std::memcpy(&u, &x, sizeof(u));
+        return u;
+      };
+      auto ptr = [](const void* q) { return (unsigned long long)(uintptr_t)q; };
+      unsigned long long key[kLoopKey] = {
+          (unsigned long long)v.g.nx | ((unsigned long long)v.g.ny << 20) | ((unsigned long long)v.g.nz << 40),
+          (unsigned long long)M0 | ((unsigned long long)Ne << 20), bits(lmin), bits(lmax), bits(tol),
+          bits(h->opt.ir_tol),
+          (unsigned long long)lp.early | ((unsigned long long)lp.max_loops << 8) | ((unsigned long long)lp.ir_max << 24),
+          ptr(v.A27), ptr(v.B27), ptr(h->Zd.p), ptr(h->coefd.p), ptr(h->status.p), ptr(h->RHS.p), ptr(h->Q.p),
+          ptr(h->Qp.p), ptr(h->Xb.p), ptr(h->Yb.p), ptr(h->eps.p), ptr(h->AQf.p), ptr(h->BQf.p), ptr(h->part.p),
+          ptr(h->AQ.p), ptr(h->BQ.p), ptr(h->Phi.p), ptr(h->work.p), ptr(h->loopst.p), ptr(s), 3ULL};
+      for (int i = 0; i < 16; ++i) key[28 + i] = ptr(h->mixed.bufs[i]);
+      ck(cudaEventRecord(h->ev[2], s), "event");
+      const char* msg = mixed_loop(s, v.g, Ne, h->Zd.as<cplx>(), v.A27, v.B27, h->mixed, h->RHS.as<double>(),
+                                   h->Qp.as<double>(), h->coefd.as<cplx>(), M0, lp, h->eps.as<double>(),
+                                   h->loopst.as<LoopState>(), hooks, key, h->status.as<int>());
+      if (msg && msg != kNotCaptured) fail(FEAST_ERR_CUDA, msg);
+      if (!msg) {
+        device_loop = true;
+        ck(cudaEventRecord(h->ev[4], s), "event");
+        LoopState ls{};
+        ck(cudaMemcpyAsync(&ls, h->loopst.p, sizeof(LoopState), cudaMemcpyDeviceToHost, s), "loop state");
+        ck(cudaMemcpyAsync(eps.data(), h->eps.p, sizeof(double) * M0, cudaMemcpyDeviceToHost, s), "eps");
+        check_status(h);
+        if (ls.fail == 1) fail(FEAST_ERR_CUDA, "iterative refinement did not reach the tolerance");
+        if (ls.fail == 2) fail(FEAST_ERR_CUDA, "non-finite residual in the refinement");
+        loop = ls.loop;
+        count = ls.count;
+        converged = ls.converged != 0;
+        for (int i = 0; i < std::min(loop, 64); ++i) {
+          h->info.trace[i] = ls.trace_hist[i];
+          h->info.rel_change[i] = ls.change_hist[i];
+        }
+        h->info.ir_steps_max = ls.ir_steps_max;
+        h->info.ir_resid_max = ls.ir_resid_max;
+        t_solve = elapsed(h->ev[2], h->ev[4]);   // the whole loop: node solves and Rayleigh-Ritz
+        t_rr = -1.0;
+        h->info.loop_graphs = 1;
+        // the kernels the graph ran: its loop bodies and refinement steps
+        prof::count_launch((int)(1 + (long long)loop * h->mixed.loop_outer_launches +
+                                 (long long)ls.ir_steps_total * h->mixed.loop_inner_launches));
+        ++h->loop_graph_solves;
+      }
+    }
+    for (loop = device_loop ? loop : 1; !device_loop && loop <= h->opt.max_loops; ++loop) {
+
       ck(cudaEventRecord(h->ev[2], s), "event");
       // step 2: RHS = B Y, node solves, quadrature (Eq. 15)
       stencil_apply(s, v.g, v.B27, h->Yb.as<double>(), N, h->RHS.as<double>(), N, M0);
       // refinement target of this loop: loosened in loops 1 and 2 (their subspace
       // is still far from converged, so their solves need less accuracy)
       double ir_loop = h->opt.ir_tol;
-      if (h->opt.ir_early && !Y0 && prec == FEAST_PREC_MIXED && loop <= 2)
-        ir_loop = std::max(ir_loop, loop == 1 ? 1e-5 : 1e-8);
+      if (early && loop <= 2) ir_loop = std::max(ir_loop, loop == 1 ? 1e-5 : 1e-8);
       const bool exact_loop = ir_loop <= h->opt.ir_tol;
       node_solves_and_quadrature(h, v, Ne, prec, h->RHS.as<double>(), M0, ir_loop, h->Q.as<double>());
       ck(cudaEventRecord(h->ev[3], s), "event");
@@ -636,7 +712,9 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
         if (loop - 1 < 64) h->info.rel_change[loop - 1] = change;
         if (count == prev_count && change <= tol && exact_loop) converged = true;
       }
-      std::swap(h->Xb, h->Yb);  // Y = X: the next right-hand side is B X
+      // Y = X: the next right-hand side is B X (a copy, so that the loop's
+      // buffers keep their addresses for the captured form above)
+      ck(cudaMemcpyAsync(h->Yb.p, h->Xb.p, blk, cudaMemcpyDeviceToDevice, s), "Y = X");
       if (converged) break;
       prev_trace = trace;
       prev_count = count;

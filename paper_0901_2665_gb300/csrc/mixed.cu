@@ -709,11 +709,13 @@ __device__ __forceinline__ void write_emb(const Dims& d, float* Bemb, int e, int
 __global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, Chains ch, int has_prev, int middle, int has_prev1,
                                                        const f2* __restrict__ Cf, const double* __restrict__ Rreal,
                                                        const f2* __restrict__ Rc, const f2* __restrict__ Tout,
-                                                       f2* __restrict__ Gc, float* __restrict__ Bemb, NodeList nl) {
+                                                       f2* __restrict__ Gc, float* __restrict__ Bemb, NodeList nl,
+                                                       const int* __restrict__ active) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y, v = tc::nth_set_bit(nl.mask, (int)blockIdx.z);
   if (p >= d.n) return;
   const int c = chain_of(ch, v), e = node_of(ch, v);
+  if (active && !active[e]) return;   // a node the device-side refinement left out
   const long long row = (long long)ch.layer[c] * d.n + p;
   const long long sG = d.N * d.k;
   f2 g = Rc ? Rc[e * sG + (long long)m * d.N + row] : f2{(float)Rreal[(long long)m * d.N + row], 0.f};
@@ -744,11 +746,12 @@ __global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, Chains ch, int ha
 // last layer of a one-ended elimination) takes s = g.
 __global__ void __launch_bounds__(128) k_mx_couple_bwd(Dims d, Chains ch, const f2* __restrict__ Cf,
                                                        const f2* __restrict__ Gc, float* __restrict__ Bemb,
-                                                       NodeList nl) {
+                                                       NodeList nl, const int* __restrict__ active) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y, v = tc::nth_set_bit(nl.mask, (int)blockIdx.z);
   if (p >= d.n) return;
   const int c = chain_of(ch, v), e = node_of(ch, v);
+  if (active && !active[e]) return;
   const int layer = ch.layer[c], next = c ? layer - 1 : layer + 1;
   const long long row = (long long)layer * d.n + p;
   const long long sG = d.N * d.k;
@@ -828,12 +831,14 @@ __global__ void __launch_bounds__(kResThreads) k_mx_residual(Dims d, const cplx*
                                                              const double* __restrict__ RHS,
                                                              const f2* __restrict__ Q, f2* __restrict__ Rc,
                                                              cplx* __restrict__ R64, double* __restrict__ partial,
-                                                             const int* __restrict__ active) {
+                                                             const int* __restrict__ active,
+                                                             const double* __restrict__ target) {
   extern __shared__ cplx rsm[];
   __shared__ double red[2][kResThreads];
   const int e = blockIdx.y;
   const int tid = threadIdx.x;
   if (!active[e]) return;   // block-uniform; the norm kernel ignores inactive nodes
+  if (target && !(*target < kFFirstTol)) return;   // a loose target: the double-float kernel runs instead
   const long long i0 = (long long)blockIdx.x * kResRows;
   const cplx z = Z[e];
   for (int t = tid; t < 27 * kResRows; t += kResThreads) {
@@ -938,13 +943,15 @@ __global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, cons
                                                                  const f2* __restrict__ delta, f2* __restrict__ Rc,
                                                                  cplx* __restrict__ R64, double* __restrict__ partial,
                                                                  const int* __restrict__ active,
-                                                                 const double* __restrict__ RHS) {
+                                                                 const double* __restrict__ RHS,
+                                                                 const double* __restrict__ target) {
   extern __shared__ float4 csm[];   // per (slot, row): Re c hi/lo, Im c hi/lo
   __shared__ double red[kResThreads];
   __shared__ double redb[kFirst ? kResThreads : 1];
   const int e = blockIdx.y;
   const int tid = threadIdx.x;
   if (!active[e]) return;
+  if (kFirst && target && !(*target >= kFFirstTol)) return;   // a tight target: the FP64 kernel runs instead
   const long long i0 = (long long)blockIdx.x * kResRows;
   const cplx z = Z[e];
   for (int t = tid; t < 27 * kResRows; t += kResThreads) {
@@ -1177,6 +1184,14 @@ void MixedWork::release() {
     sizes[i] = 0;
   }
   nz_factored = 0;
+  if (loop_graph) cudaGraphExecDestroy(loop_graph);
+  loop_graph = nullptr;
+  std::memset(loop_key, 0, sizeof(loop_key));
+  std::memset(loop_seen, 0, sizeof(loop_seen));
+  for (cudaStream_t* c : {&cap2, &cap3}) {
+    if (*c) cudaStreamDestroy(*c);
+    *c = nullptr;
+  }
   if (side) cudaStreamDestroy(side);
   if (ev_narrow) cudaEventDestroy(ev_narrow);
   if (ev_side) cudaEventDestroy(ev_side);
@@ -1411,7 +1426,7 @@ struct QuadOut {
 template <int CB>
 const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const double* A27, const double* B27,
                          MixedWork& w, const double* Rreal, const f2* Rc, const NodeList& nl, const QuadOut& qo,
-                         int* status) {
+                         int* status, const int* dactive) {
   float* F = buf<float>(w, B_F);
   f2* Gc = buf<f2>(w, B_GC);
   f2* Tout = buf<f2>(w, B_TOUT);
@@ -1429,6 +1444,7 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
   const NodeList both{2 * nl.count, nl.mask | (nl.mask << Ne)};
   tc::Geom geo0{0, d.nz * d.n, 0, d.nblkCB * 2 * CB, nk};
   geo0.split = Ne;
+  geo0.active = dactive;
   // coupling work is counted in bytes: per entry the right-hand side and the
   // neighbouring solution (8 B each), g (8 B) and its embedded operand copy
   // (16 B), plus the 9 coefficients of each row
@@ -1468,7 +1484,7 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     prof::begin(s, prof::COUPLE);
     prof::add_work(prof::COUPLE, couple_bytes(vl.count, 40.0));
     k_mx_couple_fwd<<<dim3(cdiv(d.n, 128), d.k, vl.count), 128, 0, s>>>(d, ch, t > 0, 0, 0, Cf, Rreal, Rc, Tout, Gc,
-                                                                         Bemb, vl);
+                                                                         Bemb, vl, dactive);
     prof::end(s, prof::COUPLE);
     SolveEpi<CB> epi{Tout, (long long)d.n * d.k, d.n, d.n, d.k, 1.0f};
     if (!gemm(vl, t, d.nz - 1 - t, epi)) return "tcgen05 solve launch failed";
@@ -1480,7 +1496,7 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     prof::begin(s, prof::COUPLE);
     prof::add_work(prof::COUPLE, couple_bytes(one.count, L1 > 0 ? 48.0 : 40.0));
     k_mx_couple_fwd<<<dim3(cdiv(d.n, 128), d.k, one.count), 128, 0, s>>>(d, ch, L0 > 0, 1, L1 > 0, Cf, Rreal, Rc,
-                                                                          Tout, Gc, Bemb, one);
+                                                                          Tout, Gc, Bemb, one, dactive);
     prof::end(s, prof::COUPLE);
     if (!gemm(one, K, K, back_epi(ch))) return "tcgen05 solve launch failed";
     launches += 2;
@@ -1491,7 +1507,7 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     const NodeList& vl = u < L1 ? both : one;
     prof::begin(s, prof::COUPLE);
     prof::add_work(prof::COUPLE, couple_bytes(vl.count, 32.0));
-    k_mx_couple_bwd<<<dim3(cdiv(d.n, 128), d.k, vl.count), 128, 0, s>>>(d, ch, Cf, Gc, Bemb, vl);
+    k_mx_couple_bwd<<<dim3(cdiv(d.n, 128), d.k, vl.count), 128, 0, s>>>(d, ch, Cf, Gc, Bemb, vl, dactive);
     prof::end(s, prof::COUPLE);
     if (!gemm(vl, K - 1 - u, K + 1 + u, back_epi(ch))) return "tcgen05 solve launch failed";
     launches += 2;
@@ -1564,12 +1580,12 @@ int tuned_cb(cudaStream_t s, const Dims& d, MixedWork& w, int* status) {
 
 const char* solve_direct(cudaStream_t s, const Dims& d, const cplx* Z, const double* A27, const double* B27,
                          MixedWork& w, const double* Rreal, const f2* Rc, const NodeList& nl, const QuadOut& qo,
-                         int* status) {
+                         int* status, const int* dactive = nullptr) {
   switch (d.CB) {
-    case 8: return solve_sweeps<8>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
-    case 16: return solve_sweeps<16>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
-    case 32: return solve_sweeps<32>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
-    default: return solve_sweeps<64>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
+    case 8: return solve_sweeps<8>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
+    case 16: return solve_sweeps<16>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
+    case 32: return solve_sweeps<32>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
+    default: return solve_sweeps<64>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
   }
 }
 
@@ -1711,7 +1727,7 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
         prof::add_work(prof::FF_RESIDUAL, 216.0 * (double)d.N * k * nact);
         k_mx_residual_inc<true><<<rgrid, kResThreads, kResSmem, s>>>(
             d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<cplx>(w, B_R64), buf<double>(w, B_PART),
-            buf<int>(w, B_ACTIVE), RHS);
+            buf<int>(w, B_ACTIVE), RHS, nullptr);
         prof::end(s, prof::FF_RESIDUAL);
       } else if (steps == 0) {
         // the first residual in FP64 from Q_e itself
@@ -1719,7 +1735,7 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
         prof::add_work(prof::RESIDUAL, 216.0 * (double)d.N * k * nact);   // 108 FP64 FMAs per complex entry
         k_mx_residual<<<rgrid, kResThreads, kResSmem, s>>>(d, Z, A27, B27, RHS, buf<f2>(w, B_GC), buf<f2>(w, B_RC),
                                                            buf<cplx>(w, B_R64), buf<double>(w, B_PART),
-                                                           buf<int>(w, B_ACTIVE));
+                                                           buf<int>(w, B_ACTIVE), nullptr);
         prof::end(s, prof::RESIDUAL);
       } else {
         // later residuals move by the last correction, in double-float
@@ -1727,7 +1743,7 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
         prof::add_work(prof::FF_RESIDUAL, 216.0 * (double)d.N * k * nact);
         k_mx_residual_inc<false><<<rgrid, kResThreads, kResSmem, s>>>(
             d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<cplx>(w, B_R64), buf<double>(w, B_PART),
-            buf<int>(w, B_ACTIVE), nullptr);
+            buf<int>(w, B_ACTIVE), nullptr, nullptr);
         prof::end(s, prof::FF_RESIDUAL);
       }
     }
@@ -1763,6 +1779,259 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
     stats->steps_max = std::max(stats->steps_max, steps);
     for (int e = 0; e < Ne; ++e) stats->resid_max = std::max(stats->resid_max, final_rel[e]);
   }
+  return nullptr;
+}
+
+// ------------------------------------------------------------------ device-side loop
+
+const char* const kNotCaptured = "not captured";
+
+namespace {
+
+// Start of a FEAST loop: the loop counter, the refinement target of the loop
+// (loosened in loops 1 and 2 from a random start, as the host-driven loop
+// does) and every node active again.
+__global__ void k_loop_begin(LoopState* st, double ir_tol, int early, int* active, int Ne) {
+  if (threadIdx.x == 0) {
+    const int L = ++st->loop;
+    double t = ir_tol;
+    if (early && L == 1) t = fmax(ir_tol, 1e-5);
+    if (early && L == 2) t = fmax(ir_tol, 1e-8);
+    st->ir_target = t;
+    st->ir_step = 0;
+  }
+  for (int e = threadIdx.x; e < Ne; e += blockDim.x) active[e] = 1;
+}
+
+// After a residual of the node solves: a node whose relative residual meets
+// the loop's target stops; the nested WHILE node runs another refinement
+// step while any node is left (at most ir_max steps; then the loop fails, as
+// does a non-finite residual).
+__global__ void k_ir_control(LoopState* st, const double* __restrict__ rel, int* active, int Ne, int ir_max,
+                             double ir_tol, cudaGraphConditionalHandle more) {
+  if (threadIdx.x != 0) return;
+  const double target = st->ir_target;
+  int any = 0;
+  for (int e = 0; e < Ne; ++e) {
+    if (!active[e]) continue;
+    const double r = rel[e];
+    if (!isfinite(r)) {
+      st->fail = 2;
+      active[e] = 0;
+      continue;
+    }
+    if (r <= target) {
+      active[e] = 0;
+      if (target <= ir_tol) st->ir_resid_max = fmax(st->ir_resid_max, r);
+    } else {
+      any = 1;
+    }
+  }
+  if (any && st->ir_step >= ir_max) {
+    st->fail = 1;
+    any = 0;
+  }
+  st->ir_steps_max = max(st->ir_steps_max, st->ir_step);
+  if (any) {
+    ++st->ir_step;
+    ++st->ir_steps_total;
+  }
+  cudaGraphSetConditional(more, any ? 1u : 0u);
+}
+
+// The trace test (Fig. 2 step 6) on the loop's Ritz values (ascending): the
+// in-interval count and trace, the relative change against the previous
+// loop; the outer WHILE node runs another loop unless the count is unchanged
+// and the change is <= tol in a loop refined to ir_tol, the loop cap is
+// reached, or a failure was recorded (refinement, or the device status word).
+__global__ void k_trace_control(LoopState* st, const double* __restrict__ eps, LoopParams lp, const int* status,
+                                cudaGraphConditionalHandle again) {
+  if (threadIdx.x != 0) return;
+  int count = 0;
+  double trace = 0.0, scale = 0.0;
+  for (int j = 0; j < lp.M0; ++j) {
+    const double x = eps[j];
+    if (x >= lp.lmin && x <= lp.lmax) {
+      ++count;
+      trace += x;
+      scale += fabs(x);
+    }
+  }
+  const int L = st->loop;
+  if (L - 1 < 64) {
+    st->trace_hist[L - 1] = trace;
+    st->change_hist[L - 1] = -1.0;
+  }
+  if (L > 1) {
+    const double change = scale > 0.0 ? fabs(trace - st->prev_trace) / scale : 0.0;
+    if (L - 1 < 64) st->change_hist[L - 1] = change;
+    if (count == st->prev_count && change <= lp.tol && st->ir_target <= lp.ir_tol) st->converged = 1;
+  }
+  st->count = count;
+  st->prev_trace = trace;
+  st->prev_count = count;
+  const int cont = !st->converged && L < lp.max_loops && !st->fail && *status == 0;
+  cudaGraphSetConditional(again, cont ? 1u : 0u);
+}
+
+__global__ void k_loop_init(LoopState* st) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    LoopState z{};
+    *st = z;
+  }
+}
+
+// Adds a WHILE node on `handle` (created on the graph being captured on s) at
+// the current end of that capture and returns the node's body graph; the
+// work captured on s afterwards follows the node.
+cudaError_t capture_while(cudaStream_t s, cudaGraphConditionalHandle handle, cudaGraph_t* body) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edata = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, &edata, &ndeps);
+  if (e != cudaSuccess) return e;
+  if (cst != cudaStreamCaptureStatusActive || !g) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = handle;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  e = cudaGraphAddNode(&node, g, deps, edata, ndeps, &p);
+  if (e != cudaSuccess) return e;
+  *body = p.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+cudaStream_t loop_stream(cudaStream_t& c) {
+  if (!c && cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c = nullptr;
+  }
+  return c;
+}
+
+}  // namespace
+
+const char* mixed_loop(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
+                       MixedWork& w, const double* RHS, double* Qp, const cplx* coef, int k, const LoopParams& lp,
+                       const double* eps, LoopState* st, const LoopHooks& hooks, const unsigned long long* key,
+                       int* status) {
+  if (w.loop_graph && std::memcmp(w.loop_key, key, sizeof(w.loop_key)) == 0) {
+    if (cudaGraphLaunch(w.loop_graph, s) != cudaSuccess) return "loop graph launch failed";
+    ++w.loop_replays;
+    return nullptr;
+  }
+  if (std::memcmp(w.loop_seen, key, sizeof(w.loop_seen)) != 0) {
+    std::memcpy(w.loop_seen, key, sizeof(w.loop_seen));   // first use of the key: the host-driven loop runs
+    return kNotCaptured;
+  }
+  // the buffers and the tile width of the shape were set by the host-driven run
+  Dims d = make_dims(g, Ne, k);
+  if (w.nz_factored != d.nz || w.ne_factored != Ne || !w.bufs[B_GC] || !w.bufs[B_R64]) return kNotCaptured;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    const long long tkey = ((long long)d.n << 32) ^ ((long long)d.k << 8) ^ d.Ne;
+    int cb = 0;
+    for (auto& kv : g_tuned)
+      if (kv.first == tkey) cb = kv.second;
+    if (!cb) return kNotCaptured;
+    d = make_dims(g, Ne, k, cb);
+  }
+  if (w.loop_graph) cudaGraphExecDestroy(w.loop_graph);
+  w.loop_graph = nullptr;
+  cudaStream_t cs = capture_stream(w), cs2 = loop_stream(w.cap2), cs3 = loop_stream(w.cap3);
+  if (!cs || !cs2 || !cs3) return kNotCaptured;
+  const dim3 rgrid(cdiv(d.N, kResRows), Ne);
+  const long long nblk = rgrid.x;
+  int* active = buf<int>(w, B_ACTIVE);
+  const NodeList all{Ne, Ne >= 64 ? ~0ULL : ((1ULL << Ne) - 1ULL)};
+  const long long launches0 = prof::launches();
+  cudaGraph_t graph = nullptr;
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess) return kNotCaptured;
+  const char* msg = nullptr;
+  cudaError_t ce = cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  bool c2 = false, c3 = false;
+  if (ce == cudaSuccess) {
+    k_loop_init<<<1, 1, 0, cs>>>(st);
+    // conditions: `again` (another FEAST loop) starts at 1 at every launch;
+    // `more` (another refinement step) is set before its node is reached
+    cudaGraphConditionalHandle again = 0, more = 0;
+    cudaGraph_t outer = nullptr, inner = nullptr;
+    ce = cudaGraphConditionalHandleCreate(&again, graph, 1u, cudaGraphCondAssignDefault);
+    if (ce == cudaSuccess) ce = capture_while(cs, again, &outer);
+    if (ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(&more, outer, 0u, cudaGraphCondAssignDefault);
+    if (ce == cudaSuccess) ce = cudaStreamBeginCaptureToGraph(cs2, outer, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    c2 = ce == cudaSuccess;
+    long long n_outer0 = 0, n_inner0 = 0, n_inner1 = 0;
+    if (c2) {
+      n_outer0 = prof::launches();
+      // one FEAST loop: B Y, the first solve of every node and its residual
+      k_loop_begin<<<1, 64, 0, cs2>>>(st, lp.ir_tol, lp.early, active, Ne);
+      prof::count_launch();
+      hooks.rhs(cs2);
+      msg = solve_direct(cs2, d, Z, A27, B27, w, RHS, nullptr, all, QuadOut{Qp, coef, 1}, status, active);
+      k_mx_residual<<<rgrid, kResThreads, kResSmem, cs2>>>(d, Z, A27, B27, RHS, buf<f2>(w, B_GC), buf<f2>(w, B_RC),
+                                                            buf<cplx>(w, B_R64), buf<double>(w, B_PART), active,
+                                                            &st->ir_target);
+      k_mx_residual_inc<true><<<rgrid, kResThreads, kResSmem, cs2>>>(
+          d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<cplx>(w, B_R64), buf<double>(w, B_PART), active,
+          RHS, &st->ir_target);
+      k_mx_resnorm<<<Ne, 256, 0, cs2>>>(Ne, nblk, buf<double>(w, B_PART), buf<double>(w, B_REL), active);
+      k_ir_control<<<1, 32, 0, cs2>>>(st, buf<double>(w, B_REL), active, Ne, lp.ir_max, lp.ir_tol, more);
+      prof::count_launch(4);
+      // the refinement steps: a nested WHILE node
+      ce = capture_while(cs2, more, &inner);
+      if (ce == cudaSuccess) ce = cudaStreamBeginCaptureToGraph(cs3, inner, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      c3 = ce == cudaSuccess;
+      if (c3 && !msg) {
+        n_inner0 = prof::launches();
+        msg = solve_direct(cs3, d, Z, A27, B27, w, nullptr, buf<f2>(w, B_RC), all, QuadOut{Qp, coef, 0}, status,
+                           active);
+        k_mx_residual_inc<false><<<rgrid, kResThreads, kResSmem, cs3>>>(
+            d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<cplx>(w, B_R64), buf<double>(w, B_PART), active,
+            nullptr, nullptr);
+        k_mx_resnorm<<<Ne, 256, 0, cs3>>>(Ne, nblk, buf<double>(w, B_PART), buf<double>(w, B_REL), active);
+        k_ir_control<<<1, 32, 0, cs3>>>(st, buf<double>(w, B_REL), active, Ne, lp.ir_max, lp.ir_tol, more);
+        prof::count_launch(3);
+        n_inner1 = prof::launches();
+      }
+      if (c3) {
+        cudaGraph_t done = nullptr;
+        const cudaError_t e3 = cudaStreamEndCapture(cs3, &done);
+        if (ce == cudaSuccess) ce = e3;
+      }
+      if (ce == cudaSuccess && !msg) {
+        hooks.quad_rr(cs2);
+        k_trace_control<<<1, 1, 0, cs2>>>(st, eps, lp, status, again);
+        prof::count_launch();
+        hooks.next_y(cs2);
+        w.loop_inner_launches = n_inner1 - n_inner0;
+        w.loop_outer_launches = prof::launches() - n_outer0 - w.loop_inner_launches;
+      }
+      cudaGraph_t done = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(cs2, &done);
+      if (ce == cudaSuccess) ce = e2;
+    }
+    cudaGraph_t done = nullptr;
+    const cudaError_t e1 = cudaStreamEndCapture(cs, &done);
+    if (ce == cudaSuccess) ce = e1;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (msg || ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    cudaGetLastError();
+    prof::count_launch((int)(launches0 - prof::launches()));   // nothing of the capture ran
+    if (msg) return msg;
+    return kNotCaptured;
+  }
+  cudaGraphDestroy(graph);
+  prof::count_launch((int)(launches0 - prof::launches()));
+  w.loop_graph = exec;
+  std::memcpy(w.loop_key, key, sizeof(w.loop_key));
+  if (cudaGraphLaunch(exec, s) != cudaSuccess) return "loop graph launch failed";
   return nullptr;
 }
 

@@ -3,6 +3,8 @@
 // every node solution (internal interface).
 #pragma once
 
+#include <functional>
+
 #include "common.cuh"
 
 namespace feast {
@@ -18,6 +20,7 @@ struct MixedSolveStats {
 // the captured launches depend on; least recently used entry replaced.  A
 // key is captured the second time it is seen (a capture and instantiation
 // cost more than one direct run, so one-off shapes stay direct).
+constexpr int kLoopKey = 48;
 constexpr int kSweepGraphs = 8;
 constexpr int kSweepKey = 20;
 struct SweepGraphCache {
@@ -27,6 +30,37 @@ struct SweepGraphCache {
   unsigned long long clock = 0;
   unsigned long long seen[kSweepGraphs][kSweepKey] = {};   // keys run once, directly
   int seen_next = 0;
+};
+
+// Device-side state of a solve whose refinement loops (Fig. 2 steps 2-6 and
+// the refinement of every node solve) run inside one CUDA graph with
+// device-side loop conditions.
+struct LoopState {
+  int loop;             // loops started (1-based once running)
+  int ir_step;          // refinement steps of the current loop's node solves
+  int count, prev_count;
+  int converged;        // trace test met in a loop refined to ir_tol
+  int fail;             // 1: refinement cap reached, 2: a non-finite residual
+  int ir_steps_max;
+  int ir_steps_total;   // refinement steps of all loops
+  double trace, prev_trace;
+  double ir_target;     // refinement target of the current loop
+  double ir_resid_max;  // largest relative residual at which a node solve run to ir_tol stopped
+  double trace_hist[64], change_hist[64];
+};
+
+// Fixed parameters of such a graph.
+struct LoopParams {
+  double lmin, lmax, tol, ir_tol;
+  int early;            // loosened refinement targets in loops 1 and 2
+  int max_loops, ir_max, M0;
+};
+
+// The steps of a loop outside the node solves, launched on the stream given.
+struct LoopHooks {
+  std::function<void(cudaStream_t)> rhs;       // RHS = B Y
+  std::function<void(cudaStream_t)> quad_rr;   // Q from the quadrature shares; Rayleigh-Ritz -> eps, X
+  std::function<void(cudaStream_t)> next_y;    // Y = X
 };
 
 struct MixedWork {
@@ -44,6 +78,12 @@ struct MixedWork {
   unsigned long long factor_seen[kSweepKey] = {};   // last factorisation run directly
   long long factor_launches = 0;               // kernels in it
   long long factor_replays = 0;
+  cudaStream_t cap2 = nullptr, cap3 = nullptr; // streams that capture the bodies of loop nodes
+  cudaGraphExec_t loop_graph = nullptr;        // the captured loop of a solve
+  unsigned long long loop_key[kLoopKey] = {};
+  unsigned long long loop_seen[kLoopKey] = {};
+  long long loop_replays = 0;
+  long long loop_outer_launches = 0, loop_inner_launches = 0;   // kernels of one loop body, one refinement step
   void release();
 };
 
@@ -57,5 +97,19 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
 const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
                         MixedWork& w, const double* RHS, cplx* G, double* Qp, const cplx* coef, int k, double ir_tol,
                         int ir_max, MixedSolveStats* stats, int* status);
+
+// The loop of a mixed-precision solve (factors in place, Y set) as one CUDA
+// graph with device-side conditions: a WHILE node over the FEAST loops whose
+// body holds the node solves with a nested WHILE node over their refinement
+// steps, the quadrature and Rayleigh-Ritz hooks, and the trace test; the
+// state ends in *st.  key: everything the captured launches depend on.  The
+// graph is captured the second time a key is seen and replayed afterwards;
+// returns "not captured" (nothing launched) when the caller must run the
+// host-driven loop instead, nullptr once the graph ran, else an error.
+const char* mixed_loop(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
+                       MixedWork& w, const double* RHS, double* Qp, const cplx* coef, int k, const LoopParams& lp,
+                       const double* eps, LoopState* st, const LoopHooks& hooks, const unsigned long long* key,
+                       int* status);
+extern const char* const kNotCaptured;
 
 }  // namespace feast

@@ -203,6 +203,11 @@ struct Geom {
   // other end of a two-ended elimination)
   int split = 0;
   int a_row0_hi = 0;
+  // active != nullptr: a CTA whose node is inactive (active[b], b the batch
+  // index, or b - split above the split) leaves at once: a launch of fixed
+  // shape, as a CUDA graph replays it, over the nodes a device-side decision
+  // selects
+  const int* active = nullptr;
 };
 
 // Position of the z-th set bit (z from 0) of a 64-bit mask.
@@ -285,6 +290,7 @@ __global__ void __launch_bounds__(kThreads)
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int e = geo.node_mask ? nth_set_bit(geo.node_mask, (int)blockIdx.z) : (int)blockIdx.z;
+  if (geo.active && !geo.active[geo.split > 0 && e >= geo.split ? e - geo.split : e]) return;   // uniform per CTA
   const int tm = blockIdx.y;
   int tn = (int)blockIdx.x + geo.tn_base;
   if (geo.tn_skip >= 0 && tn >= geo.tn_skip) ++tn;

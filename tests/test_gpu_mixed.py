@@ -139,3 +139,35 @@ def test_graph_replayed_sweeps_match_direct_launches(intervals):
         assert g[4] == direct[0][4] == iv["M"]
         np.testing.assert_array_equal(g[1], direct[0][1])
         np.testing.assert_array_equal(g[2], direct[0][2])
+
+
+@pytest.mark.parametrize("key,seed,early", [("q1_10x10x20/seed1", 1, True), ("q1_10x10x20/seed4", 4, False)])
+def test_device_loop_graph_equals_host_loop(intervals, key, seed, early):
+    """The same solve three times on one handle: the first runs the loop from
+    the host, the second captures it as one CUDA graph whose loop conditions
+    (the refinement of every node solve and the trace test) are decided on
+    the device, the third replays that graph.  The kernels and decisions are
+    the same, so eigenvalues, eigenvectors, loop counts and the trace history
+    are bit-identical; and they match the oracle."""
+    wl = workloads.WORKLOADS["q1_10x10x20_fp64"]
+    op = wl.operator(seed)
+    iv = intervals[key]
+    dop, keep = dev_op(op)
+    h = F().Handle(precision=F().FEAST_PREC_MIXED, seed=1000 + seed, ir_early=early)
+    out = []
+    for rep in range(3):
+        lam = torch.zeros(wl.M0, dtype=torch.float64, device="cuda")
+        X = torch.zeros((wl.M0, op.N), dtype=torch.float64, device="cuda")
+        resid = torch.zeros(wl.M0, dtype=torch.float64, device="cuda")
+        r = h.feast_solve(dop, iv["lmin"], iv["lmax"], wl.M0, wl.Ne, wl.tol, None, lam, X, resid, allow=())
+        out.append((r, lam.cpu().numpy(), back(X), resid.cpu().numpy()))
+    assert [o[0].info.loop_graphs for o in out] == [0, 1, 1]
+    r0, lam0, X0, res0 = out[0]
+    for r, lam, X, res in out[1:]:
+        assert r.m_found == r0.m_found and r.loops == r0.loops
+        assert np.array_equal(lam, lam0) and np.array_equal(X, X0) and np.array_equal(res, res0)
+        assert list(r.info.trace[:r.loops]) == list(r0.info.trace[:r0.loops])
+        assert r.info.ir_steps_max == r0.info.ir_steps_max
+    ref = oracle.feast(op, iv["lmin"], iv["lmax"], wl.M0, wl.Ne, workloads.random_Y(op.N, wl.M0, 1000 + seed),
+                       tol=wl.tol)
+    _compare_feast(lam0, X0, r0.m_found, r0.loops, ref, op, iv["M"])
