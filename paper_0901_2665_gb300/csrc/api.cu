@@ -618,6 +618,10 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
       h->BQ.ensure(sizeof(double) * M0 * M0, "B_Q");
       h->Phi.ensure(sizeof(double) * M0 * M0, "Phi");
       h->work.ensure(sizeof(double) * 3 * M0 * M0, "eig work");
+      // node-solve buffers too, so that the key below is the same from the
+      // first solve on
+      if (const char* m = mixed_solve_prepare(s, v.g, Ne, M0, h->mixed, h->status.as<int>()))
+        fail(FEAST_ERR_CUDA, m);
       const LoopParams lp{lmin, lmax, tol, h->opt.ir_tol, early ? 1 : 0, h->opt.max_loops, h->opt.ir_max, M0};
       LoopHooks hooks;
       hooks.rhs = [&](cudaStream_t st) {

@@ -1666,9 +1666,9 @@ const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const doubl
 
 }  // namespace
 
-const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
-                        MixedWork& w, const double* RHS, cplx* G, double* Qp, const cplx* coef, int k, double ir_tol,
-                        int ir_max, MixedSolveStats* stats, int* status) {
+// Work buffers, kernel attributes and the tuned tile width of a node solve of
+// k right-hand sides; *dout: its dimensions.
+static const char* solve_prepare(cudaStream_t s, Grid g, int Ne, int k, MixedWork& w, int* status, Dims* dout) {
   Dims d = make_dims(g, Ne, k);
   if (w.nz_factored != d.nz || w.ne_factored != Ne) return "mixed solve called without matching factors";
   const long long sG = d.N * k;
@@ -1684,8 +1684,7 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
   w.bemb_k = k;
   d = make_dims(g, Ne, k, tuned_cb(s, d, w, status));
   if (shape_changed) cudaMemsetAsync(w.bufs[B_BEMB], 0, bemb, s);
-  const dim3 rgrid(cdiv(d.N, kResRows), Ne);
-  const long long nblk = rgrid.x;
+  const long long nblk = cdiv(d.N, kResRows);
   static PerDevice<cudaError_t> res_attr;
   if (res_attr.get(
           [] {
@@ -1705,6 +1704,23 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
   if (!ensure(w, B_REL, sizeof(double) * Ne, s)) return "out of device memory";
   if (!ensure(w, B_ACTIVE, sizeof(int) * Ne, s)) return "out of device memory";
   if (!ensure(w, B_R64, sizeof(cplx) * (size_t)Ne * sG, s)) return "out of device memory (residuals)";
+  *dout = d;
+  return nullptr;
+}
+
+const char* mixed_solve_prepare(cudaStream_t s, Grid g, int Ne, int k, MixedWork& w, int* status) {
+  Dims d;
+  return solve_prepare(s, g, Ne, k, w, status, &d);
+}
+
+const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
+                        MixedWork& w, const double* RHS, cplx* G, double* Qp, const cplx* coef, int k, double ir_tol,
+                        int ir_max, MixedSolveStats* stats, int* status) {
+  Dims d;
+  if (const char* m = solve_prepare(s, g, Ne, k, w, status, &d)) return m;
+  const long long sG = d.N * k;
+  const dim3 rgrid(cdiv(d.N, kResRows), Ne);
+  const long long nblk = rgrid.x;
   std::vector<int> active(Ne, 1);
   cudaMemcpyAsync(w.bufs[B_ACTIVE], active.data(), sizeof(int) * Ne, cudaMemcpyHostToDevice, s);
   std::vector<double> rel(Ne, 0.0), final_rel(Ne, 0.0);

@@ -90,6 +90,9 @@ struct MixedWork {
 // Both return nullptr on success, else a static error message.
 const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
                          MixedWork& w, int* status);
+// Allocates the work buffers and sets the kernel attributes of a node solve
+// of k right-hand sides (factors in place), as mixed_solve does first.
+const char* mixed_solve_prepare(cudaStream_t s, Grid g, int Ne, int k, MixedWork& w, int* status);
 // Solves (Z_e B - A) Q_e = RHS for every node e to the refinement tolerance.
 // G (nullable): receives Q_e (Ne x N x k complex128).  Qp (nullable):
 // receives the node shares Re{coef_e Q_e} of the quadrature sum (Eq. 15,
