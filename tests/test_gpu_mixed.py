@@ -115,9 +115,9 @@ def test_feast_solve_mixed_matches_oracle(intervals, key, seed, zero):
 
 
 def test_graph_replayed_sweeps_match_direct_launches(intervals):
-    """The node-solve sweeps run from captured CUDA graphs (replayed on the
-    second solve of a handle); with kernel timing on they are launched one by
-    one.  Both give the same result bit for bit."""
+    """The node-solve sweeps run from captured CUDA graphs (the first solve of
+    a handle; the second runs its whole loop as one graph); with kernel timing
+    on they are launched one by one.  All give the same result bit for bit."""
     wl = workloads.WORKLOADS["q1_10x10x20_fp64"]
     op = wl.operator(2)
     iv = intervals["q1_10x10x20/seed2"]
@@ -130,11 +130,12 @@ def test_graph_replayed_sweeps_match_direct_launches(intervals):
             lam = torch.zeros(wl.M0, dtype=torch.float64, device="cuda")
             X = torch.zeros((wl.M0, op.N), dtype=torch.float64, device="cuda")
             r = h.feast_solve(dop, iv["lmin"], iv["lmax"], wl.M0, wl.Ne, wl.tol, cm(Y), lam, X, None, allow=())
-            runs.append((profile, lam.cpu().numpy(), back(X), r.info.sweep_graphs, r.m_found))
+            runs.append((profile, lam.cpu().numpy(), back(X), (r.info.sweep_graphs, r.info.loop_graphs), r.m_found))
         h.close()
     graphed = [x for x in runs if not x[0]]
     direct = [x for x in runs if x[0]]
-    assert all(x[3] > 0 for x in graphed) and all(x[3] == 0 for x in direct)
+    assert graphed[0][3][0] > 0 and graphed[0][3][1] == 0 and graphed[1][3][1] == 1
+    assert all(x[3] == (0, 0) for x in direct)
     for g in graphed + direct[1:]:
         assert g[4] == direct[0][4] == iv["M"]
         np.testing.assert_array_equal(g[1], direct[0][1])
