@@ -59,6 +59,7 @@ struct Dims {
   int nblk64;    // ceil(n / 64)
   int k;         // right-hand sides
   int CB;        // complex columns per solve-GEMM tile
+  int ST;        // pipeline stages of the solve GEMM
   int nblkCB;    // ceil(k / CB)
   int ldB;       // floats per embedded RHS row
   int K;         // middle layer of the two-ended elimination (nz - 1: one-ended)
@@ -1147,7 +1148,9 @@ cudaStream_t capture_stream(MixedWork& w) {
   return w.cap;
 }
 
-Dims make_dims(Grid g, int Ne, int k, int cb = 0) {
+// cfg: the solve-GEMM configuration, CB | ST << 8 (0: the default for k)
+Dims make_dims(Grid g, int Ne, int k, int cfg = 0) {
+  const int cb = cfg & 255, st = cfg >> 8;
   Dims d;
   d.nx = g.nx;
   d.ny = g.ny;
@@ -1159,6 +1162,7 @@ Dims make_dims(Grid g, int Ne, int k, int cb = 0) {
   d.nblk64 = (d.n + 63) / 64;
   d.k = k;
   d.CB = cb > 0 ? cb : (k <= 8 ? 8 : (k <= 16 ? 16 : (k <= 32 ? 32 : 64)));
+  d.ST = st > 0 ? st : 4;
   d.nblkCB = (k + d.CB - 1) / d.CB;
   d.ldB = d.ldF;
   // two chains need 2 Ne virtual nodes in the 64-bit node masks of the sweeps
@@ -1423,7 +1427,7 @@ struct QuadOut {
 // sweep runs up both chains (chain 0 from layer 0, chain 1 from layer nz-1)
 // to the middle layer K, whose solution x_K = -S'_K g_K starts the backward
 // sweep, which then runs out along both chains.  nl: the real nodes swept.
-template <int CB>
+template <int CB, int ST>
 const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const double* A27, const double* B27,
                          MixedWork& w, const double* Rreal, const f2* Rc, const NodeList& nl, const QuadOut& qo,
                          int* status, const int* dactive) {
@@ -1457,7 +1461,7 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     prof::begin(s, prof::SOLVE_GEMM);
     prof::add_work(prof::SOLVE_GEMM, 8.0 * d.n * (double)d.n * d.k * vl.count);
     const bool ok =
-        launch_tc<2 * CB, 4>(s, dim3(d.nblkCB, cdiv(d.n, 128), vl.count), tmF, tmB, geo, epi, status) == cudaSuccess;
+        launch_tc<2 * CB, ST>(s, dim3(d.nblkCB, cdiv(d.n, 128), vl.count), tmF, tmB, geo, epi, status) == cudaSuccess;
     prof::end(s, prof::SOLVE_GEMM);
     return ok;
   };
@@ -1516,25 +1520,34 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
   return nullptr;
 }
 
-// ---- autotuner of the solve-GEMM tile width (complex columns per CTA tile)
-template <int CB>
+// ---- autotuner of the solve GEMM: tile width (complex columns per CTA
+// tile) and pipeline stages, timed at the launch shape of the sweeps (both
+// chains' virtual nodes, a different layer per launch).  Fewer stages can
+// win: two CTAs then share an SM and overlap one's epilogue with the other's
+// main loop.
+template <int CB, int ST>
 float time_solve_gemm(cudaStream_t s, const Dims& d0, MixedWork& w, int* status) {
   Dims d = d0;
   d.CB = CB;
   d.nblkCB = (d.k + CB - 1) / CB;
+  const int V = d.K < d.nz - 1 ? 2 * d.Ne : d.Ne;
   CUtensorMap tmF, tmB;
   if (!make_map(&tmF, buf<float>(w, B_F), 2 * d.n, (long long)d.Ne * d.nz * d.n, d.ldF, 128)) return 1e30f;
-  if (!make_map(&tmB, buf<float>(w, B_BEMB), 2 * d.n, (long long)d.Ne * d.nblkCB * 2 * CB, d.ldB, 2 * CB)) return 1e30f;
+  if (!make_map(&tmB, buf<float>(w, B_BEMB), 2 * d.n, (long long)V * d.nblkCB * 2 * CB, d.ldB, 2 * CB)) return 1e30f;
   const int nk = (2 * d.n + tc::kBlockK - 1) / tc::kBlockK;
   SolveEpi<CB> epi{buf<f2>(w, B_TOUT), (long long)d.n * d.k, d.n, d.n, d.k, 1.0f};
   tc::Geom geo{0, d.nz * d.n, 0, d.nblkCB * 2 * CB, nk};
+  geo.split = d.Ne;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   float best = 1e30f;
   for (int rep = 0; rep < 4; ++rep) {
+    const int t = rep % d.nz;
+    geo.a_row0 = t * d.n;
+    geo.a_row0_hi = (d.nz - 1 - t) * d.n;
     cudaEventRecord(a, s);
-    launch_tc<2 * CB, 4>(s, dim3(d.nblkCB, cdiv(d.n, 128), d.Ne), tmF, tmB, geo, epi, status);
+    launch_tc<2 * CB, ST>(s, dim3(d.nblkCB, cdiv(d.n, 128), V), tmF, tmB, geo, epi, status);
     cudaEventRecord(b, s);
     cudaEventSynchronize(b);
     float ms = 0.f;
@@ -1548,44 +1561,49 @@ float time_solve_gemm(cudaStream_t s, const Dims& d0, MixedWork& w, int* status)
 }
 
 std::mutex g_tune_mutex;
-std::vector<std::pair<long long, int>> g_tuned;   // (n, k, Ne) key -> CB
+std::vector<std::pair<long long, int>> g_tuned;   // (n, k, Ne) key -> CB | ST << 8
 
-int tuned_cb(cudaStream_t s, const Dims& d, MixedWork& w, int* status) {
+constexpr int cfg_of(int cb, int st) { return cb | st << 8; }
+
+int tuned_cfg(cudaStream_t s, const Dims& d, MixedWork& w, int* status) {
   const long long key = ((long long)d.n << 32) ^ ((long long)d.k << 8) ^ d.Ne;
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     for (auto& kv : g_tuned)
       if (kv.first == key) return kv.second;
   }
-  int best_cb = d.CB;
+  int best_cfg = cfg_of(d.CB, d.ST);
   float best = 1e30f;
-  auto consider = [&](int cb, float ms) {
+  auto consider = [&](int cfg, float ms) {
     if (ms < best) {
       best = ms;
-      best_cb = cb;
+      best_cfg = cfg;
     }
   };
   if (d.k <= 16) {
-    consider(8, time_solve_gemm<8>(s, d, w, status));
-    consider(16, time_solve_gemm<16>(s, d, w, status));
+    consider(cfg_of(8, 4), time_solve_gemm<8, 4>(s, d, w, status));
+    consider(cfg_of(16, 4), time_solve_gemm<16, 4>(s, d, w, status));
   } else {
-    consider(16, time_solve_gemm<16>(s, d, w, status));
-    consider(32, time_solve_gemm<32>(s, d, w, status));
-    consider(64, time_solve_gemm<64>(s, d, w, status));
+    consider(cfg_of(16, 4), time_solve_gemm<16, 4>(s, d, w, status));
+    consider(cfg_of(32, 4), time_solve_gemm<32, 4>(s, d, w, status));
+    consider(cfg_of(64, 3), time_solve_gemm<64, 3>(s, d, w, status));
+    consider(cfg_of(64, 4), time_solve_gemm<64, 4>(s, d, w, status));
   }
   std::lock_guard<std::mutex> lock(g_tune_mutex);
-  g_tuned.push_back({key, best_cb});
-  return best_cb;
+  g_tuned.push_back({key, best_cfg});
+  return best_cfg;
 }
 
 const char* solve_direct(cudaStream_t s, const Dims& d, const cplx* Z, const double* A27, const double* B27,
                          MixedWork& w, const double* Rreal, const f2* Rc, const NodeList& nl, const QuadOut& qo,
                          int* status, const int* dactive = nullptr) {
-  switch (d.CB) {
-    case 8: return solve_sweeps<8>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
-    case 16: return solve_sweeps<16>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
-    case 32: return solve_sweeps<32>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
-    default: return solve_sweeps<64>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
+  switch (cfg_of(d.CB, d.ST)) {
+    case cfg_of(8, 4): return solve_sweeps<8, 4>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
+    case cfg_of(16, 4): return solve_sweeps<16, 4>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
+    case cfg_of(32, 4): return solve_sweeps<32, 4>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
+    case cfg_of(64, 3): return solve_sweeps<64, 3>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
+    case cfg_of(64, 4): return solve_sweeps<64, 4>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
+    default: return "solve-GEMM configuration without an instantiation";
   }
 }
 
@@ -1606,7 +1624,7 @@ const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const doubl
   if (prof::enabled() || !w.use_graphs) return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
   const unsigned long long key[kSweepKey] = {
       (unsigned long long)d.nx | ((unsigned long long)d.ny << 20) | ((unsigned long long)d.nz << 40),
-      (unsigned long long)d.k | ((unsigned long long)d.CB << 20) | ((unsigned long long)d.Ne << 40),
+      (unsigned long long)d.k | ((unsigned long long)cfg_of(d.CB, d.ST) << 20) | ((unsigned long long)d.Ne << 40),
       nl.mask,
       (unsigned long long)(uintptr_t)Rreal, (unsigned long long)(uintptr_t)Rc, (unsigned long long)(uintptr_t)Z,
       (unsigned long long)(uintptr_t)A27, (unsigned long long)(uintptr_t)B27, (unsigned long long)(uintptr_t)status,
@@ -1682,7 +1700,7 @@ static const char* solve_prepare(cudaStream_t s, Grid g, int Ne, int k, MixedWor
   const bool shape_changed = w.sizes[B_BEMB] < bemb || w.bemb_k != k;
   if (!ensure(w, B_BEMB, bemb, s, shape_changed)) return "out of device memory";
   w.bemb_k = k;
-  d = make_dims(g, Ne, k, tuned_cb(s, d, w, status));
+  d = make_dims(g, Ne, k, tuned_cfg(s, d, w, status));
   if (shape_changed) cudaMemsetAsync(w.bufs[B_BEMB], 0, bemb, s);
   const long long nblk = cdiv(d.N, kResRows);
   static PerDevice<cudaError_t> res_attr;
@@ -1950,11 +1968,11 @@ const char* mixed_loop(cudaStream_t s, Grid g, int Ne, const cplx* Z, const doub
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     const long long tkey = ((long long)d.n << 32) ^ ((long long)d.k << 8) ^ d.Ne;
-    int cb = 0;
+    int cfg = 0;
     for (auto& kv : g_tuned)
-      if (kv.first == tkey) cb = kv.second;
-    if (!cb) return kNotCaptured;
-    d = make_dims(g, Ne, k, cb);
+      if (kv.first == tkey) cfg = kv.second;
+    if (!cfg) return kNotCaptured;
+    d = make_dims(g, Ne, k, cfg);
   }
   if (w.loop_graph) cudaGraphExecDestroy(w.loop_graph);
   w.loop_graph = nullptr;
