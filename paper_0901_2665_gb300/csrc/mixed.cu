@@ -38,7 +38,11 @@ namespace feast {
 namespace {
 
 constexpr int kPanel = 64;   // sweep panel width (complex columns)
-constexpr int kRowsPerPanelCta = 16;
+#ifndef FEAST_PANEL_ROWS
+#define FEAST_PANEL_ROWS 32
+#endif
+// rows per CTA of the panel product (each CTA stages the 64 x 64 inverse)
+constexpr int kRowsPerPanelCta = FEAST_PANEL_ROWS;
 
 struct f2 {
   float x, y;
@@ -114,32 +118,56 @@ __device__ __forceinline__ int prev_slot(int chain) { return chain ? 18 : 0; }
 // The fp32 working copies of S_i / S'_i live in a two-plane ping-pong buffer
 // F[v][plane] per virtual node: the recursion only ever needs the previous
 // layer of its chain.
+// In-plane neighbour t (dx = t % 3 - 1, dy = t / 3 - 1) of grid row p as an
+// offset, 0 where it falls outside the cross-section: its coupling
+// coefficient is zero there, and reading the row itself keeps the load in
+// bounds without a branch, so that all taps' loads are independent.
+__device__ __forceinline__ int tap_offset(const Dims& d, int p, int t) {
+  const int px = p % d.nx, py = p / d.nx;
+  const int dx = t % 3 - 1, dy = t / 3 - 1;
+  const bool ok = (dx < 0 ? px > 0 : (dx > 0 ? px + 1 < d.nx : true)) &&
+                  (dy < 0 ? py > 0 : (dy > 0 ? py + 1 < d.ny : true));
+  return ok ? dx + d.nx * dy : 0;
+}
+
+constexpr int kSchurRows = 8;   // rows a of S' per thread of k_mx_schur1
+
 // T1[v][a, q] = sum_b S'[a, b] C[q, b] (row-split, fp32), C = the coupling of
-// the chain's layer to its previous layer (v = blockIdx.z)
+// the chain's layer to its previous layer (v = blockIdx.z).  A thread takes
+// column q of kSchurRows consecutive rows a and loads q's 9 coefficients once.
 __global__ void __launch_bounds__(256) k_mx_schur1(Dims d, Chains ch, const f2* __restrict__ Cf,
                                                    const float* __restrict__ F, float* __restrict__ T1) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  const int a = blockIdx.y, v = blockIdx.z;
+  const int a0 = blockIdx.y * kSchurRows, v = blockIdx.z;
   if (q >= d.n) return;
   const int c = chain_of(ch, v), e = node_of(ch, v);
   const long long rowq = (long long)ch.layer[c] * d.n + q;
-  const float* S = F + (((long long)v * 2 + ch.rplane[c]) * d.n + a) * d.ldF;
-  f2 acc{0.f, 0.f};
+  f2 cv[9];
+  int b[9];
 #pragma unroll
   for (int t = 0; t < 9; ++t) {
-    const int b = q + (t % 3 - 1) + d.nx * (t / 3 - 1);
-    const f2 cv = cf_at(d, Cf, e, prev_slot(c) + t, rowq);
-    if (cv.x != 0.f || cv.y != 0.f) f2fma(acc, f2{S[b], S[d.n + b]}, cv);
+    cv[t] = cf_at(d, Cf, e, prev_slot(c) + t, rowq);
+    b[t] = q + tap_offset(d, q, t);
   }
-  float* out = T1 + ((long long)v * d.n + a) * d.ldF;
-  out[q] = acc.x;
-  out[d.n + q] = acc.y;
+  for (int r = 0; r < kSchurRows; ++r) {
+    const int a = a0 + r;
+    if (a >= d.n) break;
+    const float* S = F + (((long long)v * 2 + ch.rplane[c]) * d.n + a) * d.ldF;
+    f2 acc{0.f, 0.f};
+#pragma unroll
+    for (int t = 0; t < 9; ++t) f2fma(acc, f2{S[b[t]], S[d.n + b[t]]}, cv[t]);
+    float* out = T1 + ((long long)v * d.n + a) * d.ldF;
+    out[q] = acc.x;
+    out[d.n + q] = acc.y;
+  }
 }
 
 // S[p, q] = D[p, q] + sum_a C[p, a] T1[a, q] -> F (plane wplane of v), with
 // C the coupling of v's layer to its previous layer (has_prev: 0 on a chain's
 // first layer).  middle: v < Ne only; the middle layer takes both chains'
 // contributions, C0 T1[v] + C1 T1[v + Ne] (the second when has_prev1).
+// Row p's coefficients are loaded first and the T1 rows of all taps are read
+// unconditionally (tap_offset), so that the loads overlap.
 __global__ void __launch_bounds__(256) k_mx_schur2(Dims d, Chains ch, int has_prev, int middle, int has_prev1,
                                                    const f2* __restrict__ Cf, const float* __restrict__ T1,
                                                    float* __restrict__ F) {
@@ -154,12 +182,13 @@ __global__ void __launch_bounds__(256) k_mx_schur2(Dims d, Chains ch, int has_pr
   if (ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1) acc = cf_at(d, Cf, e, 9 + (ddy + 1) * 3 + (ddx + 1), rowp);
   auto add = [&](int vt, int slot0) {
     const float* T = T1 + (long long)vt * d.n * d.ldF;
+    f2 cv[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) cv[t] = cf_at(d, Cf, e, slot0 + t, rowp);
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
-      const f2 cv = cf_at(d, Cf, e, slot0 + t, rowp);
-      if (cv.x == 0.f && cv.y == 0.f) continue;
-      const float* Trow = T + (long long)(p + (t % 3 - 1) + d.nx * (t / 3 - 1)) * d.ldF;
-      f2fma(acc, cv, f2{Trow[q], Trow[d.n + q]});
+      const float* Trow = T + (long long)(p + tap_offset(d, p, t)) * d.ldF;
+      f2fma(acc, cv[t], f2{Trow[q], Trow[d.n + q]});
     }
   };
   if (has_prev) add(v, prev_slot(c));
@@ -312,8 +341,10 @@ constexpr int kPinvRpt = FEAST_PINV_RPT;   // rows per thread of the panel inver
 __global__ void __launch_bounds__(256) k_mx_panel_T(Dims d, int plane, int k0, int bw, const float* __restrict__ F,
                                                     const f2* __restrict__ PinvIn, float* __restrict__ Aop,
                                                     float* __restrict__ Bop, f2* __restrict__ Tc) {
-  __shared__ f2 Ps[kPanel][kPanel + 1];
-  __shared__ f2 Ls[kRowsPerPanelCta][kPanel + 1];
+  // unpadded: the accesses below are consecutive along the second index or
+  // warp-wide broadcasts, so no bank conflicts (and 32 rows fit in 48 KB)
+  __shared__ f2 Ps[kPanel][kPanel];
+  __shared__ f2 Ls[kRowsPerPanelCta][kPanel];
   const int e = blockIdx.y;
   const int r0 = blockIdx.x * kRowsPerPanelCta;
   const int tid = threadIdx.x;
@@ -699,82 +730,96 @@ __device__ __forceinline__ void write_emb(const Dims& d, float* Bemb, int e, int
   im_row[d.n + p] = tc::to_tf32(g.x);
 }
 
+constexpr int kCoupleCols = 4;   // right-hand-side columns per thread of the coupling kernels
+
 // forward: g = R + C t on a chain's layer, t = S'_prev g_prev the product
-// of the chain's previous step (has_prev: 0 on the chain's first layer);
-// one thread per (row p, column m).  R is the real RHS (Rreal) or the
-// complex64 residual of the node (Rc).  middle (chain-0 virtual nodes only):
-// the middle layer adds both chains' products, C0 Tout[v] + C1 Tout[v + Ne]
-// (the second when has_prev1).  CTA z handles the virtual node of the z-th
-// set bit of nl.mask; g goes to the node's solution column, its embedded
-// copy to the virtual node's GEMM operand.
+// of the chain's previous step (has_prev: 0 on a chain's first layer).  R is
+// the real RHS (Rreal) or the complex64 residual of the node (Rc).  middle
+// (chain-0 virtual nodes only): the middle layer adds both chains' products,
+// C0 Tout[v] + C1 Tout[v + Ne] (the second when has_prev1).  A thread takes
+// row p of kCoupleCols columns m and loads the row's taps once; CTA z
+// handles the virtual node of the z-th set bit of nl.mask.  g goes to the
+// node's solution column, its embedded copy to the virtual node's GEMM
+// operand.
 __global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, Chains ch, int has_prev, int middle, int has_prev1,
                                                        const f2* __restrict__ Cf, const double* __restrict__ Rreal,
                                                        const f2* __restrict__ Rc, const f2* __restrict__ Tout,
                                                        f2* __restrict__ Gc, float* __restrict__ Bemb, NodeList nl,
                                                        const int* __restrict__ active) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int m = blockIdx.y, v = tc::nth_set_bit(nl.mask, (int)blockIdx.z);
+  const int m0 = blockIdx.y * kCoupleCols, v = tc::nth_set_bit(nl.mask, (int)blockIdx.z);
   if (p >= d.n) return;
   const int c = chain_of(ch, v), e = node_of(ch, v);
   if (active && !active[e]) return;   // a node the device-side refinement left out
   const long long row = (long long)ch.layer[c] * d.n + p;
   const long long sG = d.N * d.k;
-  f2 g = Rc ? Rc[e * sG + (long long)m * d.N + row] : f2{(float)Rreal[(long long)m * d.N + row], 0.f};
-  const int px = p % d.nx, py = p / d.nx;
-  const bool xm = px > 0, xp = px + 1 < d.nx, ym = py > 0, yp = py + 1 < d.ny;
-  auto add = [&](int vt, int slot0) {
-    const f2* T = Tout + ((long long)vt * d.k + m) * d.n;
-    const f2* C = Cf + ((long long)e * 27 + slot0) * d.N + row;
-    // branch-free taps: an in-plane neighbour outside the grid has a zero
-    // coefficient and is read at offset 0 (the row itself) to stay in bounds
+  // branch-free taps: an in-plane neighbour outside the grid has a zero
+  // coefficient and is read at offset 0 (the row itself) to stay in bounds
+  int off[9];
+  f2 c0[9], c1[9];
+  const bool two = middle && has_prev1;
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {
-      const int dx = t % 3 - 1, dy = t / 3 - 1;
-      const bool ok = (dx < 0 ? xm : (dx > 0 ? xp : true)) && (dy < 0 ? ym : (dy > 0 ? yp : true));
-      f2fma(g, C[(long long)t * d.N], T[p + (ok ? dx + d.nx * dy : 0)]);
+  for (int t = 0; t < 9; ++t) {
+    off[t] = p + tap_offset(d, p, t);
+    c0[t] = has_prev ? Cf[((long long)e * 27 + prev_slot(c) + t) * d.N + row] : f2{0.f, 0.f};
+    c1[t] = two ? Cf[((long long)e * 27 + prev_slot(1) + t) * d.N + row] : f2{0.f, 0.f};
+  }
+  for (int m = m0; m < m0 + kCoupleCols && m < d.k; ++m) {
+    f2 g = Rc ? Rc[e * sG + (long long)m * d.N + row] : f2{(float)Rreal[(long long)m * d.N + row], 0.f};
+    if (has_prev) {
+      const f2* T = Tout + ((long long)v * d.k + m) * d.n;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) f2fma(g, c0[t], T[off[t]]);
     }
-  };
-  if (has_prev) add(v, prev_slot(c));
-  if (middle && has_prev1) add(v + ch.Ne, prev_slot(1));
-  Gc[e * sG + (long long)m * d.N + row] = g;
-  write_emb(d, Bemb, v, p, m, g);
+    if (two) {
+      const f2* T = Tout + ((long long)(v + ch.Ne) * d.k + m) * d.n;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) f2fma(g, c1[t], T[off[t]]);
+    }
+    Gc[e * sG + (long long)m * d.N + row] = g;
+    write_emb(d, Bemb, v, p, m, g);
+  }
 }
 
 // backward: s = g - U x_next on a chain's layer, x_next the solution of the
 // chain's next layer towards the middle (chain 0: layer + 1, coupled through
 // the dz = +1 slots; chain 1: layer - 1, the dz = -1 slots); the embedded s
 // goes to the virtual node's GEMM operand.  A layer without a next one (the
-// last layer of a one-ended elimination) takes s = g.
+// last layer of a one-ended elimination) takes s = g.  Threads as in the
+// forward coupling.
 __global__ void __launch_bounds__(128) k_mx_couple_bwd(Dims d, Chains ch, const f2* __restrict__ Cf,
                                                        const f2* __restrict__ Gc, float* __restrict__ Bemb,
                                                        NodeList nl, const int* __restrict__ active) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int m = blockIdx.y, v = tc::nth_set_bit(nl.mask, (int)blockIdx.z);
+  const int m0 = blockIdx.y * kCoupleCols, v = tc::nth_set_bit(nl.mask, (int)blockIdx.z);
   if (p >= d.n) return;
   const int c = chain_of(ch, v), e = node_of(ch, v);
   if (active && !active[e]) return;
   const int layer = ch.layer[c], next = c ? layer - 1 : layer + 1;
+  const bool has_next = next >= 0 && next < d.nz;
   const long long row = (long long)layer * d.n + p;
   const long long sG = d.N * d.k;
-  const f2* col = Gc + e * sG + (long long)m * d.N + row;
-  f2 sv = col[0];
-  if (next >= 0 && next < d.nz) {
-    const f2* C = Cf + ((long long)e * 27 + prev_slot(1 - c)) * d.N + row;
-    const long long dn = c ? -(long long)d.n : (long long)d.n;
-    const int px = p % d.nx, py = p / d.nx;
-    const bool xm = px > 0, xp = px + 1 < d.nx, ym = py > 0, yp = py + 1 < d.ny;
-    // branch-free taps, as in the forward coupling
+  const long long dn = c ? -(long long)d.n : (long long)d.n;
+  int off[9];
+  f2 cv[9];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {
-      const int dx = t % 3 - 1, dy = t / 3 - 1;
-      const bool ok = (dx < 0 ? xm : (dx > 0 ? xp : true)) && (dy < 0 ? ym : (dy > 0 ? yp : true));
-      const f2 cv = C[(long long)t * d.N];
-      const f2 x = col[dn + (ok ? dx + d.nx * dy : 0)];
-      sv.x -= cv.x * x.x - cv.y * x.y;
-      sv.y -= cv.x * x.y + cv.y * x.x;
-    }
+  for (int t = 0; t < 9; ++t) {
+    off[t] = tap_offset(d, p, t);
+    cv[t] = has_next ? Cf[((long long)e * 27 + prev_slot(1 - c) + t) * d.N + row] : f2{0.f, 0.f};
   }
-  write_emb(d, Bemb, v, p, m, sv);
+  for (int m = m0; m < m0 + kCoupleCols && m < d.k; ++m) {
+    const f2* col = Gc + e * sG + (long long)m * d.N + row;
+    f2 sv = col[0];
+    if (has_next) {
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const f2 x = col[dn + off[t]];
+        sv.x -= cv[t].x * x.x - cv[t].y * x.y;
+        sv.y -= cv[t].x * x.y + cv[t].y * x.x;
+      }
+    }
+    write_emb(d, Bemb, v, p, m, sv);
+  }
 }
 
 // ------------------------------------------------------------------ refinement
@@ -1337,7 +1382,7 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
       prof::begin(s, prof::SCHUR);
       prof::add_work(prof::SCHUR, (t > 0 ? 144.0 : 0.0) * d.n * (double)d.n * nv);
       if (t > 0)
-        k_mx_schur1<<<dim3(sgrid.x, sgrid.y, nv), 256, 0, s>>>(d, ch, Cf, F, buf<float>(w, B_T1));
+        k_mx_schur1<<<dim3(sgrid.x, cdiv(d.n, kSchurRows), nv), 256, 0, s>>>(d, ch, Cf, F, buf<float>(w, B_T1));
       k_mx_schur2<<<dim3(sgrid.x, sgrid.y, nv), 256, 0, s>>>(d, ch, t > 0, 0, 0, Cf, buf<float>(w, B_T1), F);
       prof::end(s, prof::SCHUR);
       prof::count_launch(t > 0 ? 2 : 1);
@@ -1349,7 +1394,8 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
       prof::begin(s, prof::SCHUR);
       prof::add_work(prof::SCHUR, (L0 > 0 ? 144.0 : 0.0) * (L1 > 0 ? 2.0 : 1.0) * d.n * (double)d.n * Ne);
       if (L0 > 0)
-        k_mx_schur1<<<dim3(sgrid.x, sgrid.y, L1 > 0 ? V : Ne), 256, 0, s>>>(d, ch, Cf, F, buf<float>(w, B_T1));
+        k_mx_schur1<<<dim3(sgrid.x, cdiv(d.n, kSchurRows), L1 > 0 ? V : Ne), 256, 0, s>>>(d, ch, Cf, F,
+                                                                                         buf<float>(w, B_T1));
       k_mx_schur2<<<dim3(sgrid.x, sgrid.y, Ne), 256, 0, s>>>(d, ch, L0 > 0, 1, L1 > 0, Cf, buf<float>(w, B_T1), F);
       prof::end(s, prof::SCHUR);
       prof::count_launch(L0 > 0 ? 2 : 1);
@@ -1487,8 +1533,8 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     const NodeList& vl = t < L1 ? both : one;
     prof::begin(s, prof::COUPLE);
     prof::add_work(prof::COUPLE, couple_bytes(vl.count, 40.0));
-    k_mx_couple_fwd<<<dim3(cdiv(d.n, 128), d.k, vl.count), 128, 0, s>>>(d, ch, t > 0, 0, 0, Cf, Rreal, Rc, Tout, Gc,
-                                                                         Bemb, vl, dactive);
+    k_mx_couple_fwd<<<dim3(cdiv(d.n, 128), cdiv(d.k, kCoupleCols), vl.count), 128, 0, s>>>(
+        d, ch, t > 0, 0, 0, Cf, Rreal, Rc, Tout, Gc, Bemb, vl, dactive);
     prof::end(s, prof::COUPLE);
     SolveEpi<CB> epi{Tout, (long long)d.n * d.k, d.n, d.n, d.k, 1.0f};
     if (!gemm(vl, t, d.nz - 1 - t, epi)) return "tcgen05 solve launch failed";
@@ -1499,8 +1545,8 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     const Chains ch{Ne, {K, K}, {0, 0}, 0};
     prof::begin(s, prof::COUPLE);
     prof::add_work(prof::COUPLE, couple_bytes(one.count, L1 > 0 ? 48.0 : 40.0));
-    k_mx_couple_fwd<<<dim3(cdiv(d.n, 128), d.k, one.count), 128, 0, s>>>(d, ch, L0 > 0, 1, L1 > 0, Cf, Rreal, Rc,
-                                                                          Tout, Gc, Bemb, one, dactive);
+    k_mx_couple_fwd<<<dim3(cdiv(d.n, 128), cdiv(d.k, kCoupleCols), one.count), 128, 0, s>>>(
+        d, ch, L0 > 0, 1, L1 > 0, Cf, Rreal, Rc, Tout, Gc, Bemb, one, dactive);
     prof::end(s, prof::COUPLE);
     if (!gemm(one, K, K, back_epi(ch))) return "tcgen05 solve launch failed";
     launches += 2;
@@ -1511,7 +1557,8 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     const NodeList& vl = u < L1 ? both : one;
     prof::begin(s, prof::COUPLE);
     prof::add_work(prof::COUPLE, couple_bytes(vl.count, 32.0));
-    k_mx_couple_bwd<<<dim3(cdiv(d.n, 128), d.k, vl.count), 128, 0, s>>>(d, ch, Cf, Gc, Bemb, vl, dactive);
+    k_mx_couple_bwd<<<dim3(cdiv(d.n, 128), cdiv(d.k, kCoupleCols), vl.count), 128, 0, s>>>(d, ch, Cf, Gc, Bemb, vl,
+                                                                                          dactive);
     prof::end(s, prof::COUPLE);
     if (!gemm(vl, K - 1 - u, K + 1 + u, back_epi(ch))) return "tcgen05 solve launch failed";
     launches += 2;
