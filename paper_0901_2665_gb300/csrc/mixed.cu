@@ -200,6 +200,16 @@ __global__ void __launch_bounds__(256) k_mx_schur2(Dims d, Chains ch, int has_pr
 
 // ------------------------------------------------------------------ panel
 
+// In-place output of a diagonal block of the recursive inversion:
+// -S[K,K]^{-1} back into the block of F and, for a block that no later step
+// changes, its TF32-rounded copy into the layer's solve operand Fr.
+struct LeafOut {
+  float* F = nullptr;
+  float* Fr = nullptr;
+  Chains ch{};
+  int nz = 0;
+};
+
 // 1/a for complex fp32 with scaling, from approximate reciprocals (a couple
 // of ulp, far below the TF32 rounding the factors are used at): on the panel
 // inverse's critical path every pivot waits for one of these.
@@ -233,8 +243,8 @@ __device__ __forceinline__ f2 f2inv_fast(f2 a) {
 // 32 rows per thread leaves one warp per scheduler to hide every latency.
 template <int RPT>
 __global__ void __launch_bounds__(kPanel * (kPanel / RPT)) k_mx_pinv(Dims d, int plane, int k0, int bw,
-                                                                         const float* __restrict__ F,
-                                                                         f2* __restrict__ PinvOut, int* status) {
+                                                                         const float* F, f2* __restrict__ PinvOut,
+                                                                         int* status, LeafOut lo) {
   constexpr int H = kPanel / RPT;   // row blocks
   static_assert(RPT % 2 == 0 && kPanel % RPT == 0, "rows per thread");
   __shared__ __align__(16) f2 rowb[2][kPanel];   // row k of P before pivot k
@@ -315,13 +325,40 @@ __global__ void __launch_bounds__(kPanel * (kPanel / RPT)) k_mx_pinv(Dims d, int
     }
   }
   // P holds -S[K,K]^{-1}
+  if (PinvOut) {
 #pragma unroll
-  for (int a = 0; a < RPT; ++a) {
-    const int i = h * RPT + a;
-    PinvOut[(long long)e * kPanel * kPanel + i * kPanel + j] = f2{-v[a].x, -v[a].y};
+    for (int a = 0; a < RPT; ++a) {
+      const int i = h * RPT + a;
+      PinvOut[(long long)e * kPanel * kPanel + i * kPanel + j] = f2{-v[a].x, -v[a].y};
+    }
+  }
+  if (lo.F) {
+    float* Fw = lo.F + ((long long)e * 2 + plane) * n * d.ldF;
+    float* Frw = lo.Fr ? lo.Fr + ((long long)node_of(lo.ch, e) * lo.nz + lo.ch.layer[chain_of(lo.ch, e)]) * n * d.ldF
+                       : nullptr;
+#pragma unroll
+    for (int a = 0; a < RPT; ++a) {
+      const int i = h * RPT + a;
+      if (i < bw && j < bw) {
+        const long long at = (long long)(k0 + i) * d.ldF + k0 + j;
+        Fw[at] = v[a].x;
+        Fw[at + n] = v[a].y;
+        if (Frw) {
+          Frw[at] = tc::to_tf32(v[a].x);
+          Frw[at + n] = tc::to_tf32(v[a].y);
+        }
+      }
+    }
   }
   if (tid == 0 && bad) atomicExch(status, (int)DEV_PIVOT);
 }
+
+#ifndef FEAST_FACTOR_PANEL_SWEEP
+#define FEAST_FACTOR_PANEL_SWEEP 0
+#endif
+// 1: invert the layer complements by the 64-column panel sweep even where the
+// recursive block inversion applies
+constexpr bool kFactorPanelSweep = FEAST_FACTOR_PANEL_SWEEP != 0;
 
 #ifndef FEAST_WIDE_STAGES
 #define FEAST_WIDE_STAGES 1
@@ -703,6 +740,114 @@ struct SolveEpi {
           const f2 x{alpha * re[t], alpha * im[t]};
           o[(long long)m * ldo + p] = x;
           if (q) q[(long long)m * ldq + p] = pre.q[c0 + t] + (ce.re * (double)x.x - ce.im * (double)x.y);
+        }
+      }
+    }
+  }
+};
+
+// ------------------------------------------------------------------ recursive inversion
+// The layer complement S (complex symmetric) is inverted in place by 2 x 2
+// block elimination, S = [A B; B^T D] with the split at a multiple of 64:
+//   Abar = -A^{-1} (recursively),        Xbar = Abar B,
+//   D   <- D + Xbar^T B  (the Schur complement D - B^T A^{-1} B),
+//   Sbar = -D^{-1} (recursively),        Ybar = Xbar Sbar,
+//   -S^{-1} = [Abar + Ybar Xbar^T, Ybar; Ybar^T, Sbar],
+// the diagonal blocks of 64 by the Gauss-Jordan sweep of k_mx_pinv.  Every
+// product is a batched complex TF32 GEMM (tc::k_cgemm, C = U V^T) over the
+// virtual nodes; its epilogue writes C transposed (lanes are rows of C, so
+// the stores of a warp are contiguous) and/or as is, adds C^T into a
+// symmetric block instead, and copies the blocks that no later step changes
+// into the TF32 solve operand Fr.
+
+// Destination of a row-split block: element (r, c) of batch b at
+// base + b bstride + r ld + c (real part; imaginary part imoff further).
+struct InvDest {
+  float* base = nullptr;
+  long long bstride = 0;
+  int ld = 0, imoff = 0;
+};
+
+constexpr int kInvBN = 64;   // complex columns per CTA tile of the inversion GEMMs
+#ifndef FEAST_INV_STAGES
+#define FEAST_INV_STAGES 2
+#endif
+constexpr int kInvStages = FEAST_INV_STAGES;
+
+struct InvEpi {
+  InvDest t;           // C^T: element (j, i) <- C[i, j]
+  InvDest r;           // C:   element (i, j) <- C[i, j]
+  int add = 0;         // t += C^T instead of t = C^T
+  int M = 0, N = 0;    // rows and columns of C
+  // final blocks: TF32 copies at offsets fr_t / fr_r of the layer's plane of
+  // Fr (row stride ld_fr, imaginary parts imoff_fr further); fr == nullptr: none
+  float* fr = nullptr;
+  long long fr_t = -1, fr_r = -1;
+  int ld_fr = 0, imoff_fr = 0;
+  long long fr_plane = 0;
+  Chains ch{};
+  int nz = 0;
+  __device__ void operator()(int b, int tm, int tn, int row, uint32_t taddr) const {
+    const int i = tm * tc::kBlockM + row;
+    float* frp = nullptr;
+    if (fr) frp = fr + ((long long)node_of(ch, b) * nz + ch.layer[chain_of(ch, b)]) * fr_plane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < kInvBN; c0 += 16) {
+      float re[16], im[16];
+      tc::cload16<kInvBN>(taddr, c0, re, im);   // warp-collective: before any exit
+      const int j0 = tn * kInvBN + c0;
+      if (i >= M || j0 >= N) continue;
+      if (t.base) {
+        float* tb = t.base + b * t.bstride + i;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int j = j0 + u;
+          if (j < N) {
+            float* p = tb + (long long)j * t.ld;
+            float xr = re[u], xi = im[u];
+            if (add) {
+              xr += p[0];
+              xi += p[t.imoff];
+            }
+            p[0] = xr;
+            p[t.imoff] = xi;
+            if (frp && fr_t >= 0) {
+              float* q = frp + fr_t + (long long)j * ld_fr + i;
+              q[0] = tc::to_tf32(xr);
+              q[imoff_fr] = tc::to_tf32(xi);
+            }
+          }
+        }
+      }
+      if (r.base) {
+        float* p = r.base + b * r.bstride + (long long)i * r.ld + j0;
+        float* q = (frp && fr_r >= 0) ? frp + fr_r + (long long)i * ld_fr + j0 : nullptr;
+        const uintptr_t al = reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(p + r.imoff) |
+                             (q ? reinterpret_cast<uintptr_t>(q) | reinterpret_cast<uintptr_t>(q + imoff_fr) : 0);
+        if (j0 + 16 <= N && (al & 15) == 0) {
+#pragma unroll
+          for (int u = 0; u < 16; u += 4) {
+            *reinterpret_cast<float4*>(p + u) = make_float4(re[u], re[u + 1], re[u + 2], re[u + 3]);
+            *reinterpret_cast<float4*>(p + r.imoff + u) = make_float4(im[u], im[u + 1], im[u + 2], im[u + 3]);
+            if (q) {
+              *reinterpret_cast<float4*>(q + u) = make_float4(tc::to_tf32(re[u]), tc::to_tf32(re[u + 1]),
+                                                              tc::to_tf32(re[u + 2]), tc::to_tf32(re[u + 3]));
+              *reinterpret_cast<float4*>(q + imoff_fr + u) = make_float4(
+                  tc::to_tf32(im[u]), tc::to_tf32(im[u + 1]), tc::to_tf32(im[u + 2]), tc::to_tf32(im[u + 3]));
+            }
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            if (j0 + u < N) {
+              p[u] = re[u];
+              p[r.imoff + u] = im[u];
+              if (q) {
+                q[u] = tc::to_tf32(re[u]);
+                q[imoff_fr + u] = tc::to_tf32(im[u]);
+              }
+            }
+          }
         }
       }
     }
@@ -1215,6 +1360,166 @@ Dims make_dims(Grid g, int Ne, int k, int cfg = 0) {
   return d;
 }
 
+// ---- recursive inversion: launch plan
+// Workspace of recursion level L (blocks of at most cap[L] rows): Xbar and
+// Xbar^T of every virtual node, row-split with row stride 2 cap[L], at float
+// offset woff[L] of the buffers W and W2.
+struct InvLevels {
+  std::vector<int> cap;
+  std::vector<long long> woff;
+  long long floats = 0;   // per buffer
+};
+
+// Split of a block of s rows (s > 64): the first part is a multiple of 64.
+inline int inv_split(int s) { return 64 * (((s + 63) / 64 + 1) / 2); }
+
+InvLevels inv_levels(int n, int V) {
+  InvLevels lv;
+  for (int s = n; s > kPanel; s = inv_split(s)) {
+    const int h = inv_split(s);
+    lv.cap.push_back(h);
+    lv.woff.push_back(lv.floats);
+    lv.floats += (long long)V * h * 2 * h;
+  }
+  return lv;
+}
+
+struct InvOp {
+  int leaf = 0;       // 1: diagonal block [off, off + s) by k_mx_pinv, final when fin
+  int off = 0, s = 0, fin = 0;
+  CUtensorMap m[4];   // U re, U im, V re, V im
+  tc::CGeom geo{};
+  int M = 0, N = 0;
+  double flops = 0;   // per virtual node
+  InvEpi epi;         // ch set per layer step
+};
+
+// The launches that invert every virtual node's plane `plane` of F in place
+// (S <- -S^{-1}), final blocks also into Fr.  Returns an error or nullptr.
+const char* build_inversion(const Dims& d, int V, int plane, float* F, float* Fr, float* W, float* W2,
+                            const InvLevels& lv, std::vector<InvOp>& ops) {
+  const long long planeF = (long long)d.n * d.ldF;
+  float* Fp = F + plane * planeF;
+  // F block (row0, col0, rows x cols) of every virtual node's plane: z = 2 b + plane
+  auto fmap = [&](CUtensorMap* m, int row0, int col0, int rows, int cols, int box_rows) {
+    const float* base = F + (long long)row0 * d.ldF + col0;
+    return make_map_3d(m, base, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, cols, rows, 2LL * V, d.ldF, planeF, tc::kBlockK,
+                       box_rows, CU_TENSOR_MAP_SWIZZLE_128B) &&
+           make_map_3d(m + 1, base + d.n, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, cols, rows, 2LL * V, d.ldF, planeF,
+                       tc::kBlockK, box_rows, CU_TENSOR_MAP_SWIZZLE_128B);
+  };
+  // level-L workspace block (rows x cols from the origin): z = b
+  auto wmap = [&](CUtensorMap* m, const float* Wb, int L, int rows, int cols, int box_rows) {
+    const int cap = lv.cap[L];
+    const float* base = Wb + lv.woff[L];
+    return make_map_3d(m, base, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, cols, rows, V, 2LL * cap, (long long)cap * 2 * cap,
+                       tc::kBlockK, box_rows, CU_TENSOR_MAP_SWIZZLE_128B) &&
+           make_map_3d(m + 1, base + cap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, cols, rows, V, 2LL * cap,
+                       (long long)cap * 2 * cap, tc::kBlockK, box_rows, CU_TENSOR_MAP_SWIZZLE_128B);
+  };
+  auto fdest = [&](int row0, int col0) {
+    return InvDest{Fp + (long long)row0 * d.ldF + col0, 2 * planeF, d.ldF, d.n};
+  };
+  auto wdest = [&](float* Wb, int L) {
+    const int cap = lv.cap[L];
+    return InvDest{Wb + lv.woff[L], (long long)cap * 2 * cap, 2 * cap, cap};
+  };
+  auto gemm = [&](int M, int N, int K, bool u_in_f, bool v_in_f) {
+    InvOp op;
+    op.M = M;
+    op.N = N;
+    op.geo = tc::CGeom{(K + tc::kBlockK - 1) / tc::kBlockK, u_in_f ? 2 : 1, u_in_f ? plane : 0, v_in_f ? 2 : 1,
+                       v_in_f ? plane : 0};
+    op.flops = 8.0 * M * (double)N * K;
+    op.epi.M = M;
+    op.epi.N = N;
+    op.epi.ld_fr = d.ldF;
+    op.epi.imoff_fr = d.n;
+    op.epi.fr_plane = planeF;
+    op.epi.nz = d.nz;
+    return op;
+  };
+  auto rec = [&](auto&& self, int L, int off, int s, bool fin) -> const char* {
+    if (s <= kPanel) {
+      InvOp op;
+      op.leaf = 1;
+      op.off = off;
+      op.s = s;
+      op.fin = fin;
+      op.flops = 8.0 * s * (double)s * s;
+      ops.push_back(op);
+      return nullptr;
+    }
+    const int h = inv_split(s), t = s - h;
+    if (const char* m = self(self, L + 1, off, h, false)) return m;
+    {  // Xbar^T = B^T Abar -> Xbar (W, transposed) and Xbar^T (W2)
+      InvOp op = gemm(t, h, h, true, true);
+      if (!fmap(op.m, off + h, off, t, h, tc::kBlockM) || !fmap(op.m + 2, off, off, h, h, kInvBN))
+        return "tensor map (inversion) rejected";
+      op.epi.t = wdest(W, L);
+      op.epi.r = wdest(W2, L);
+      ops.push_back(op);
+    }
+    {  // D += Xbar^T B
+      InvOp op = gemm(t, t, h, false, true);
+      if (!wmap(op.m, W2, L, t, h, tc::kBlockM) || !fmap(op.m + 2, off + h, off, t, h, kInvBN))
+        return "tensor map (inversion) rejected";
+      op.epi.t = fdest(off + h, off + h);
+      op.epi.add = 1;
+      ops.push_back(op);
+    }
+    if (const char* m = self(self, L + 1, off + h, t, fin)) return m;
+    {  // Ybar^T = Sbar Xbar^T -> upper-right block (transposed) and lower-left block
+      InvOp op = gemm(t, h, t, true, false);
+      if (!fmap(op.m, off + h, off + h, t, t, tc::kBlockM) || !wmap(op.m + 2, W, L, h, t, kInvBN))
+        return "tensor map (inversion) rejected";
+      op.epi.t = fdest(off, off + h);
+      op.epi.r = fdest(off + h, off);
+      if (fin) {
+        op.epi.fr = Fr;
+        op.epi.fr_t = (long long)off * d.ldF + off + h;
+        op.epi.fr_r = (long long)(off + h) * d.ldF + off;
+      }
+      ops.push_back(op);
+    }
+    {  // Abar += Ybar Xbar^T
+      InvOp op = gemm(h, h, t, true, false);
+      if (!fmap(op.m, off, off + h, h, t, tc::kBlockM) || !wmap(op.m + 2, W, L, h, t, kInvBN))
+        return "tensor map (inversion) rejected";
+      op.epi.t = fdest(off, off);
+      op.epi.add = 1;
+      if (fin) {
+        op.epi.fr = Fr;
+        op.epi.fr_t = (long long)off * d.ldF + off;
+      }
+      ops.push_back(op);
+    }
+    return nullptr;
+  };
+  return rec(rec, 0, 0, d.n, true);
+}
+
+template <class Epi>
+cudaError_t cg_attr() {
+  constexpr size_t smem = tc::CSmem<kInvBN, kInvStages>::kBytes;
+  static PerDevice<cudaError_t> attr;
+  return attr.get(
+      [] {
+        return cudaFuncSetAttribute(tc::k_cgemm<kInvBN, kInvStages, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+      },
+      cudaErrorInvalidDevice);
+}
+
+template <class Epi>
+cudaError_t launch_cg(cudaStream_t s, dim3 grid, const CUtensorMap* m, const tc::CGeom& geo, const Epi& epi,
+                      int* status) {
+  constexpr size_t smem = tc::CSmem<kInvBN, kInvStages>::kBytes;
+  if (const cudaError_t e = cg_attr<Epi>()) return e;
+  tc::k_cgemm<kInvBN, kInvStages, Epi><<<grid, tc::kThreads, smem, s>>>(m[0], m[1], m[2], m[3], geo, epi, status);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 void MixedWork::release() {
@@ -1257,13 +1562,20 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
   if (!ensure(w, B_F, fbytes, s)) return "out of device memory (mixed factors)";
   if (!ensure(w, B_FW, sizeof(float) * (size_t)V * 2 * d.n * d.ldF, s)) return "out of device memory (working layers)";
   if (!ensure(w, B_T1, sizeof(float) * (size_t)V * d.n * d.ldF, s)) return "out of device memory (schur scratch)";
-  // panel operands are double-buffered by panel parity (lookahead)
+  // The recursive block inversion needs 16-byte aligned imaginary halves of
+  // the row-split rows (n a multiple of 4) for its tensor maps; otherwise
+  // the layers are inverted by the panel sweep.
+  const bool recursive = !kFactorPanelSweep && d.n % 4 == 0 && d.n > kPanel;
+  const InvLevels lv = inv_levels(d.n, V);
+  // panel operands are double-buffered by panel parity (lookahead); the
+  // recursive inversion keeps its workspaces Xbar and Xbar^T in the same buffers
   const size_t aop_sz = (size_t)V * d.n * 2 * kPanel;
   const size_t bop_sz = (size_t)V * d.nblk64 * 128 * 2 * kPanel;
   const size_t tc_sz = (size_t)V * d.n * kPanel;
   const size_t pinv_sz = (size_t)V * kPanel * kPanel;
-  if (!ensure(w, B_AOP, sizeof(float) * 2 * aop_sz, s, true)) return "out of device memory";
-  if (!ensure(w, B_BOP, sizeof(float) * 2 * bop_sz, s, true)) return "out of device memory";
+  const size_t wfl = recursive ? (size_t)lv.floats : 0;
+  if (!ensure(w, B_AOP, sizeof(float) * std::max(2 * aop_sz, wfl), s, true)) return "out of device memory";
+  if (!ensure(w, B_BOP, sizeof(float) * std::max(2 * bop_sz, wfl), s, true)) return "out of device memory";
   if (!ensure(w, B_TC, sizeof(f2) * 2 * tc_sz, s)) return "out of device memory";
   if (!ensure(w, B_PINV, sizeof(f2) * 2 * pinv_sz, s)) return "out of device memory";
   if (!ensure(w, B_CF, sizeof(f2) * (size_t)Ne * 27 * d.N, s)) return "out of device memory (coefficients)";
@@ -1283,6 +1595,12 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
   float* F = buf<float>(w, B_FW);    // fp32 working layers (ping-pong per virtual node)
   f2* Cf = buf<f2>(w, B_CF);
   const int K = d.K, L0 = K, L1 = d.nz - 1 - K;   // middle layer, chain lengths
+  std::vector<InvOp> inv_ops[2];
+  if (recursive)
+    for (int plane = 0; plane < 2; ++plane)
+      if (const char* m = build_inversion(d, V, plane, F, Fr, buf<float>(w, B_AOP), buf<float>(w, B_BOP), lv,
+                                          inv_ops[plane]))
+        return m;
   // The launches of the factorisation (both streams).  Without kernel timing
   // they are captured once into a CUDA graph (node priorities kept, so the
   // lookahead chain still goes first) and replayed while the shape, the
@@ -1308,7 +1626,8 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
       const int k0 = kp * kPanel, bw = std::min(kPanel, d.n - k0), q = kp & 1;
       prof::begin(st, prof::PINV);
       prof::add_work(prof::PINV, 8.0 * kPanel * kPanel * kPanel * nv);
-      k_mx_pinv<kPinvRpt><<<nv, kPanel * (kPanel / kPinvRpt), 0, st>>>(d, ch.wplane, k0, bw, F, Pv[q], status);
+      k_mx_pinv<kPinvRpt><<<nv, kPanel * (kPanel / kPinvRpt), 0, st>>>(d, ch.wplane, k0, bw, F, Pv[q], status,
+                                                                      LeafOut{});
       prof::end(st, prof::PINV);
       prof::begin(st, prof::PANEL_T);
       prof::add_work(prof::PANEL_T, 8.0 * d.n * kPanel * kPanel * nv);
@@ -1353,8 +1672,32 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
       prof::count_launch();
       return err;
     };
+    // the recursive inversion of the complements of the nv virtual nodes (plane ch.wplane)
+    auto invert = [&](const Chains& ch, int nv) -> const char* {
+      for (const InvOp& op : inv_ops[ch.wplane]) {
+        if (op.leaf) {
+          prof::begin(s, prof::PINV);
+          prof::add_work(prof::PINV, op.flops * nv);
+          k_mx_pinv<kPinvRpt><<<nv, kPanel * (kPanel / kPinvRpt), 0, s>>>(
+              d, ch.wplane, op.off, op.s, F, nullptr, status, LeafOut{F, op.fin ? Fr : nullptr, ch, d.nz});
+          prof::end(s, prof::PINV);
+        } else {
+          InvEpi epi = op.epi;
+          epi.ch = ch;
+          prof::begin(s, prof::SWEEP_GEMM);
+          prof::add_work(prof::SWEEP_GEMM, op.flops * nv);
+          const cudaError_t err =
+              launch_cg(s, dim3(cdiv(op.N, kInvBN), cdiv(op.M, tc::kBlockM), nv), op.m, op.geo, epi, status);
+          prof::end(s, prof::SWEEP_GEMM);
+          if (err != cudaSuccess) return "tcgen05 inversion launch failed";
+        }
+        prof::count_launch();
+      }
+      return nullptr;
+    };
     // the block sweep of the complements of the nv virtual nodes (plane ch.wplane)
     auto sweep = [&](const Chains& ch, int nv) -> const char* {
+      if (recursive) return invert(ch, nv);
       panel(s, ch, nv, 0);
       for (int kp = 0; kp < npan; ++kp) {
         if (kp + 1 < npan) {
@@ -1427,7 +1770,8 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
     } else {
       if (w.factor_graph) cudaGraphExecDestroy(w.factor_graph);
       w.factor_graph = nullptr;
-      if (tc_attr<128, kWideStages, SweepEpiTma>() || tc_attr<128, 4, SweepEpiTma>() || tc_attr<128, 2, SweepEpi>())
+      if (tc_attr<128, kWideStages, SweepEpiTma>() || tc_attr<128, 4, SweepEpiTma>() || tc_attr<128, 2, SweepEpi>() ||
+          cg_attr<InvEpi>())
         return "tcgen05 sweep-update attribute rejected";
       cudaGraph_t graph = nullptr;
       cudaGraphExec_t exec = nullptr;

@@ -395,5 +395,148 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched complex TF32 GEMM on row-split fp32 blocks (real parts of a row,
+// then its imaginary parts):
+//   C_b (M x N complex) = U_b V_b^T,   C[i, j] = sum_k U[i, k] V[j, k],
+// with U and V each given by two 3-D tensor maps (real and imaginary part;
+// x: column k of the block, y: row, z: batch plane) whose extents end at the
+// block, so that TMA fills the ragged edges of every tile with zeros.  Per
+// K-block the four parts are staged in 128-byte-swizzled shared memory and
+// one thread issues four tcgen05.mma.kind::tf32 per 8-wide K step into three
+// TMEM accumulators
+//   rr = Ur Vr^T,   ii = Ui Vi^T,   ri = Ur Vi^T + Ui Vr^T,
+// so that C = (rr - ii) + i ri (no embedded copy of either operand).  Warp
+// roles, bounded waits and the TMEM release on abort as in k_tc_gemm; the
+// epilogue is epi(b, tm, tn, row, lane_taddr) and reads C through cload16.
+template <int BN, int STAGES>
+struct CSmem {
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "complex tile width");
+  static constexpr int kUBytes = kBlockM * kBlockK * 4;   // 16 KB per part
+  static constexpr int kVBytes = BN * kBlockK * 4;
+  static constexpr int kStageBytes = 2 * kUBytes + 2 * kVBytes;
+  static constexpr int kTmemCols = 3 * BN <= 64 ? 64 : (3 * BN <= 128 ? 128 : (3 * BN <= 256 ? 256 : 512));
+  static constexpr size_t kPipeBytes = (size_t)STAGES * kStageBytes;
+  static constexpr size_t kBytes = 1024 /*align slack*/ + kPipeBytes + 256;
+};
+
+// CTA (tn, tm, b) reads U rows tm*128.. at plane b*uz_mul + uz_add and V rows
+// tn*BN.. at plane b*vz_mul + vz_add, nk K-blocks of 32 columns.
+struct CGeom {
+  int nk;
+  int uz_mul, uz_add;
+  int vz_mul, vz_add;
+};
+
+// C[i, tn*BN + c0 + t] (t < 16) of this thread's row: real and imaginary parts.
+template <int BN>
+__device__ __forceinline__ void cload16(uint32_t taddr, int c0, float* re, float* im) {
+  float ii[16];
+  tmem_ld16(taddr + c0, re);
+  tmem_ld16(taddr + BN + c0, ii);
+  tmem_ld16(taddr + 2 * BN + c0, im);
+#pragma unroll
+  for (int t = 0; t < 16; ++t) re[t] -= ii[t];
+}
+
+template <int BN, int STAGES, class Epi>
+__global__ void __launch_bounds__(kThreads)
+    k_cgemm(const __grid_constant__ CUtensorMap mUr, const __grid_constant__ CUtensorMap mUi,
+            const __grid_constant__ CUtensorMap mVr, const __grid_constant__ CUtensorMap mVi, CGeom geo,
+            const __grid_constant__ Epi epi, int* status) {
+  using S = CSmem<BN, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::kPipeBytes);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tfull + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int b = blockIdx.z, tm = blockIdx.y, tn = blockIdx.x;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(tfull, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, S::kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const int uz = b * geo.uz_mul + geo.uz_add, vz = b * geo.vz_mul + geo.vz_add;
+      int issued = 0;
+      for (int kb = 0; kb < geo.nk; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (kb >= STAGES && !mbar_wait(&empty[s], ph ^ 1, status, abort_flag)) break;
+        uint8_t* st = smem + (size_t)s * S::kStageBytes;
+        mbar_arrive_expect_tx(&full[s], S::kStageBytes);
+        tma_load_3d(st, &mUr, &full[s], kb * kBlockK, tm * kBlockM, uz);
+        tma_load_3d(st + S::kUBytes, &mUi, &full[s], kb * kBlockK, tm * kBlockM, uz);
+        tma_load_3d(st + 2 * S::kUBytes, &mVr, &full[s], kb * kBlockK, tn * BN, vz);
+        tma_load_3d(st + 2 * S::kUBytes + S::kVBytes, &mVi, &full[s], kb * kBlockK, tn * BN, vz);
+        issued = kb + 1;
+      }
+      if (*abort_flag) {
+        // drain: wait (bounded) for the last load issued into every stage
+        for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb) {
+          for (long long it = 0; it < kWaitLimit; ++it)
+            if (mbar_try_wait(&full[kb % STAGES], (kb / STAGES) & 1)) break;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32(kBlockM, BN);
+      for (int kb = 0; kb < geo.nk; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(&full[s], ph, status, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t ur = smem_u32(smem + (size_t)s * S::kStageBytes);
+        const uint32_t ui = ur + S::kUBytes;
+        const uint32_t vr = ur + 2 * S::kUBytes;
+        const uint32_t vi = vr + S::kVBytes;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {   // four 32-byte K steps per 128-byte row
+          const uint32_t acc = (kb | kk) != 0;
+          const uint32_t o = kk * 32;
+          mma_tf32(tmem, sdesc_sw128(ur + o), sdesc_sw128(vr + o), idesc, acc);
+          mma_tf32(tmem + BN, sdesc_sw128(ui + o), sdesc_sw128(vi + o), idesc, acc);
+          mma_tf32(tmem + 2 * BN, sdesc_sw128(ur + o), sdesc_sw128(vi + o), idesc, acc);
+          mma_tf32(tmem + 2 * BN, sdesc_sw128(ui + o), sdesc_sw128(vr + o), idesc, 1u);
+        }
+        mma_commit(&empty[s]);
+      }
+      // always signal: the epilogue (and the TMEM release) wait for every
+      // issued MMA to finish, also on the abort path
+      mma_commit(tfull);
+    }
+  } else {
+    const int q = warp % 4;
+    const int row = q * 32 + lane;
+    mbar_wait(tfull, 0, status, abort_flag);
+    tc_fence_after();
+    epilogue_sync();   // one abort decision for the whole epilogue group
+    if (!*abort_flag) epi(b, tm, tn, row, tmem + (static_cast<uint32_t>(q * 32) << 16));
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, S::kTmemCols);
+  }
+}
+
 }  // namespace tc
 }  // namespace feast
