@@ -167,11 +167,10 @@ __global__ void __launch_bounds__(256) k_mx_schur1(Dims d, Chains ch, const f2* 
 // first layer).  middle: v < Ne only; the middle layer takes both chains'
 // contributions, C0 T1[v] + C1 T1[v + Ne] (the second when has_prev1).
 // Row p's coefficients are loaded first and the T1 rows of all taps are read
-// unconditionally (tap_offset), so that the loads overlap.  round_tf32: S is
-// stored rounded to TF32 (nearest), the recursive inversion's operand.
+// unconditionally (tap_offset), so that the loads overlap.
 __global__ void __launch_bounds__(256) k_mx_schur2(Dims d, Chains ch, int has_prev, int middle, int has_prev1,
                                                    const f2* __restrict__ Cf, const float* __restrict__ T1,
-                                                   float* __restrict__ F, int round_tf32) {
+                                                   float* __restrict__ F) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y, v = blockIdx.z;
   if (q >= d.n) return;
@@ -195,8 +194,8 @@ __global__ void __launch_bounds__(256) k_mx_schur2(Dims d, Chains ch, int has_pr
   if (has_prev) add(v, prev_slot(c));
   if (middle && has_prev1) add(v + ch.Ne, prev_slot(1));
   float* out = F + (((long long)v * 2 + ch.wplane) * d.n + p) * d.ldF;
-  out[q] = round_tf32 ? tc::to_tf32(acc.x) : acc.x;
-  out[d.n + q] = round_tf32 ? tc::to_tf32(acc.y) : acc.y;
+  out[q] = acc.x;
+  out[d.n + q] = acc.y;
 }
 
 // ------------------------------------------------------------------ panel
@@ -342,12 +341,11 @@ __global__ void __launch_bounds__(kPanel * (kPanel / RPT)) k_mx_pinv(Dims d, int
       const int i = h * RPT + a;
       if (i < bw && j < bw) {
         const long long at = (long long)(k0 + i) * d.ldF + k0 + j;
-        const float xr = tc::to_tf32(v[a].x), xi = tc::to_tf32(v[a].y);
-        Fw[at] = xr;
-        Fw[at + n] = xi;
+        Fw[at] = v[a].x;
+        Fw[at + n] = v[a].y;
         if (Frw) {
-          Frw[at] = xr;
-          Frw[at + n] = xi;
+          Frw[at] = tc::to_tf32(v[a].x);
+          Frw[at + n] = tc::to_tf32(v[a].y);
         }
       }
     }
@@ -760,10 +758,8 @@ struct SolveEpi {
 // virtual nodes; its epilogue writes C transposed (lanes are rows of C, so
 // the stores of a warp are contiguous) and/or as is, adds C^T into a
 // symmetric block instead, and copies the blocks that no later step changes
-// into the TF32 solve operand Fr.  Every value it stores (and the complement
-// S it starts from) is rounded to TF32 to nearest: the tensor cores would
-// otherwise drop the low mantissa bits of the fp32 operands, a biased error
-// that adds up coherently over the long K of the large products.
+// into the TF32 solve operand Fr.  Blocks stay fp32 in F and the workspaces;
+// the GEMM rounds its staged operands to TF32 (nearest).
 
 // Destination of a row-split block: element (r, c) of batch b at
 // base + b bstride + r ld + c (real part; imaginary part imoff further).
@@ -814,24 +810,17 @@ struct InvEpi {
               xr += p[0];
               xi += p[t.imoff];
             }
-            xr = tc::to_tf32(xr);
-            xi = tc::to_tf32(xi);
             p[0] = xr;
             p[t.imoff] = xi;
             if (frp && fr_t >= 0) {
               float* q = frp + fr_t + (long long)j * ld_fr + i;
-              q[0] = xr;
-              q[imoff_fr] = xi;
+              q[0] = tc::to_tf32(xr);
+              q[imoff_fr] = tc::to_tf32(xi);
             }
           }
         }
       }
       if (r.base) {
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          re[u] = tc::to_tf32(re[u]);
-          im[u] = tc::to_tf32(im[u]);
-        }
         float* p = r.base + b * r.bstride + (long long)i * r.ld + j0;
         float* q = (frp && fr_r >= 0) ? frp + fr_r + (long long)i * ld_fr + j0 : nullptr;
         const uintptr_t al = reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(p + r.imoff) |
@@ -842,8 +831,10 @@ struct InvEpi {
             *reinterpret_cast<float4*>(p + u) = make_float4(re[u], re[u + 1], re[u + 2], re[u + 3]);
             *reinterpret_cast<float4*>(p + r.imoff + u) = make_float4(im[u], im[u + 1], im[u + 2], im[u + 3]);
             if (q) {
-              *reinterpret_cast<float4*>(q + u) = make_float4(re[u], re[u + 1], re[u + 2], re[u + 3]);
-              *reinterpret_cast<float4*>(q + imoff_fr + u) = make_float4(im[u], im[u + 1], im[u + 2], im[u + 3]);
+              *reinterpret_cast<float4*>(q + u) = make_float4(tc::to_tf32(re[u]), tc::to_tf32(re[u + 1]),
+                                                              tc::to_tf32(re[u + 2]), tc::to_tf32(re[u + 3]));
+              *reinterpret_cast<float4*>(q + imoff_fr + u) = make_float4(
+                  tc::to_tf32(im[u]), tc::to_tf32(im[u + 1]), tc::to_tf32(im[u + 2]), tc::to_tf32(im[u + 3]));
             }
           }
         } else {
@@ -853,8 +844,8 @@ struct InvEpi {
               p[u] = re[u];
               p[r.imoff + u] = im[u];
               if (q) {
-                q[u] = re[u];
-                q[imoff_fr + u] = im[u];
+                q[u] = tc::to_tf32(re[u]);
+                q[imoff_fr + u] = tc::to_tf32(im[u]);
               }
             }
           }
@@ -1736,8 +1727,7 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
       prof::add_work(prof::SCHUR, (t > 0 ? 144.0 : 0.0) * d.n * (double)d.n * nv);
       if (t > 0)
         k_mx_schur1<<<dim3(sgrid.x, cdiv(d.n, kSchurRows), nv), 256, 0, s>>>(d, ch, Cf, F, buf<float>(w, B_T1));
-      k_mx_schur2<<<dim3(sgrid.x, sgrid.y, nv), 256, 0, s>>>(d, ch, t > 0, 0, 0, Cf, buf<float>(w, B_T1), F,
-                                                             recursive ? 1 : 0);
+      k_mx_schur2<<<dim3(sgrid.x, sgrid.y, nv), 256, 0, s>>>(d, ch, t > 0, 0, 0, Cf, buf<float>(w, B_T1), F);
       prof::end(s, prof::SCHUR);
       prof::count_launch(t > 0 ? 2 : 1);
       if (const char* m = sweep(ch, nv)) return m;
@@ -1750,8 +1740,7 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
       if (L0 > 0)
         k_mx_schur1<<<dim3(sgrid.x, cdiv(d.n, kSchurRows), L1 > 0 ? V : Ne), 256, 0, s>>>(d, ch, Cf, F,
                                                                                          buf<float>(w, B_T1));
-      k_mx_schur2<<<dim3(sgrid.x, sgrid.y, Ne), 256, 0, s>>>(d, ch, L0 > 0, 1, L1 > 0, Cf, buf<float>(w, B_T1), F,
-                                                             recursive ? 1 : 0);
+      k_mx_schur2<<<dim3(sgrid.x, sgrid.y, Ne), 256, 0, s>>>(d, ch, L0 > 0, 1, L1 > 0, Cf, buf<float>(w, B_T1), F);
       prof::end(s, prof::SCHUR);
       prof::count_launch(L0 > 0 ? 2 : 1);
       if (const char* m = sweep(ch, Ne)) return m;

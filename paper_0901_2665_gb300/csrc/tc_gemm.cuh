@@ -44,6 +44,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -407,9 +411,13 @@ __global__ void __launch_bounds__(kThreads)
 // one thread issues four tcgen05.mma.kind::tf32 per 8-wide K step into three
 // TMEM accumulators
 //   rr = Ur Vr^T,   ii = Ui Vi^T,   ri = Ur Vi^T + Ui Vr^T,
-// so that C = (rr - ii) + i ri (no embedded copy of either operand).  Warp
-// roles, bounded waits and the TMEM release on abort as in k_tc_gemm; the
-// epilogue is epi(b, tm, tn, row, lane_taddr) and reads C through cload16.
+// so that C = (rr - ii) + i ri (no embedded copy of either operand).  The
+// operands are fp32 in memory; the four epilogue warps, idle during the main
+// loop, round each staged K-block to TF32 (nearest) in shared memory before
+// the MMA reads it -- the tensor cores would otherwise drop the low mantissa
+// bits, a biased error that adds up coherently over a long K.  Warp roles,
+// bounded waits and the TMEM release on abort as in k_tc_gemm; the epilogue
+// is epi(b, tm, tn, row, lane_taddr) and reads C through cload16.
 template <int BN, int STAGES>
 struct CSmem {
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "complex tile width");
@@ -450,7 +458,8 @@ __global__ void __launch_bounds__(kThreads)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::kPipeBytes);
   uint64_t* empty = full + STAGES;
-  uint64_t* tfull = empty + STAGES;
+  uint64_t* rounded = empty + STAGES;   // stage rounded to TF32 (128 arrivals)
+  uint64_t* tfull = rounded + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tfull + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -460,6 +469,7 @@ __global__ void __launch_bounds__(kThreads)
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      mbar_init(&rounded[s], 4 * 32);
     }
     mbar_init(tfull, 1);
     *abort_flag = 0;
@@ -501,7 +511,7 @@ __global__ void __launch_bounds__(kThreads)
       for (int kb = 0; kb < geo.nk; ++kb) {
         const int s = kb % STAGES;
         const uint32_t ph = (kb / STAGES) & 1;
-        if (!mbar_wait(&full[s], ph, status, abort_flag)) break;
+        if (!mbar_wait(&rounded[s], ph, status, abort_flag)) break;
         tc_fence_after();
         const uint32_t ur = smem_u32(smem + (size_t)s * S::kStageBytes);
         const uint32_t ui = ur + S::kUBytes;
@@ -525,6 +535,24 @@ __global__ void __launch_bounds__(kThreads)
   } else {
     const int q = warp % 4;
     const int row = q * 32 + lane;
+    const int et = static_cast<int>(threadIdx.x) - 64;   // 0..127
+    // round every staged K-block to TF32 in place, then release it to the MMA
+    for (int kb = 0; kb < geo.nk; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&full[s], (kb / STAGES) & 1, status, abort_flag)) break;
+      float4* st = reinterpret_cast<float4*>(smem + (size_t)s * S::kStageBytes);
+#pragma unroll 4
+      for (int x = et; x < S::kStageBytes / 16; x += 128) {
+        float4 v = st[x];
+        v.x = to_tf32(v.x);
+        v.y = to_tf32(v.y);
+        v.z = to_tf32(v.z);
+        v.w = to_tf32(v.w);
+        st[x] = v;
+      }
+      fence_proxy_async_smem();   // generic-proxy writes -> the tensor cores' reads
+      mbar_arrive(&rounded[s]);
+    }
     mbar_wait(tfull, 0, status, abort_flag);
     tc_fence_after();
     epilogue_sync();   // one abort decision for the whole epilogue group
