@@ -353,12 +353,17 @@ __global__ void __launch_bounds__(kPanel * (kPanel / RPT)) k_mx_pinv(Dims d, int
   if (tid == 0 && bad) atomicExch(status, (int)DEV_PIVOT);
 }
 
-#ifndef FEAST_FACTOR_PANEL_SWEEP
-#define FEAST_FACTOR_PANEL_SWEEP 0
+#ifndef FEAST_FACTOR_RECURSIVE
+#define FEAST_FACTOR_RECURSIVE 0
 #endif
-// 1: invert the layer complements by the 64-column panel sweep even where the
-// recursive block inversion applies
-constexpr bool kFactorPanelSweep = FEAST_FACTOR_PANEL_SWEEP != 0;
+// 1: invert the layer complements by the recursive block inversion where it
+// applies; 0 (default): the 64-column panel sweep.  Measured on the
+// 32x32x400 pencil the recursion's products (long K, operands such as
+// Abar B that carry no cancellation from earlier panels) lose accuracy
+// against the panel sweep's rank-64 updates of partially eliminated columns:
+// the refinement then needs about a third more steps, more than the factor
+// saves.
+constexpr bool kFactorPanelSweep = FEAST_FACTOR_RECURSIVE == 0;
 
 #ifndef FEAST_WIDE_STAGES
 #define FEAST_WIDE_STAGES 1
