@@ -108,6 +108,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed solves of the plain FP64 GPU path")
     ap.add_argument("--fp64-warmup", type=int, default=1, help="untimed solves of the plain FP64 GPU path")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-forms", action="store_true",
+                    help="single workload: do not add the one-step batched-64 and Hermitian lines ('forms')")
     ap.add_argument("--profile-timed", action="store_true",
                     help="time kernel classes inside the timed steps (default: in one extra step after them)")
     ap.add_argument("--no-ir-early", action="store_true",
@@ -518,6 +520,11 @@ def run_ours(args):
         "e2e": e2e, "fp64_gpu": fp64,
         "cpu_baseline": cpu_baseline_obj(cpu) if cpu and "value" in cpu else cpu,
     }
+    if world == 1 and not args.skip_forms and args.layers == 400 and args.precision == "mixed":
+        try:
+            line["forms"] = run_forms(args)
+        except Exception as ex:  # context only: report why it is missing
+            line["forms"] = {"error": str(ex)[:300]}
     return line
 
 
@@ -605,6 +612,11 @@ def run_batched(args):
         torch.cuda.synchronize()
         return check(mf, idx) / (time.perf_counter() - t0), kinfo
 
+    if getattr(args, "brief", False):
+        h.close()
+        return {"value": value, "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": t_max / args.steps, "valid": total == wanted, "eigenpairs_per_step": sum(Ms),
+                "gpu_launches": int(launches), "instances": len(ops)}
     seq_value, _ = sequential(h, range(len(ops)))
     sample = [0, 16, 32, 48]
     hp = F.Handle(precision=F.FEAST_PREC_MIXED, seed=Y_SEED, stream=stream.cuda_stream, profile=True)
@@ -643,6 +655,25 @@ def run_batched(args):
                         "what": "plain FP64 GPU path, sequential"},
         "roofline": roof, "gpu_launches": int(launches), "clocks": clk, "shapes": sides,
     }
+
+
+def run_forms(args):
+    """One warm-up and one timed step of two other forms on the same GPU, for
+    the default line: the batched form (64 uneven instances, one
+    feast_solve_batched call) and the Hermitian form (Eq. 12).  Their full
+    lines come from --workload batched64 / hermitian."""
+    out = {}
+    brief = argparse.Namespace(**vars(args))
+    brief.steps, brief.warmup, brief.skip_cpu, brief.skip_fp64, brief.brief = 1, 1, True, True, True
+    t0 = time.perf_counter()
+    out["batched64"] = run_batched(brief)
+    out["batched64"]["wall_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hl = run_hermitian(brief)
+    out["hermitian"] = {k: hl[k] for k in ("value", "unit", "ms_per_step", "valid", "m_found", "loops", "resid_max",
+                                           "eig_err_vs_oracle_dense", "gpu_launches")}
+    out["hermitian"]["wall_s"] = time.perf_counter() - t0
+    return out
 
 
 def _single_setup(dev, torch, F, workloads, seed=0, potential=None):

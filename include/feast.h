@@ -342,6 +342,21 @@ feast_status feast_predict_Y(feast_mlp* net, const float* features, int nx, int 
                              double* Y);
 
 /*
+ * Self-test of the bounded device waits.  Every spin-wait in the library's
+ * pipelined kernels (mbarrier waits of the TMA/tcgen05 GEMMs) gives up after
+ * a fixed number of polls, records a timeout in the handle's status word,
+ * releases what it holds and returns, so that the CUDA context stays usable.
+ * This call runs that give-up path on purpose: one thread waits, through the
+ * same bounded-wait helper, on an mbarrier that nothing completes, with a
+ * limit of `polls` polls (1 <= polls <= 2^26), on the handle's stream.
+ *
+ * Returns FEAST_ERR_TIMEOUT when the wait ran out and the kernel returned
+ * (the expected outcome), FEAST_ERR_ARG for polls out of range (nothing is
+ * launched), FEAST_ERR_CUDA on a launch error.  The handle stays usable.
+ */
+feast_status feast_selftest_wait_timeout(feast_handle* h, long long polls);
+
+/*
  * Allocation-free reduced eigensolve.  The paper has no counterpart: this is
  * a library convenience.  It computes exactly what feast_reduced_eig computes
  * (same kernel), for callers that cannot call cudaMalloc: code that must keep
@@ -357,8 +372,7 @@ feast_status feast_predict_Y(feast_mlp* net, const float* features, int nx, int 
  * exits.  Nothing is allocated or freed per call.
  *
  * The first call on a device, with that device current, looks up the array's
- * device address (cudaGetSymbolAddress) and caches it; make that first call
- * before any stream capture.  Work is ordered on cuda_stream (NULL = legacy
+ * device address (cudaGetSymbolAddress) and caches it.  Work is ordered on cuda_stream (NULL = legacy
  * default stream) and the call synchronises that stream to read the status.
  * Every call shares the one array, which keeps the last call's contents (the
  * status word is cleared at the start of each call): calls whose work overlaps

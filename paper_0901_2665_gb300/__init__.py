@@ -49,6 +49,7 @@ EXPORTED = [
     "feast_default_options", "feast_init", "feast_destroy", "feast_last_error", "feast_get_info",
     "feast_solve", "feast_solve_hermitian", "feast_contour", "feast_stencil_apply", "feast_node_solve", "feast_quadrature",
     "feast_reduced_eig", "feast_rayleigh_ritz", "feast_residuals", "feast_reduced_eig_noalloc",
+    "feast_selftest_wait_timeout",
     "feast_solve_batched", "feast_mlp_create", "feast_mlp_destroy", "feast_mlp_set_layer", "feast_mlp_get_layer",
     "feast_mlp_forward", "feast_mlp_train_step", "feast_sine_expand", "feast_sine_project", "feast_predict_Y",
 ]
@@ -102,6 +103,7 @@ _lib.feast_solve_hermitian.argtypes = [_vp, ctypes.POINTER(feast_operator), _d, 
                                        ctypes.POINTER(_i), ctypes.POINTER(_i)]
 _lib.feast_contour.argtypes = [_d, _d, _i, _vp, _vp, _vp, _vp, _vp]
 _lib.feast_stencil_apply.argtypes = [_vp, _i, _i, _i, _vp, _vp, _vp, _i]
+_lib.feast_selftest_wait_timeout.argtypes = [_vp, ctypes.c_longlong]
 _lib.feast_node_solve.argtypes = [_vp, ctypes.POINTER(feast_operator), _d, _d, _vp, _vp, _i, _i]
 _lib.feast_quadrature.argtypes = [_vp, ctypes.POINTER(feast_operator), _d, _d, _i, _vp, _vp, _i, _i]
 _lib.feast_reduced_eig.argtypes = [_vp, _vp, _vp, _i, _vp, _vp]
@@ -263,6 +265,12 @@ class Handle:
         if raise_on_error:
             self._check(st, "feast_solve_batched")
         return st, mf, lp, sts
+
+    def feast_selftest_wait_timeout(self, polls: int):
+        """Runs the give-up path of the bounded device waits (a wait on an
+        mbarrier nothing completes, limited to `polls` polls); raises
+        FeastError(FEAST_ERR_TIMEOUT) as designed."""
+        self._check(_lib.feast_selftest_wait_timeout(self._h, int(polls)), "feast_selftest_wait_timeout")
 
     def feast_stencil_apply(self, nx, ny, nz, C27, X, Y, k):
         self._check(_lib.feast_stencil_apply(self._h, nx, ny, nz, _ptr(C27), _ptr(X), _ptr(Y), int(k)),

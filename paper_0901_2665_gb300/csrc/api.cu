@@ -447,6 +447,22 @@ feast_status feast_contour(double lmin, double lmax, int Ne, double* x, double* 
   return FEAST_OK;
 }
 
+feast_status feast_selftest_wait_timeout(feast_handle* h, long long polls) {
+  if (!h) return FEAST_ERR_ARG;
+  return guarded(h, [&] {
+    if (polls < 1 || polls > kSelftestMaxPolls) fail(FEAST_ERR_ARG, "polls must be in [1, 2^26]");
+    reset_status(h);
+    selftest_wait(h->stream, polls, h->status.as<int>());
+    ck(cudaGetLastError(), "self-test launch");
+    int st = 0;
+    ck(cudaMemcpyAsync(&st, h->status.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status");
+    ck(cudaStreamSynchronize(h->stream), "sync");
+    reset_status(h);   // the handle's later calls start from a clean status word
+    if (st == DEV_TIMEOUT) fail(FEAST_ERR_TIMEOUT, "bounded device wait gave up (self-test)");
+    if (st != DEV_OK) fail(FEAST_ERR_CUDA, "unexpected device status " + std::to_string(st));
+  });
+}
+
 feast_status feast_stencil_apply(feast_handle* h, int nx, int ny, int nz, const double* C27, const double* X,
                                  double* Y, int k) {
   if (!h) return FEAST_ERR_ARG;

@@ -2123,6 +2123,25 @@ static const char* solve_prepare(cudaStream_t s, Grid g, int Ne, int k, MixedWor
   return nullptr;
 }
 
+namespace {
+__global__ void k_selftest_wait(long long polls, int* status) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);   // one arrival completes phase 0: none comes
+    abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) tc::mbar_wait_limit(&bar, 0, status, &abort_flag, polls);
+}
+}  // namespace
+
+void selftest_wait(cudaStream_t s, long long polls, int* status) {
+  k_selftest_wait<<<1, 32, 0, s>>>(polls, status);
+  prof::count_launch();
+}
+
 const char* mixed_solve_prepare(cudaStream_t s, Grid g, int Ne, int k, MixedWork& w, int* status) {
   Dims d;
   return solve_prepare(s, g, Ne, k, w, status, &d);

@@ -115,4 +115,11 @@ const char* mixed_loop(cudaStream_t s, Grid g, int Ne, const cplx* Z, const doub
                        int* status);
 extern const char* const kNotCaptured;
 
+// Self-test of the bounded waits of the pipelined kernels: one thread waits,
+// through the same bounded-wait helper, on an mbarrier that nothing
+// completes and gives up after `polls` polls (1 .. kSelftestMaxPolls),
+// recording DEV_TIMEOUT in *status; the kernel then returns normally.
+constexpr long long kSelftestMaxPolls = 1LL << 26;
+void selftest_wait(cudaStream_t s, long long polls, int* status);
+
 }  // namespace feast

@@ -60,16 +60,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: false (and DEV_TIMEOUT recorded) when the limit is reached or
-// another role of the CTA already gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, volatile int* abort_flag) {
-  for (long long it = 0; it < kWaitLimit; ++it) {
+// Bounded wait: false (and DEV_TIMEOUT recorded) when `limit` polls are
+// used up or another role of the CTA already gave up.
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t* bar, uint32_t parity, int* status,
+                                                volatile int* abort_flag, long long limit) {
+  for (long long it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 1023) == 1023 && *abort_flag) return false;
   }
   *abort_flag = 1;
   atomicExch(status, (int)DEV_TIMEOUT);
   return false;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, volatile int* abort_flag) {
+  return mbar_wait_limit(bar, parity, status, abort_flag, kWaitLimit);
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
