@@ -1654,12 +1654,13 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
         return "tensor map (working layers) rejected";
     }
     // trailing update of panel kp over the column tiles [base, base + count) except `skip`
-    auto update = [&](const Chains& ch, int nv, int kp, int base, int count, int skip) -> cudaError_t {
+    auto update = [&](cudaStream_t st, const Chains& ch, int nv, int kp, int base, int count,
+                      int skip) -> cudaError_t {
       const int k0 = kp * kPanel, bw = std::min(kPanel, d.n - k0), q = kp & 1;
       const bool last = kp == npan - 1;
       tc::Geom geo{0, d.n, 0, d.nblk64 * 128, (2 * kPanel) / tc::kBlockK, base, skip};
       const int cls = base > 0 ? prof::SWEEP_NARROW : prof::SWEEP_GEMM;   // the narrow update starts at tile kp+1
-      prof::begin(s, cls);
+      prof::begin(st, cls);
       prof::add_work(cls, 8.0 * d.n * (64.0 * count) * bw * nv);
       cudaError_t err;
       const dim3 grid(count, cdiv(d.n, 128), nv);
@@ -1667,14 +1668,14 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
         SweepEpiTma epi{mapF, mapFr, ch.wplane, ch, d.nz, d.n, k0, bw, last ? 1 : 0, Tc[q], Pv[q]};
         // the narrow update (one column tile, few CTAs, on the critical path)
         // pipelines its K-blocks; the wide one keeps two CTAs per SM instead
-        err = count == 1 ? launch_tc<128, 4>(s, grid, tmA[q], tmB[q], geo, epi, status)
-                         : launch_tc<128, kWideStages>(s, grid, tmA[q], tmB[q], geo, epi, status);
+        err = count == 1 ? launch_tc<128, 4>(st, grid, tmA[q], tmB[q], geo, epi, status)
+                         : launch_tc<128, kWideStages>(st, grid, tmA[q], tmB[q], geo, epi, status);
       } else {
         SweepEpi epi{F + (long long)ch.wplane * d.n * d.ldF, sF, last ? Fr : nullptr, sFr, d.ldF, d.n, k0, bw,
                      Tc[q], Pv[q], ch};
-        err = launch_tc<128, 2>(s, grid, tmA[q], tmB[q], geo, epi, status);
+        err = launch_tc<128, 2>(st, grid, tmA[q], tmB[q], geo, epi, status);
       }
-      prof::end(s, cls);
+      prof::end(st, cls);
       prof::count_launch();
       return err;
     };
@@ -1707,18 +1708,22 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
       panel(s, ch, nv, 0);
       for (int kp = 0; kp < npan; ++kp) {
         if (kp + 1 < npan) {
-          // narrow update: the next panel's columns first ...
-          if (update(ch, nv, kp, kp + 1, 1, -1) != cudaSuccess) return "tcgen05 sweep-update launch failed";
+          // fork: the previous wide update and this panel's inverse and
+          // product (joined into s below) precede both updates of panel kp
           cudaEventRecord(w.ev_narrow, s);
-          // ... so its inversion and product overlap the wide update
           cudaStreamWaitEvent(s2, w.ev_narrow, 0);
+          // the lookahead chain on the side stream: the narrow update of the
+          // next panel's columns, then that panel's inverse and product ...
+          if (update(s2, ch, nv, kp, kp + 1, 1, -1) != cudaSuccess) return "tcgen05 sweep-update launch failed";
           panel(s2, ch, nv, kp + 1);
           cudaEventRecord(w.ev_side, s2);
-          if (npan > 1 && update(ch, nv, kp, 0, npan - 1, kp + 1) != cudaSuccess)
+          // ... beside the wide update of the other column tiles (disjoint
+          // tiles, the same panel operands)
+          if (npan > 1 && update(s, ch, nv, kp, 0, npan - 1, kp + 1) != cudaSuccess)
             return "tcgen05 sweep-update launch failed";
           cudaStreamWaitEvent(s, w.ev_side, 0);
         } else {
-          if (update(ch, nv, kp, 0, npan, -1) != cudaSuccess) return "tcgen05 sweep-update launch failed";
+          if (update(s, ch, nv, kp, 0, npan, -1) != cudaSuccess) return "tcgen05 sweep-update launch failed";
         }
       }
       return nullptr;
