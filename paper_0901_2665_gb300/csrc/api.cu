@@ -300,9 +300,8 @@ void solve_nodes(feast_handle* h, const OpView& op, int Ne, int precision, const
                k, Qp, h->coefd.as<cplx>());
   } else {
     MixedSolveStats st;
-    const char* msg = mixed_solve(h->stream, op.g, Ne, h->Zd.as<cplx>(), op.A27, op.B27, h->mixed, RHS, G,
-                                  reinterpret_cast<float2*>(Qp), h->coefd.as<cplx>(), k, ir_tol, h->opt.ir_max, &st,
-                                  h->status.as<int>());
+    const char* msg = mixed_solve(h->stream, op.g, Ne, h->Zd.as<cplx>(), op.A27, op.B27, h->mixed, RHS, G, Qp,
+                                  h->coefd.as<cplx>(), k, ir_tol, h->opt.ir_max, &st, h->status.as<int>());
     if (msg) fail(FEAST_ERR_CUDA, msg);
     h->info.ir_steps_max = std::max(h->info.ir_steps_max, st.steps_max);
     if (ir_tol <= h->opt.ir_tol) h->info.ir_resid_max = std::max(h->info.ir_resid_max, st.resid_max);
@@ -323,11 +322,7 @@ void node_solves_and_quadrature(feast_handle* h, const OpView& op, int Ne, int p
   }
   h->Qp.ensure(sizeof(double) * (size_t)Ne * N * k, "quadrature shares");
   solve_nodes(h, op, Ne, precision, RHS, nullptr, h->Qp.as<double>(), k, ir_tol);
-  // the mixed path keeps its shares as double-float pairs, the FP64 path in FP64
-  if (precision == FEAST_PREC_MIXED)
-    quadrature_sum_df(h->stream, N, k, Ne, h->Qp.as<float2>(), N * k, Q);
-  else
-    quadrature_sum(h->stream, N, k, Ne, h->Qp.as<double>(), N * k, Q);
+  quadrature_sum(h->stream, N, k, Ne, h->Qp.as<double>(), N * k, Q);
 }
 
 void upload_contour(feast_handle* h, const Contour& ct) {
@@ -649,7 +644,7 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
         stencil_apply(st, v.g, v.B27, h->Yb.as<double>(), N, h->RHS.as<double>(), N, M0);
       };
       hooks.quad_rr = [&](cudaStream_t st) {
-        quadrature_sum_df(st, N, M0, Ne, h->Qp.as<float2>(), N * M0, h->Q.as<double>());
+        quadrature_sum(st, N, M0, Ne, h->Qp.as<double>(), N * M0, h->Q.as<double>());
         rayleigh_ritz_dev(h, v, h->Q.as<double>(), M0, h->eps.as<double>(), h->Xb.as<double>(), nullptr, nullptr, st);
       };
       hooks.next_y = [&](cudaStream_t st) { cudaMemcpyAsync(h->Yb.p, h->Xb.p, blk, cudaMemcpyDeviceToDevice, st); };
@@ -670,7 +665,7 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
       for (int i = 0; i < 16; ++i) key[28 + i] = ptr(h->mixed.bufs[i]);
       ck(cudaEventRecord(h->ev[2], s), "event");
       const char* msg = mixed_loop(s, v.g, Ne, h->Zd.as<cplx>(), v.A27, v.B27, h->mixed, h->RHS.as<double>(),
-                                   h->Qp.as<float2>(), h->coefd.as<cplx>(), M0, lp, h->eps.as<double>(),
+                                   h->Qp.as<double>(), h->coefd.as<cplx>(), M0, lp, h->eps.as<double>(),
                                    h->loopst.as<LoopState>(), hooks, key, h->status.as<int>());
       if (msg && msg != kNotCaptured) fail(FEAST_ERR_CUDA, msg);
       if (!msg) {

@@ -685,49 +685,21 @@ struct SweepEpiTma {
   }
 };
 
-// s + Re{c x} as a double-float pair (s itself when `first` is false; 0 when
-// true), c = (crh + crl) + i (cih + cil) split into floats, x exact in fp32:
-// the leading products exact by one FMA each (Dekker), the sums by TwoSum
-// (Knuth) and a final Fast2Sum; the rounding-explicit intrinsics keep the
-// compiler from fusing the error terms away.  Relative error ~2^-47.
-__device__ __forceinline__ float2 df_share(float2 s, bool first, float crh, float crl, float cih, float cil, f2 x) {
-  const float ph = __fmul_rn(x.x, crh);
-  const float pl = __fmaf_rn(x.x, crl, __fmaf_rn(x.x, crh, -ph));
-  const float qh = __fmul_rn(x.y, cih);
-  const float ql = __fmaf_rn(x.y, cil, __fmaf_rn(x.y, cih, -qh));
-  // v = p - q
-  const float vh = __fsub_rn(ph, qh);
-  const float vb = __fsub_rn(vh, ph);
-  const float ve = __fadd_rn(__fsub_rn(ph, __fsub_rn(vh, vb)), __fsub_rn(__fmul_rn(-1.f, qh), vb));
-  const float vl = __fadd_rn(ve, __fsub_rn(pl, ql));
-  float th = vh, tl = vl;
-  if (!first) {   // t = s + v
-    th = __fadd_rn(s.x, vh);
-    const float tb = __fsub_rn(th, s.x);
-    const float te = __fadd_rn(__fsub_rn(s.x, __fsub_rn(th, tb)), __fsub_rn(vh, tb));
-    tl = __fadd_rn(te, __fadd_rn(s.y, vl));
-  }
-  const float rh = __fadd_rn(th, tl);
-  return make_float2(rh, __fsub_rn(tl, __fsub_rn(rh, th)));
-}
-
 // Solve product: out[m*ldo + p] = alpha * (S' g)[p, m] (complex64); lanes are
 // consecutive rows p, so the stores of a warp are contiguous.
 // With qp set (the backward sweep of feast_solve / feast_quadrature) the
 // epilogue also folds the layer's solution x into the node's share of the
-// quadrature sum (Eq. 15):  qp[m*ldq + p] (= or +=) Re{coef_e x},
+// quadrature sum (Eq. 15):  qp[m*ldq + p] (= or +=) Re{coef_e x}  in FP64,
 // coef_e = -(w_e/2) r e^{i theta_e}.  x of the first solve is Q_e itself and
 // x of each refinement step is its correction, so after the last step the
-// node's share is Re{coef_e Q_e}, without Q_e ever being stored.  The share
-// is a double-float pair (hi, lo): the FP64 pipe, 1/64 of the FP32 rate here,
-// would otherwise bound the epilogue (df_share).
+// node's share is Re{coef_e Q_e}, without Q_e ever being stored.
 template <int CB>
 struct SolveEpi {
   f2* out;
   long long sOut, ldo;
   int n, k;
   float alpha;
-  float2* qp = nullptr;        // per-node quadrature shares, double-float (hi, lo)
+  double* qp = nullptr;        // per-node quadrature partials
   long long sQ = 0, ldq = 0;   // node stride, column stride
   const cplx* coef = nullptr;  // Ne quadrature coefficients
   int qfirst = 0;              // 1: store (first solve), 0: accumulate (refinement)
@@ -742,30 +714,24 @@ struct SolveEpi {
   // the old shares of this thread's row, loaded while the main loop runs
   // (a refinement step reads them back)
   struct Pre {
-    float2 q[CB];
+    double q[CB];
   };
   __device__ void prefetch(int e, int tm, int tn, int row, Pre& pre) const {
     const int p = tm * tc::kBlockM + row;
     const bool rd = qp && !qfirst && p < n;
-    const float2* q = qp ? qp + base(e, sQ) : nullptr;
+    const double* q = qp ? qp + base(e, sQ) : nullptr;
 #pragma unroll
     for (int t = 0; t < CB; ++t) {
       const int m = tn * CB + t;
-      pre.q[t] = (rd && m < k) ? q[(long long)m * ldq + p] : make_float2(0.f, 0.f);
+      pre.q[t] = (rd && m < k) ? q[(long long)m * ldq + p] : 0.0;
     }
   }
   __device__ void operator()(int e, int tm, int tn, int row, uint32_t taddr, int, uint8_t*, const Pre& pre) const {
     const int p = tm * tc::kBlockM + row;
     f2* o = out + base(e, sOut);
-    float2* q = qp ? qp + base(e, sQ) : nullptr;
-    float crh = 0.f, crl = 0.f, cih = 0.f, cil = 0.f;   // coef_e split into float pairs
-    if (qp) {
-      const cplx ce = coef[node_of(ch, e)];
-      crh = (float)ce.re;
-      crl = (float)(ce.re - (double)crh);
-      cih = (float)ce.im;
-      cil = (float)(ce.im - (double)cih);
-    }
+    double* q = qp ? qp + base(e, sQ) : nullptr;
+    cplx ce{0.0, 0.0};
+    if (qp) ce = coef[node_of(ch, e)];
 #pragma unroll
     for (int c0 = 0; c0 < CB; c0 += 16) {
       float re[16], im[16];
@@ -778,7 +744,7 @@ struct SolveEpi {
         if (c0 + t < CB && m < k) {
           const f2 x{alpha * re[t], alpha * im[t]};
           o[(long long)m * ldo + p] = x;
-          if (q) q[(long long)m * ldq + p] = df_share(pre.q[c0 + t], qfirst != 0, crh, crl, cih, cil, x);
+          if (q) q[(long long)m * ldq + p] = pre.q[c0 + t] + (ce.re * (double)x.x - ce.im * (double)x.y);
         }
       }
     }
@@ -1853,7 +1819,7 @@ namespace {
 // and whether this sweep stores (the first solve) or accumulates (a
 // refinement step).  qp == nullptr: no folding.
 struct QuadOut {
-  float2* qp;   // double-float shares
+  double* qp;
   const cplx* coef;
   int first;
 };
@@ -2181,37 +2147,13 @@ void selftest_wait(cudaStream_t s, long long polls, int* status) {
   prof::count_launch();
 }
 
-namespace {
-// Q = sum_e (hi_e + lo_e) over the nodes in order e = 1..Ne (FP64), from the
-// double-float shares; the conversions run on the integer pipe.
-__global__ void k_quadrature_node_sum_df(long long total, int Ne, const float2* __restrict__ Qp, long long sQ,
-                                         double* __restrict__ Q) {
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int e = 0; e < Ne; ++e) {
-      const float2 v = Qp[e * sQ + t];
-      acc += f32_to_f64(v.x) + f32_to_f64(v.y);
-    }
-    Q[t] = acc;
-  }
-}
-}  // namespace
-
-void quadrature_sum_df(cudaStream_t s, long long N, int k, int Ne, const float2* Qp, long long sQ, double* Q) {
-  const long long total = N * k;
-  const long long blocks = std::max<long long>(1, std::min<long long>((total + 255) / 256, 152LL * 32));
-  k_quadrature_node_sum_df<<<(unsigned)blocks, 256, 0, s>>>(total, Ne, Qp, sQ, Q);
-  prof::count_launch();
-}
-
 const char* mixed_solve_prepare(cudaStream_t s, Grid g, int Ne, int k, MixedWork& w, int* status) {
   Dims d;
   return solve_prepare(s, g, Ne, k, w, status, &d);
 }
 
 const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
-                        MixedWork& w, const double* RHS, cplx* G, float2* Qp, const cplx* coef, int k, double ir_tol,
+                        MixedWork& w, const double* RHS, cplx* G, double* Qp, const cplx* coef, int k, double ir_tol,
                         int ir_max, MixedSolveStats* stats, int* status) {
   Dims d;
   if (const char* m = solve_prepare(s, g, Ne, k, w, status, &d)) return m;
@@ -2429,7 +2371,7 @@ cudaStream_t loop_stream(cudaStream_t& c) {
 }  // namespace
 
 const char* mixed_loop(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
-                       MixedWork& w, const double* RHS, float2* Qp, const cplx* coef, int k, const LoopParams& lp,
+                       MixedWork& w, const double* RHS, double* Qp, const cplx* coef, int k, const LoopParams& lp,
                        const double* eps, LoopState* st, const LoopHooks& hooks, const unsigned long long* key,
                        int* status) {
   if (w.loop_graph && std::memcmp(w.loop_key, key, sizeof(w.loop_key)) == 0) {

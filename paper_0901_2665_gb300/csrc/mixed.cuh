@@ -96,10 +96,9 @@ const char* mixed_solve_prepare(cudaStream_t s, Grid g, int Ne, int k, MixedWork
 // Solves (Z_e B - A) Q_e = RHS for every node e to the refinement tolerance.
 // G (nullable): receives Q_e (Ne x N x k complex128).  Qp (nullable):
 // receives the node shares Re{coef_e Q_e} of the quadrature sum (Eq. 15,
-// Ne x N x k, each a double-float pair hi + lo), accumulated in the
-// backward-sweep epilogue; quadrature_sum_df adds them up.
+// Ne x N x k real), accumulated in the backward-sweep epilogue.
 const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
-                        MixedWork& w, const double* RHS, cplx* G, float2* Qp, const cplx* coef, int k, double ir_tol,
+                        MixedWork& w, const double* RHS, cplx* G, double* Qp, const cplx* coef, int k, double ir_tol,
                         int ir_max, MixedSolveStats* stats, int* status);
 
 // The loop of a mixed-precision solve (factors in place, Y set) as one CUDA
@@ -111,13 +110,10 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
 // returns "not captured" (nothing launched) when the caller must run the
 // host-driven loop instead, nullptr once the graph ran, else an error.
 const char* mixed_loop(cudaStream_t s, Grid g, int Ne, const cplx* Z, const double* A27, const double* B27,
-                       MixedWork& w, const double* RHS, float2* Qp, const cplx* coef, int k, const LoopParams& lp,
+                       MixedWork& w, const double* RHS, double* Qp, const cplx* coef, int k, const LoopParams& lp,
                        const double* eps, LoopState* st, const LoopHooks& hooks, const unsigned long long* key,
                        int* status);
 extern const char* const kNotCaptured;
-
-// Q (N x k) = sum over the nodes, in order, of the double-float shares Qp.
-void quadrature_sum_df(cudaStream_t s, long long N, int k, int Ne, const float2* Qp, long long sQ, double* Q);
 
 // Self-test of the bounded waits of the pipelined kernels: one thread waits,
 // through the same bounded-wait helper, on an mbarrier that nothing
