@@ -685,6 +685,21 @@ struct SweepEpiTma {
   }
 };
 
+// fp32 -> fp64 through the bit fields (IEEE 754 binary32 -> binary64:
+// exponent rebiased by 1023 - 127, mantissa shifted by 29), on the integer
+// pipe: the FP64 refinement residual converts 54 values per complex entry,
+// and a float-to-double conversion instruction would take an FP64-pipe slot
+// each.  Exact for zero and normal numbers; an fp32 subnormal (|x| < 2^-126)
+// becomes a signed zero, infinities and NaNs stay infinities and NaNs.
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned ex = (u >> 23) & 0xFFu;
+  const unsigned e64 = ex == 0xFFu ? 0x7FFu : ex + (1023u - 127u);
+  const unsigned hi = (u & 0x80000000u) | (ex ? (e64 << 20) | ((u >> 3) & 0xFFFFFu) : 0u);
+  const unsigned lo = ex ? (u << 29) : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // Solve product: out[m*ldo + p] = alpha * (S' g)[p, m] (complex64); lanes are
 // consecutive rows p, so the stores of a warp are contiguous.
 // With qp set (the backward sweep of feast_solve / feast_quadrature) the
@@ -744,7 +759,8 @@ struct SolveEpi {
         if (c0 + t < CB && m < k) {
           const f2 x{alpha * re[t], alpha * im[t]};
           o[(long long)m * ldo + p] = x;
-          if (q) q[(long long)m * ldq + p] = pre.q[c0 + t] + (ce.re * (double)x.x - ce.im * (double)x.y);
+          // two FP64 FMAs; the conversions run on the integer pipe
+          if (q) q[(long long)m * ldq + p] = fma(ce.re, f32_to_f64(x.x), fma(-ce.im, f32_to_f64(x.y), pre.q[c0 + t]));
         }
       }
     }
@@ -991,21 +1007,6 @@ __global__ void k_mx_accumulate(long long total, int first, const f2* __restrict
       Q[e * total + t] = q;
     }
   }
-}
-
-// fp32 -> fp64 through the bit fields (IEEE 754 binary32 -> binary64:
-// exponent rebiased by 1023 - 127, mantissa shifted by 29), on the integer
-// pipe: the FP64 refinement residual converts 54 values per complex entry,
-// and a float-to-double conversion instruction would take an FP64-pipe slot
-// each.  Exact for zero and normal numbers; an fp32 subnormal (|x| < 2^-126)
-// becomes a signed zero, infinities and NaNs stay infinities and NaNs.
-__device__ __forceinline__ double f32_to_f64(float x) {
-  const unsigned u = __float_as_uint(x);
-  const unsigned ex = (u >> 23) & 0xFFu;
-  const unsigned e64 = ex == 0xFFu ? 0x7FFu : ex + (1023u - 127u);
-  const unsigned hi = (u & 0x80000000u) | (ex ? (e64 << 20) | ((u >> 3) & 0xFFFFFu) : 0u);
-  const unsigned lo = ex ? (u << 29) : 0u;
-  return __hiloint2double((int)hi, (int)lo);
 }
 
 constexpr int kResRows = 128;      // grid rows per block
