@@ -700,6 +700,22 @@ __device__ __forceinline__ double f32_to_f64(float x) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// fp64 -> fp32 by truncation of the mantissa, on the integer pipe: for the
+// complex64 copy of the refinement residual, which only feeds the next
+// correction's right-hand side (rounded to TF32 there), so a one-ulp
+// truncation error is immaterial.  Magnitudes below 2^-126 become a signed
+// zero, above the fp32 range an infinity; NaN stays NaN.
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const int ex = (int)((hi >> 20) & 0x7FFu);
+  if (ex == 0x7FF) return __uint_as_float(sign | 0x7F800000u | ((hi & 0xFFFFFu) | lo ? 0x400000u : 0u));
+  const int e32 = ex - (1023 - 127);
+  if (e32 <= 0) return __uint_as_float(sign);
+  if (e32 >= 0xFF) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((unsigned)e32 << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
 // Solve product: out[m*ldo + p] = alpha * (S' g)[p, m] (complex64); lanes are
 // consecutive rows p, so the stores of a warp are contiguous.
 // With qp set (the backward sweep of feast_solve / feast_quadrature) the
@@ -932,7 +948,7 @@ __global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, Chains ch, int ha
     c1[t] = two ? Cf[((long long)e * 27 + prev_slot(1) + t) * d.N + row] : f2{0.f, 0.f};
   }
   for (int m = m0; m < m0 + kCoupleCols && m < d.k; ++m) {
-    f2 g = Rc ? Rc[e * sG + (long long)m * d.N + row] : f2{(float)Rreal[(long long)m * d.N + row], 0.f};
+    f2 g = Rc ? Rc[e * sG + (long long)m * d.N + row] : f2{f64_to_f32_trunc(Rreal[(long long)m * d.N + row]), 0.f};
     if (has_prev) {
       const f2* T = Tout + ((long long)v * d.k + m) * d.n;
 #pragma unroll
@@ -1082,7 +1098,7 @@ __global__ void __launch_bounds__(kResThreads) k_mx_residual(Dims d, const cplx*
         aim = fma(-c.re, v.im, aim);
         aim = fma(-c.im, v.re, aim);
       }
-      Rc[e * sG + (long long)m * d.N + i] = f2{(float)are, (float)aim};
+      Rc[e * sG + (long long)m * d.N + i] = f2{f64_to_f32_trunc(are), f64_to_f32_trunc(aim)};
       R64[e * sG + (long long)m * d.N + i] = cplx{are, aim};
       rr += are * are + aim * aim;
       bb += b * b;
@@ -1217,10 +1233,10 @@ __global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, cons
         } else {
           R = R64[at];
         }
-        R.re -= (double)ah + (double)al;
-        R.im -= (double)bh + (double)bl;
+        R.re -= f32_to_f64(ah) + f32_to_f64(al);
+        R.im -= f32_to_f64(bh) + f32_to_f64(bl);
         R64[at] = R;
-        Rc[at] = f2{(float)R.re, (float)R.im};
+        Rc[at] = f2{f64_to_f32_trunc(R.re), f64_to_f32_trunc(R.im)};
         rr += R.re * R.re + R.im * R.im;
       }
       if (two) {
@@ -1233,10 +1249,10 @@ __global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, cons
         } else {
           R = R64[at];
         }
-        R.re -= (double)ch + (double)cl;
-        R.im -= (double)eh + (double)el;
+        R.re -= f32_to_f64(ch) + f32_to_f64(cl);
+        R.im -= f32_to_f64(eh) + f32_to_f64(el);
         R64[at] = R;
-        Rc[at] = f2{(float)R.re, (float)R.im};
+        Rc[at] = f2{f64_to_f32_trunc(R.re), f64_to_f32_trunc(R.im)};
         rr += R.re * R.re + R.im * R.im;
       }
     }
