@@ -701,9 +701,11 @@ __device__ __forceinline__ double f32_to_f64(float x) {
 }
 
 // fp64 -> fp32 by truncation of the mantissa, on the integer pipe: for the
-// complex64 copy of the refinement residual, which only feeds the next
-// correction's right-hand side (rounded to TF32 there), so a one-ulp
-// truncation error is immaterial.  Magnitudes below 2^-126 become a signed
+// complex64 copy of the FP64 refinement residual (whose FP64 pipe is its
+// bound), which only feeds the next correction's right-hand side (rounded
+// to TF32 there), so a one-ulp truncation error is immaterial.  (The
+// double-float residual and the couplings keep the conversion instructions:
+// they are bound by instruction issue, where the integer sequence costs more.)  Magnitudes below 2^-126 become a signed
 // zero, above the fp32 range an infinity; NaN stays NaN.
 __device__ __forceinline__ float f64_to_f32_trunc(double x) {
   const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
@@ -948,7 +950,7 @@ __global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, Chains ch, int ha
     c1[t] = two ? Cf[((long long)e * 27 + prev_slot(1) + t) * d.N + row] : f2{0.f, 0.f};
   }
   for (int m = m0; m < m0 + kCoupleCols && m < d.k; ++m) {
-    f2 g = Rc ? Rc[e * sG + (long long)m * d.N + row] : f2{f64_to_f32_trunc(Rreal[(long long)m * d.N + row]), 0.f};
+    f2 g = Rc ? Rc[e * sG + (long long)m * d.N + row] : f2{(float)Rreal[(long long)m * d.N + row], 0.f};
     if (has_prev) {
       const f2* T = Tout + ((long long)v * d.k + m) * d.n;
 #pragma unroll
@@ -1233,10 +1235,10 @@ __global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, cons
         } else {
           R = R64[at];
         }
-        R.re -= f32_to_f64(ah) + f32_to_f64(al);
-        R.im -= f32_to_f64(bh) + f32_to_f64(bl);
+        R.re -= (double)ah + (double)al;
+        R.im -= (double)bh + (double)bl;
         R64[at] = R;
-        Rc[at] = f2{f64_to_f32_trunc(R.re), f64_to_f32_trunc(R.im)};
+        Rc[at] = f2{(float)R.re, (float)R.im};
         rr += R.re * R.re + R.im * R.im;
       }
       if (two) {
@@ -1249,10 +1251,10 @@ __global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, cons
         } else {
           R = R64[at];
         }
-        R.re -= f32_to_f64(ch) + f32_to_f64(cl);
-        R.im -= f32_to_f64(eh) + f32_to_f64(el);
+        R.re -= (double)ch + (double)cl;
+        R.im -= (double)eh + (double)el;
         R64[at] = R;
-        Rc[at] = f2{f64_to_f32_trunc(R.re), f64_to_f32_trunc(R.im)};
+        Rc[at] = f2{(float)R.re, (float)R.im};
         rr += R.re * R.re + R.im * R.im;
       }
     }
