@@ -158,6 +158,7 @@ struct feast_handle {
   // loop buffers
   DevBuf RHS, Q, Qp, AQf, BQf, Xb, Yb, Xout, part, AQ, BQ, eps, Phi, work, norms, normA, lam_d, perm_d, resid_d,
       residp_d, loopst;
+  DevBuf Qdf;   // double-float copy of Q (or of Y) for the mixed path's products
   long long loop_graph_solves = 0;   // solves whose loop ran as one CUDA graph
   MixedWork mixed;
   // Hermitian path (complex buffers)
@@ -168,7 +169,7 @@ struct feast_handle {
     for (DevBuf* b : {&opA, &opB, &F, &T1, &T, &L, &Pinv, &G, &Tmp, &Zd, &coefd, &status, &cgw, &RHS, &Q, &Qp, &AQf,
                       &BQf,
                       &Xb, &Yb, &Xout, &part, &AQ, &BQ, &eps, &Phi, &work, &norms, &normA, &lam_d, &perm_d,
-                      &resid_d, &residp_d, &loopst, &hF, &hG, &hTmp, &hRHS, &hQ, &hAQf, &hBQf, &hX, &hY, &hXout, &hPart, &hAQ,
+                      &resid_d, &residp_d, &loopst, &Qdf, &hF, &hG, &hTmp, &hRHS, &hQ, &hAQf, &hBQf, &hX, &hY, &hXout, &hPart, &hAQ,
                       &hBQ, &hPhi, &hWork, &hZ, &hCoef, &hEps})
       b->release();
     mixed.release();
@@ -334,25 +335,59 @@ void upload_contour(feast_handle* h, const Contour& ct) {
 }
 
 // Rayleigh-Ritz on Q (device, N x M0): eps (device, M0), X (device, N x M0).
-void rayleigh_ritz_dev(feast_handle* h, const OpView& op, const double* Q, int M0, double* eps, double* X,
-                       double* AQout, double* BQout, cudaStream_t st = nullptr) {
-  const long long N = op.g.N();
-  cudaStream_t s = st ? st : h->stream;
+// Work space of rayleigh_ritz_dev and rhs_dev for M0 columns (allocated
+// before a stream capture can start).
+void rr_workspace(feast_handle* h, long long N, int M0, bool df) {
   h->AQf.ensure(sizeof(double) * N * M0, "AQ full");
   h->BQf.ensure(sizeof(double) * N * M0, "BQ full");
-  h->part.ensure(sizeof(double) * gram_partial_elems(N, M0, M0), "gram partials");
+  h->part.ensure(sizeof(double) * std::max(gram_partial_elems(N, M0, M0), df ? gram_partial_elems_df(N, M0, M0) : 0),
+                 "gram partials");
   h->AQ.ensure(sizeof(double) * M0 * M0, "A_Q");
   h->BQ.ensure(sizeof(double) * M0 * M0, "B_Q");
   h->Phi.ensure(sizeof(double) * M0 * M0, "Phi");
   h->work.ensure(sizeof(double) * 3 * M0 * M0, "eig work");
-  stencil_apply(s, op.g, op.A27, Q, N, h->AQf.as<double>(), N, M0);
-  stencil_apply(s, op.g, op.B27, Q, N, h->BQf.as<double>(), N, M0);
+  if (df) h->Qdf.ensure(sizeof(float2) * N * M0, "double-float block");
+}
+
+// Steps 3-5 (Eqs. 6-9).  df (mixed path): the operator products, Gram
+// matrices and X = Q Phi in double-float arithmetic (rr_df.cu); the reduced
+// eigensolve in FP64 either way.
+void rayleigh_ritz_dev(feast_handle* h, const OpView& op, const double* Q, int M0, double* eps, double* X,
+                       double* AQout, double* BQout, cudaStream_t st = nullptr, bool df = false) {
+  const long long N = op.g.N();
+  cudaStream_t s = st ? st : h->stream;
+  rr_workspace(h, N, M0, df);
   double* AQ = AQout ? AQout : h->AQ.as<double>();
   double* BQ = BQout ? BQout : h->BQ.as<double>();
+  if (df) {
+    float2* Qd = h->Qdf.as<float2>();
+    split_df(s, N * M0, Q, Qd);
+    stencil_apply_df(s, op.g, op.A27, Qd, N, h->AQf.as<float2>(), N, M0);
+    stencil_apply_df(s, op.g, op.B27, Qd, N, h->BQf.as<float2>(), N, M0);
+    gram_df(s, N, M0, M0, Qd, h->AQf.as<float2>(), h->part.as<double>(), AQ, true);   // Q^T (A Q), A symmetric
+    gram_df(s, N, M0, M0, Qd, h->BQf.as<float2>(), h->part.as<double>(), BQ, true);
+    reduced_eig(s, M0, AQ, BQ, eps, h->Phi.as<double>(), h->work.as<double>(), h->status.as<int>());
+    gemm_tall_df(s, N, M0, M0, Qd, h->Phi.as<double>(), X);
+    return;
+  }
+  stencil_apply(s, op.g, op.A27, Q, N, h->AQf.as<double>(), N, M0);
+  stencil_apply(s, op.g, op.B27, Q, N, h->BQf.as<double>(), N, M0);
   gram(s, N, M0, M0, Q, h->AQf.as<double>(), h->part.as<double>(), AQ, true);   // Q^T (A Q), A symmetric
   gram(s, N, M0, M0, Q, h->BQf.as<double>(), h->part.as<double>(), BQ, true);
   reduced_eig(s, M0, AQ, BQ, eps, h->Phi.as<double>(), h->work.as<double>(), h->status.as<int>());
   dgemm_tall(s, N, M0, M0, Q, h->Phi.as<double>(), X);
+}
+
+// Step 2's right-hand side RHS = B Y (N x M0); df as in rayleigh_ritz_dev.
+void rhs_dev(feast_handle* h, const OpView& op, const double* Y, int M0, double* RHS, cudaStream_t s, bool df) {
+  const long long N = op.g.N();
+  if (df) {
+    h->Qdf.ensure(sizeof(float2) * N * M0, "double-float block");
+    split_df(s, N * M0, Y, h->Qdf.as<float2>());
+    stencil_apply_df(s, op.g, op.B27, h->Qdf.as<float2>(), N, RHS, N, M0);
+  } else {
+    stencil_apply(s, op.g, op.B27, Y, N, RHS, N, M0);
+  }
 }
 
 void residuals_dev(feast_handle* h, const OpView& op, const double* lam, const double* X, int k, double* resid,
@@ -627,25 +662,18 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
       h->Qp.ensure(sizeof(double) * (size_t)Ne * N * M0, "quadrature shares");
       h->loopst.ensure(sizeof(LoopState), "loop state");
       // Rayleigh-Ritz work space, sized before a capture can start
-      h->AQf.ensure(sizeof(double) * N * M0, "AQ full");
-      h->BQf.ensure(sizeof(double) * N * M0, "BQ full");
-      h->part.ensure(sizeof(double) * gram_partial_elems(N, M0, M0), "gram partials");
-      h->AQ.ensure(sizeof(double) * M0 * M0, "A_Q");
-      h->BQ.ensure(sizeof(double) * M0 * M0, "B_Q");
-      h->Phi.ensure(sizeof(double) * M0 * M0, "Phi");
-      h->work.ensure(sizeof(double) * 3 * M0 * M0, "eig work");
+      rr_workspace(h, N, M0, true);
       // node-solve buffers too, so that the key below is the same from the
       // first solve on
       if (const char* m = mixed_solve_prepare(s, v.g, Ne, M0, h->mixed, h->status.as<int>()))
         fail(FEAST_ERR_CUDA, m);
       const LoopParams lp{lmin, lmax, tol, h->opt.ir_tol, early ? 1 : 0, h->opt.max_loops, h->opt.ir_max, M0};
       LoopHooks hooks;
-      hooks.rhs = [&](cudaStream_t st) {
-        stencil_apply(st, v.g, v.B27, h->Yb.as<double>(), N, h->RHS.as<double>(), N, M0);
-      };
+      hooks.rhs = [&](cudaStream_t st) { rhs_dev(h, v, h->Yb.as<double>(), M0, h->RHS.as<double>(), st, true); };
       hooks.quad_rr = [&](cudaStream_t st) {
         quadrature_sum(st, N, M0, Ne, h->Qp.as<double>(), N * M0, h->Q.as<double>());
-        rayleigh_ritz_dev(h, v, h->Q.as<double>(), M0, h->eps.as<double>(), h->Xb.as<double>(), nullptr, nullptr, st);
+        rayleigh_ritz_dev(h, v, h->Q.as<double>(), M0, h->eps.as<double>(), h->Xb.as<double>(), nullptr, nullptr, st,
+                          true);
       };
       hooks.next_y = [&](cudaStream_t st) { cudaMemcpyAsync(h->Yb.p, h->Xb.p, blk, cudaMemcpyDeviceToDevice, st); };
       auto bits = [](double x) {
@@ -663,6 +691,7 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
           ptr(h->Qp.p), ptr(h->Xb.p), ptr(h->Yb.p), ptr(h->eps.p), ptr(h->AQf.p), ptr(h->BQf.p), ptr(h->part.p),
           ptr(h->AQ.p), ptr(h->BQ.p), ptr(h->Phi.p), ptr(h->work.p), ptr(h->loopst.p), ptr(s), 3ULL};
       for (int i = 0; i < 16; ++i) key[28 + i] = ptr(h->mixed.bufs[i]);
+      key[44] = ptr(h->Qdf.p);
       ck(cudaEventRecord(h->ev[2], s), "event");
       const char* msg = mixed_loop(s, v.g, Ne, h->Zd.as<cplx>(), v.A27, v.B27, h->mixed, h->RHS.as<double>(),
                                    h->Qp.as<double>(), h->coefd.as<cplx>(), M0, lp, h->eps.as<double>(),
@@ -699,7 +728,7 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
 
       ck(cudaEventRecord(h->ev[2], s), "event");
       // step 2: RHS = B Y, node solves, quadrature (Eq. 15)
-      stencil_apply(s, v.g, v.B27, h->Yb.as<double>(), N, h->RHS.as<double>(), N, M0);
+      rhs_dev(h, v, h->Yb.as<double>(), M0, h->RHS.as<double>(), s, prec == FEAST_PREC_MIXED);
       // refinement target of this loop: loosened in loops 1 and 2 (their subspace
       // is still far from converged, so their solves need less accuracy)
       double ir_loop = h->opt.ir_tol;
@@ -708,7 +737,8 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
       node_solves_and_quadrature(h, v, Ne, prec, h->RHS.as<double>(), M0, ir_loop, h->Q.as<double>());
       ck(cudaEventRecord(h->ev[3], s), "event");
       // steps 3-5: Rayleigh-Ritz
-      rayleigh_ritz_dev(h, v, h->Q.as<double>(), M0, h->eps.as<double>(), h->Xb.as<double>(), nullptr, nullptr);
+      rayleigh_ritz_dev(h, v, h->Q.as<double>(), M0, h->eps.as<double>(), h->Xb.as<double>(), nullptr, nullptr,
+                        nullptr, prec == FEAST_PREC_MIXED);
       ck(cudaEventRecord(h->ev[4], s), "event");
       ck(cudaMemcpyAsync(eps.data(), h->eps.p, sizeof(double) * M0, cudaMemcpyDeviceToHost, s), "eps");
       check_status(h);

@@ -67,6 +67,25 @@ void gram(cudaStream_t s, long long N, int k1, int k2, const double* X, const do
           double* out, bool symmetric = false);
 // C (N x k, ld N) = Q (N x m, ld N) * P (m x k, ld m).
 void dgemm_tall(cudaStream_t s, long long N, int m, int k, const double* Q, const double* P, double* C);
+
+// ---------------------------------------------------------------- rr_df.cu
+// Double-float (hi + lo fp32 pairs) versions of the FP64 products above, for
+// the mixed path (the FP64 pipe is 1/64 of the FP32 rate on this GPU).
+// Y (N x k double-float) = split of X (FP64), element by element.
+void split_df(cudaStream_t s, long long total, const double* X, float2* Y);
+// Y = C X, C a 27-point FP64 operator, X double-float; Y double-float or FP64.
+void stencil_apply_df(cudaStream_t s, Grid g, const double* C27, const float2* X, long long ldx, float2* Y,
+                      long long ldy, int k);
+void stencil_apply_df(cudaStream_t s, Grid g, const double* C27, const float2* X, long long ldx, double* Y,
+                      long long ldy, int k);
+// out (k1 x k2, FP64) = X^T Y for double-float X, Y; partial: scratch of
+// gram_partial_elems_df(N, k1, k2) doubles.  Deterministic.
+long long gram_partial_elems_df(long long N, int k1, int k2);
+void gram_df(cudaStream_t s, long long N, int k1, int k2, const float2* X, const float2* Y, double* partial,
+             double* out, bool symmetric = false);
+// C (N x k, FP64) = Q (N x m, double-float) * P (m x k, FP64).
+void gemm_tall_df(cudaStream_t s, long long N, int m, int k, const float2* Q, const double* P, double* C);
+
 // Reduced generalized eigensolve A_Q Phi = eps B_Q Phi (two-stage Jacobi), m <= 128.
 // work: 3*m*m doubles scratch.  Status word gets DEV_BQ_NOT_SPD / DEV_JACOBI.
 void reduced_eig(cudaStream_t s, int m, const double* AQ, const double* BQ, double* eps, double* Phi,
