@@ -166,36 +166,68 @@ __global__ void __launch_bounds__(256) k_mx_schur1(Dims d, Chains ch, const f2* 
 // C the coupling of v's layer to its previous layer (has_prev: 0 on a chain's
 // first layer).  middle: v < Ne only; the middle layer takes both chains'
 // contributions, C0 T1[v] + C1 T1[v + Ne] (the second when has_prev1).
-// Row p's coefficients are loaded first and the T1 rows of all taps are read
-// unconditionally (tap_offset), so that the loads overlap.
+// A thread takes column q of kSchur2Rows consecutive rows p: the nine taps of
+// row p read T1 rows p + dx + nx dy, so per in-plane offset dy the thread
+// keeps a window of the three rows p - 1, p, p + 1 and loads one new row per
+// step (3 loads per output instead of 9).  A tap outside the grid has a zero
+// coefficient; its window entry is T1's own (finite) value, or zero beyond
+// the layer.
+constexpr int kSchur2Rows = 32;
 __global__ void __launch_bounds__(256) k_mx_schur2(Dims d, Chains ch, int has_prev, int middle, int has_prev1,
                                                    const f2* __restrict__ Cf, const float* __restrict__ T1,
                                                    float* __restrict__ F) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  const int p = blockIdx.y, v = blockIdx.z;
+  const int p0 = blockIdx.y * kSchur2Rows, v = blockIdx.z;
   if (q >= d.n) return;
   const int c = chain_of(ch, v), e = node_of(ch, v);
-  const long long rowp = (long long)ch.layer[c] * d.n + p;
-  const int px = p % d.nx, py = p / d.nx;
-  f2 acc{0.f, 0.f};
-  const int ddx = (q % d.nx) - px, ddy = (q / d.nx) - py;
-  if (ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1) acc = cf_at(d, Cf, e, 9 + (ddy + 1) * 3 + (ddx + 1), rowp);
-  auto add = [&](int vt, int slot0) {
-    const float* T = T1 + (long long)vt * d.n * d.ldF;
-    f2 cv[9];
-#pragma unroll
-    for (int t = 0; t < 9; ++t) cv[t] = cf_at(d, Cf, e, slot0 + t, rowp);
-#pragma unroll
-    for (int t = 0; t < 9; ++t) {
-      const float* Trow = T + (long long)(p + tap_offset(d, p, t)) * d.ldF;
-      f2fma(acc, cv[t], f2{Trow[q], Trow[d.n + q]});
-    }
+  const int n = d.n, nx = d.nx;
+  const int qx = q % nx, qy = q / nx;
+  const int p1 = min(n, p0 + kSchur2Rows);
+  auto load = [&](const float* T, int a) {
+    return (a >= 0 && a < n) ? f2{T[(long long)a * d.ldF + q], T[(long long)a * d.ldF + n + q]} : f2{0.f, 0.f};
   };
-  if (has_prev) add(v, prev_slot(c));
-  if (middle && has_prev1) add(v + ch.Ne, prev_slot(1));
-  float* out = F + (((long long)v * 2 + ch.wplane) * d.n + p) * d.ldF;
-  out[q] = acc.x;
-  out[d.n + q] = acc.y;
+  const bool two = middle && has_prev1;
+  const float* Ta = T1 + (long long)v * n * d.ldF;
+  const float* Tb = T1 + (long long)(v + ch.Ne) * n * d.ldF;
+  // windows w[source][dy + 1][dx + 1] = T1[p + dx + nx dy][q]
+  f2 wa[3][3], wb[3][3];
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      const int a = p0 - 1 + dx + nx * (dy - 1);   // rows p0 - 1 and p0 of band dy
+      wa[dy][dx + 1] = has_prev ? load(Ta, a) : f2{0.f, 0.f};
+      wb[dy][dx + 1] = two ? load(Tb, a) : f2{0.f, 0.f};
+    }
+  for (int p = p0; p < p1; ++p) {
+    const long long rowp = (long long)ch.layer[c] * n + p;
+    // slide: the windows move to rows p - 1, p, p + 1 of each band
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) {
+      wa[dy][0] = wa[dy][1];
+      wa[dy][1] = wa[dy][2];
+      wb[dy][0] = wb[dy][1];
+      wb[dy][1] = wb[dy][2];
+      const int a = p + 1 + nx * (dy - 1);
+      wa[dy][2] = has_prev ? load(Ta, a) : f2{0.f, 0.f};
+      wb[dy][2] = two ? load(Tb, a) : f2{0.f, 0.f};
+    }
+    const int px = p % nx, py = p / nx;
+    f2 acc{0.f, 0.f};
+    const int ddx = qx - px, ddy = qy - py;
+    if (ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1) acc = cf_at(d, Cf, e, 9 + (ddy + 1) * 3 + (ddx + 1), rowp);
+    if (has_prev) {
+#pragma unroll
+      for (int t = 0; t < 9; ++t) f2fma(acc, cf_at(d, Cf, e, prev_slot(c) + t, rowp), wa[t / 3][t % 3]);
+    }
+    if (two) {
+#pragma unroll
+      for (int t = 0; t < 9; ++t) f2fma(acc, cf_at(d, Cf, e, prev_slot(1) + t, rowp), wb[t / 3][t % 3]);
+    }
+    float* out = F + (((long long)v * 2 + ch.wplane) * n + p) * d.ldF;
+    out[q] = acc.x;
+    out[n + q] = acc.y;
+  }
 }
 
 // ------------------------------------------------------------------ panel
@@ -926,6 +958,8 @@ constexpr int kCoupleCols = 4;   // right-hand-side columns per thread of the co
 // handles the virtual node of the z-th set bit of nl.mask.  g goes to the
 // node's solution column, its embedded copy to the virtual node's GEMM
 // operand.
+// kTwo: the middle layer with both chains' products (a second set of taps).
+template <bool kTwo>
 __global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, Chains ch, int has_prev, int middle, int has_prev1,
                                                        const f2* __restrict__ Cf, const double* __restrict__ Rreal,
                                                        const f2* __restrict__ Rc, const f2* __restrict__ Tout,
@@ -941,13 +975,13 @@ __global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, Chains ch, int ha
   // branch-free taps: an in-plane neighbour outside the grid has a zero
   // coefficient and is read at offset 0 (the row itself) to stay in bounds
   int off[9];
-  f2 c0[9], c1[9];
-  const bool two = middle && has_prev1;
+  f2 c0[9], c1[kTwo ? 9 : 1];
+  const bool two = kTwo && middle && has_prev1;
 #pragma unroll
   for (int t = 0; t < 9; ++t) {
     off[t] = p + tap_offset(d, p, t);
     c0[t] = has_prev ? Cf[((long long)e * 27 + prev_slot(c) + t) * d.N + row] : f2{0.f, 0.f};
-    c1[t] = two ? Cf[((long long)e * 27 + prev_slot(1) + t) * d.N + row] : f2{0.f, 0.f};
+    if constexpr (kTwo) c1[t] = two ? Cf[((long long)e * 27 + prev_slot(1) + t) * d.N + row] : f2{0.f, 0.f};
   }
   for (int m = m0; m < m0 + kCoupleCols && m < d.k; ++m) {
     f2 g = Rc ? Rc[e * sG + (long long)m * d.N + row] : f2{(float)Rreal[(long long)m * d.N + row], 0.f};
@@ -956,10 +990,12 @@ __global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, Chains ch, int ha
 #pragma unroll
       for (int t = 0; t < 9; ++t) f2fma(g, c0[t], T[off[t]]);
     }
-    if (two) {
-      const f2* T = Tout + ((long long)(v + ch.Ne) * d.k + m) * d.n;
+    if constexpr (kTwo) {
+      if (two) {
+        const f2* T = Tout + ((long long)(v + ch.Ne) * d.k + m) * d.n;
 #pragma unroll
-      for (int t = 0; t < 9; ++t) f2fma(g, c1[t], T[off[t]]);
+        for (int t = 0; t < 9; ++t) f2fma(g, c1[t], T[off[t]]);
+      }
     }
     Gc[e * sG + (long long)m * d.N + row] = g;
     write_emb(d, Bemb, v, p, m, g);
@@ -1756,7 +1792,8 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
       prof::add_work(prof::SCHUR, (t > 0 ? 144.0 : 0.0) * d.n * (double)d.n * nv);
       if (t > 0)
         k_mx_schur1<<<dim3(sgrid.x, cdiv(d.n, kSchurRows), nv), 256, 0, s>>>(d, ch, Cf, F, buf<float>(w, B_T1));
-      k_mx_schur2<<<dim3(sgrid.x, sgrid.y, nv), 256, 0, s>>>(d, ch, t > 0, 0, 0, Cf, buf<float>(w, B_T1), F);
+      k_mx_schur2<<<dim3(sgrid.x, cdiv(d.n, kSchur2Rows), nv), 256, 0, s>>>(d, ch, t > 0, 0, 0, Cf,
+                                                                            buf<float>(w, B_T1), F);
       prof::end(s, prof::SCHUR);
       prof::count_launch(t > 0 ? 2 : 1);
       if (const char* m = sweep(ch, nv)) return m;
@@ -1769,7 +1806,8 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
       if (L0 > 0)
         k_mx_schur1<<<dim3(sgrid.x, cdiv(d.n, kSchurRows), L1 > 0 ? V : Ne), 256, 0, s>>>(d, ch, Cf, F,
                                                                                          buf<float>(w, B_T1));
-      k_mx_schur2<<<dim3(sgrid.x, sgrid.y, Ne), 256, 0, s>>>(d, ch, L0 > 0, 1, L1 > 0, Cf, buf<float>(w, B_T1), F);
+      k_mx_schur2<<<dim3(sgrid.x, cdiv(d.n, kSchur2Rows), Ne), 256, 0, s>>>(d, ch, L0 > 0, 1, L1 > 0, Cf,
+                                                                            buf<float>(w, B_T1), F);
       prof::end(s, prof::SCHUR);
       prof::count_launch(L0 > 0 ? 2 : 1);
       if (const char* m = sweep(ch, Ne)) return m;
@@ -1907,7 +1945,7 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     const NodeList& vl = t < L1 ? both : one;
     prof::begin(s, prof::COUPLE);
     prof::add_work(prof::COUPLE, couple_bytes(vl.count, 40.0));
-    k_mx_couple_fwd<<<dim3(cdiv(d.n, 128), cdiv(d.k, kCoupleCols), vl.count), 128, 0, s>>>(
+    k_mx_couple_fwd<false><<<dim3(cdiv(d.n, 128), cdiv(d.k, kCoupleCols), vl.count), 128, 0, s>>>(
         d, ch, t > 0, 0, 0, Cf, Rreal, Rc, Tout, Gc, Bemb, vl, dactive);
     prof::end(s, prof::COUPLE);
     SolveEpi<CB> epi{Tout, (long long)d.n * d.k, d.n, d.n, d.k, 1.0f};
@@ -1919,7 +1957,7 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     const Chains ch{Ne, {K, K}, {0, 0}, 0};
     prof::begin(s, prof::COUPLE);
     prof::add_work(prof::COUPLE, couple_bytes(one.count, L1 > 0 ? 48.0 : 40.0));
-    k_mx_couple_fwd<<<dim3(cdiv(d.n, 128), cdiv(d.k, kCoupleCols), one.count), 128, 0, s>>>(
+    k_mx_couple_fwd<true><<<dim3(cdiv(d.n, 128), cdiv(d.k, kCoupleCols), one.count), 128, 0, s>>>(
         d, ch, L0 > 0, 1, L1 > 0, Cf, Rreal, Rc, Tout, Gc, Bemb, one, dactive);
     prof::end(s, prof::COUPLE);
     if (!gemm(one, K, K, back_epi(ch))) return "tcgen05 solve launch failed";
