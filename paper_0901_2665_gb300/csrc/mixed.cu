@@ -1067,7 +1067,11 @@ constexpr int kResRows = 128;      // grid rows per block
 // Refinement targets at or above this take their first residual in
 // double-float as well (its error, ~1e-12 of ||RHS||, is far below them).
 constexpr double kFFirstTol = 1e-9;
-constexpr int kResThreads = 256;   // two columns in flight per row
+constexpr int kResThreads = 256;   // two column groups per row
+#ifndef FEAST_RES_COLS
+#define FEAST_RES_COLS 4
+#endif
+constexpr int kResCols = FEAST_RES_COLS;   // columns per pass of a thread in the double-float residual
 constexpr size_t kResSmem = sizeof(cplx) * 27 * kResRows;
 
 // R_e = RHS - (Z_e B - A) Q_e in FP64 (108 FP64 FMAs per complex entry, the
@@ -1237,12 +1241,20 @@ __global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, cons
     const long long sG = d.N * d.k;
     const int g = tid / kResRows;   // column group: columns g, g + 2, g + 4, ...
     constexpr int kGroups = kResThreads / kResRows;
-    for (int m = g; m < d.k; m += 2 * kGroups) {
-      const bool two = m + kGroups < d.k;
+    // kResCols columns of the group per pass, sharing each tap's coefficient
+    // and offset
+    for (int m = g; m < d.k; m += kResCols * kGroups) {
+      const f2* v[kResCols];
+      bool has[kResCols];
       const f2* v0 = delta + e * sG + (long long)m * d.N + i;
-      const f2* v1 = two ? v0 + (long long)kGroups * d.N : v0;
-      float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;   // column m: Re, Im (hi, lo)
-      float ch = 0.f, cl = 0.f, eh = 0.f, el = 0.f;   // column m + 2
+#pragma unroll
+      for (int j = 0; j < kResCols; ++j) {
+        has[j] = m + j * kGroups < d.k;
+        v[j] = has[j] ? v0 + (long long)j * kGroups * d.N : v0;
+      }
+      float rh[kResCols], rl[kResCols], ih[kResCols], il[kResCols];   // Re, Im (hi, lo)
+#pragma unroll
+      for (int j = 0; j < kResCols; ++j) rh[j] = rl[j] = ih[j] = il[j] = 0.f;
 #pragma unroll 9
       for (int s = 0; s < 27; ++s) {
         const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
@@ -1250,45 +1262,35 @@ __global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, cons
                         (dz < 0 ? zm : (dz > 0 ? zp : true));
         const int off = ok ? dx * sx + dy * sy + dz * sz : 0;
         const float4 c = csm[s * kResRows + r];
-        const f2 x = v0[off];
-        const f2 y = v1[off];
-        ff_axpy(c.x, c.y, x.x, ah, al);      // + Re c Re x
-        ff_axpy(c.x, c.y, x.y, bh, bl);      // + Re c Im x
-        ff_axpy(c.x, c.y, y.x, ch, cl);
-        ff_axpy(c.x, c.y, y.y, eh, el);
-        ff_axpy(-c.z, -c.w, x.y, ah, al);    // - Im c Im x
-        ff_axpy(c.z, c.w, x.x, bh, bl);      // + Im c Re x
-        ff_axpy(-c.z, -c.w, y.y, ch, cl);
-        ff_axpy(c.z, c.w, y.x, eh, el);
+        f2 x[kResCols];
+#pragma unroll
+        for (int j = 0; j < kResCols; ++j) x[j] = v[j][off];
+#pragma unroll
+        for (int j = 0; j < kResCols; ++j) {
+          ff_axpy(c.x, c.y, x[j].x, rh[j], rl[j]);     // + Re c Re x
+          ff_axpy(c.x, c.y, x[j].y, ih[j], il[j]);     // + Re c Im x
+        }
+#pragma unroll
+        for (int j = 0; j < kResCols; ++j) {
+          ff_axpy(-c.z, -c.w, x[j].y, rh[j], rl[j]);   // - Im c Im x
+          ff_axpy(c.z, c.w, x[j].x, ih[j], il[j]);     // + Im c Re x
+        }
       }
-      {
-        const long long at = e * sG + (long long)m * d.N + i;
+#pragma unroll
+      for (int j = 0; j < kResCols; ++j) {
+        if (!has[j]) continue;
+        const int mj = m + j * kGroups;
+        const long long at = e * sG + (long long)mj * d.N + i;
         cplx R;
         if constexpr (kFirst) {
-          const double b = RHS[(long long)m * d.N + i];
+          const double b = RHS[(long long)mj * d.N + i];
           R = cplx{b, 0.0};
           bb += b * b;
         } else {
           R = R64[at];
         }
-        R.re -= (double)ah + (double)al;
-        R.im -= (double)bh + (double)bl;
-        R64[at] = R;
-        Rc[at] = f2{(float)R.re, (float)R.im};
-        rr += R.re * R.re + R.im * R.im;
-      }
-      if (two) {
-        const long long at = e * sG + (long long)(m + kGroups) * d.N + i;
-        cplx R;
-        if constexpr (kFirst) {
-          const double b = RHS[(long long)(m + kGroups) * d.N + i];
-          R = cplx{b, 0.0};
-          bb += b * b;
-        } else {
-          R = R64[at];
-        }
-        R.re -= (double)ch + (double)cl;
-        R.im -= (double)eh + (double)el;
+        R.re -= (double)rh[j] + (double)rl[j];
+        R.im -= (double)ih[j] + (double)il[j];
         R64[at] = R;
         Rc[at] = f2{(float)R.re, (float)R.im};
         rr += R.re * R.re + R.im * R.im;
