@@ -46,12 +46,14 @@ FF_OPS_PER_ENTRY = 27 * 4 * 11        # fp32 instructions per complex entry of t
 # were captured on 24 of 400 layers and scaled by 400/24, their traffic being
 # proportional to the rows).  An entry is removed when its kernel changes.
 TRAFFIC = {
-    "solve_gemm": 0.5 * ((83.9 + 2.2) + (83.9 + 1.9)) * 1e6,
+    # 16 virtual nodes per launch (two chains of 8 nodes)
+    "solve_gemm": (167.9 + 4.6) * 1e6,
     # wide sweep update: 15 regular launches and the last panel's (which also
     # writes the TF32 solve copy) per layer
-    "sweep_gemm": (15 * (79.2 + 7.6) + (84.0 + 73.2)) / 16 * 1e6,
-    "fp64_residual": (718.9 + 564.9) * 1e6 * 400 / 24,
-    "ff_residual": 0.5 * ((664.0 + 549.2) + (664.1 + 549.1)) * 1e6 * 400 / 24,
+    "sweep_gemm": (15 * (158.4 + 68.1) + (167.9 + 207.7)) / 16 * 1e6,
+    "fp64_residual": (486.1 + 556.6) * 1e6 * 400 / 24,
+    # the later (incremental) residuals, 12 of the 14 launches of a solve
+    "ff_residual": (662.3 + 546.8) * 1e6 * 400 / 24,
 }
 
 
