@@ -752,23 +752,51 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
 
 // Solve product: out[m*ldo + p] = alpha * (S' g)[p, m] (complex64); lanes are
 // consecutive rows p, so the stores of a warp are contiguous.
+// With qp set (the backward sweep of feast_solve / feast_quadrature) the
+// epilogue also folds the layer's solution x into the node's share of the
+// quadrature sum (Eq. 15):  qp[m*ldq + p] (= or +=) Re{coef_e x}  in FP64,
+// coef_e = -(w_e/2) r e^{i theta_e}.  x of the first solve is Q_e itself and
+// x of each refinement step is its correction, so after the last step the
+// node's share is Re{coef_e Q_e}, without Q_e ever being stored.
 template <int CB>
 struct SolveEpi {
   f2* out;
   long long sOut, ldo;
   int n, k;
   float alpha;
-  // node_rows: out belongs to the real node of virtual node e, at the rows of
-  // its chain's layer (the backward sweep); else out is per virtual node (the
-  // forward products)
+  double* qp = nullptr;        // per-node quadrature partials
+  long long sQ = 0, ldq = 0;   // node stride, column stride
+  const cplx* coef = nullptr;  // Ne quadrature coefficients
+  int qfirst = 0;              // 1: store (first solve), 0: accumulate (refinement)
+  // node_rows: out and qp belong to the real node of virtual node e, at the
+  // rows of its chain's layer (the backward sweep); else out is per virtual
+  // node (the forward products)
   int node_rows = 0;
   Chains ch{};
   __device__ long long base(int e, long long stride) const {
     return node_rows ? node_of(ch, e) * stride + (long long)ch.layer[chain_of(ch, e)] * n : e * stride;
   }
-  __device__ void operator()(int e, int tm, int tn, int row, uint32_t taddr, int, uint8_t*) const {
+  // the old shares of this thread's row, loaded while the main loop runs
+  // (a refinement step reads them back)
+  struct Pre {
+    double q[CB];
+  };
+  __device__ void prefetch(int e, int tm, int tn, int row, Pre& pre) const {
+    const int p = tm * tc::kBlockM + row;
+    const bool rd = qp && !qfirst && p < n;
+    const double* q = qp ? qp + base(e, sQ) : nullptr;
+#pragma unroll
+    for (int t = 0; t < CB; ++t) {
+      const int m = tn * CB + t;
+      pre.q[t] = (rd && m < k) ? q[(long long)m * ldq + p] : 0.0;
+    }
+  }
+  __device__ void operator()(int e, int tm, int tn, int row, uint32_t taddr, int, uint8_t*, const Pre& pre) const {
     const int p = tm * tc::kBlockM + row;
     f2* o = out + base(e, sOut);
+    double* q = qp ? qp + base(e, sQ) : nullptr;
+    cplx ce{0.0, 0.0};
+    if (qp) ce = coef[node_of(ch, e)];
 #pragma unroll
     for (int c0 = 0; c0 < CB; c0 += 16) {
       float re[16], im[16];
@@ -779,7 +807,10 @@ struct SolveEpi {
       for (int t = 0; t < 16; ++t) {
         const int m = tn * CB + c0 + t;
         if (c0 + t < CB && m < k) {
-          o[(long long)m * ldo + p] = f2{alpha * re[t], alpha * im[t]};
+          const f2 x{alpha * re[t], alpha * im[t]};
+          o[(long long)m * ldo + p] = x;
+          // two FP64 FMAs; the conversions run on the integer pipe
+          if (q) q[(long long)m * ldq + p] = fma(ce.re, f32_to_f64(x.x), fma(-ce.im, f32_to_f64(x.y), pre.q[c0 + t]));
         }
       }
     }
@@ -1049,11 +1080,7 @@ constexpr size_t kResSmem = sizeof(cplx) * 27 * kResRows;
 // complex coefficients in shared memory while the threads sweep the columns.
 // Stores R in FP64 (R64, the start of the incremental residuals) and as
 // complex64 (the next correction's right-hand side), and per-block partial
-// sums of |R|^2 and |RHS|^2.  With qp set it also starts the node's share of
-// the quadrature sum (Eq. 15), qp = Re{coef_e Q_e} (FP64): every residual
-// kernel reads the solution or correction that the sweeps just produced, so
-// the share is folded in here, where the FP64 pipe has the room, and not in
-// the solve product's epilogue.
+// sums of |R|^2 and |RHS|^2.
 __global__ void __launch_bounds__(kResThreads) k_mx_residual(Dims d, const cplx* __restrict__ Z,
                                                              const double* __restrict__ A27,
                                                              const double* __restrict__ B27,
@@ -1061,8 +1088,7 @@ __global__ void __launch_bounds__(kResThreads) k_mx_residual(Dims d, const cplx*
                                                              const f2* __restrict__ Q, f2* __restrict__ Rc,
                                                              cplx* __restrict__ R64, double* __restrict__ partial,
                                                              const int* __restrict__ active,
-                                                             const double* __restrict__ target,
-                                                             double* __restrict__ qp, const cplx* __restrict__ coef) {
+                                                             const double* __restrict__ target) {
   extern __shared__ cplx rsm[];
   __shared__ double red[2][kResThreads];
   const int e = blockIdx.y;
@@ -1116,11 +1142,6 @@ __global__ void __launch_bounds__(kResThreads) k_mx_residual(Dims d, const cplx*
       }
       Rc[e * sG + (long long)m * d.N + i] = f2{f64_to_f32_trunc(are), f64_to_f32_trunc(aim)};
       R64[e * sG + (long long)m * d.N + i] = cplx{are, aim};
-      if (qp) {
-        const cplx ce = coef[e];
-        const f2 xc = q[0];
-        qp[e * sG + (long long)m * d.N + i] = fma(ce.re, f32_to_f64(xc.x), -ce.im * f32_to_f64(xc.y));
-      }
       rr += are * are + aim * aim;
       bb += b * b;
     }
@@ -1166,8 +1187,7 @@ __device__ __forceinline__ void ff_axpy(float ch, float cl, float v, float& sh, 
 }
 
 // R64 <- R64 - (Z_e B - A) delta, Rc <- complex64(R64), partial |R|^2 per block
-// (the |RHS|^2 partials of the first residual are kept); with qp set also
-// qp += Re{coef_e delta}, the node's share of Eq. 15 (as in k_mx_residual).
+// (the |RHS|^2 partials of the first residual are kept).
 // kFirst: the first residual of a solve whose target is loose (>= 1e-9
 // relative): R64 starts from RHS instead, delta is the first solution Q_e,
 // and the |RHS|^2 partials are written.  The product's error, ~2^-48 kappa
@@ -1180,9 +1200,7 @@ __global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, cons
                                                                  cplx* __restrict__ R64, double* __restrict__ partial,
                                                                  const int* __restrict__ active,
                                                                  const double* __restrict__ RHS,
-                                                                 const double* __restrict__ target,
-                                                                 double* __restrict__ qp,
-                                                                 const cplx* __restrict__ coef) {
+                                                                 const double* __restrict__ target) {
   extern __shared__ float4 csm[];   // per (slot, row): Re c hi/lo, Im c hi/lo
   __shared__ double red[kResThreads];
   __shared__ double redb[kFirst ? kResThreads : 1];
@@ -1276,12 +1294,6 @@ __global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, cons
         R64[at] = R;
         Rc[at] = f2{(float)R.re, (float)R.im};
         rr += R.re * R.re + R.im * R.im;
-        if (qp) {
-          const cplx ce = coef[e];
-          const f2 xc = v[j][0];
-          const double add = fma(ce.re, (double)xc.x, -ce.im * (double)xc.y);
-          qp[at] = kFirst ? add : qp[at] + add;
-        }
       }
     }
   }
@@ -1861,14 +1873,24 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
 
 namespace {
 
+// Where the backward sweep folds its solutions into the quadrature sum
+// (Eq. 15): per-node partials qp (N x k, node stride N k), the coefficients,
+// and whether this sweep stores (the first solve) or accumulates (a
+// refinement step).  qp == nullptr: no folding.
+struct QuadOut {
+  double* qp;
+  const cplx* coef;
+  int first;
+};
+
 // One pair of sweeps of the two-ended elimination (see Chains): the forward
 // sweep runs up both chains (chain 0 from layer 0, chain 1 from layer nz-1)
 // to the middle layer K, whose solution x_K = -S'_K g_K starts the backward
 // sweep, which then runs out along both chains.  nl: the real nodes swept.
 template <int CB, int ST>
 const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const double* A27, const double* B27,
-                         MixedWork& w, const double* Rreal, const f2* Rc, const NodeList& nl, int* status,
-                         const int* dactive) {
+                         MixedWork& w, const double* Rreal, const f2* Rc, const NodeList& nl, const QuadOut& qo,
+                         int* status, const int* dactive) {
   float* F = buf<float>(w, B_F);
   f2* Gc = buf<f2>(w, B_GC);
   f2* Tout = buf<f2>(w, B_TOUT);
@@ -1903,11 +1925,19 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     prof::end(s, prof::SOLVE_GEMM);
     return ok;
   };
-  // backward products x = -S' s into the nodes' solution columns
+  // backward products x = -S' s into the nodes' solution columns (and the
+  // quadrature shares)
   auto back_epi = [&](const Chains& ch) {
     SolveEpi<CB> epi{Gc, d.N * d.k, d.N, d.n, d.k, -1.0f};
     epi.node_rows = 1;
     epi.ch = ch;
+    if (qo.qp) {
+      epi.qp = qo.qp;
+      epi.sQ = d.N * d.k;
+      epi.ldq = d.N;
+      epi.coef = qo.coef;
+      epi.qfirst = qo.first;
+    }
     return epi;
   };
   int launches = 0;
@@ -2026,14 +2056,14 @@ int tuned_cfg(cudaStream_t s, const Dims& d, MixedWork& w, int* status) {
 }
 
 const char* solve_direct(cudaStream_t s, const Dims& d, const cplx* Z, const double* A27, const double* B27,
-                         MixedWork& w, const double* Rreal, const f2* Rc, const NodeList& nl, int* status,
-                         const int* dactive = nullptr) {
+                         MixedWork& w, const double* Rreal, const f2* Rc, const NodeList& nl, const QuadOut& qo,
+                         int* status, const int* dactive = nullptr) {
   switch (cfg_of(d.CB, d.ST)) {
-    case cfg_of(8, 4): return solve_sweeps<8, 4>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status, dactive);
-    case cfg_of(16, 4): return solve_sweeps<16, 4>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status, dactive);
-    case cfg_of(32, 4): return solve_sweeps<32, 4>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status, dactive);
-    case cfg_of(64, 3): return solve_sweeps<64, 3>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status, dactive);
-    case cfg_of(64, 4): return solve_sweeps<64, 4>(s, d, Z, A27, B27, w, Rreal, Rc, nl, status, dactive);
+    case cfg_of(8, 4): return solve_sweeps<8, 4>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
+    case cfg_of(16, 4): return solve_sweeps<16, 4>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
+    case cfg_of(32, 4): return solve_sweeps<32, 4>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
+    case cfg_of(64, 3): return solve_sweeps<64, 3>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
+    case cfg_of(64, 4): return solve_sweeps<64, 4>(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status, dactive);
     default: return "solve-GEMM configuration without an instantiation";
   }
 }
@@ -2044,7 +2074,7 @@ const char* solve_direct(cudaStream_t s, const Dims& d, const cplx* Z, const dou
 // back to direct launches.
 const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const double* A27, const double* B27,
                        MixedWork& w, const double* Rreal, const f2* Rc, const std::vector<int>& active,
-                       MixedSolveStats* stats, int* status) {
+                       const QuadOut& qo, MixedSolveStats* stats, int* status) {
   NodeList nl{0, 0ULL};
   for (int e = 0; e < d.Ne; ++e)
     if (active[e]) {
@@ -2052,7 +2082,7 @@ const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const doubl
       ++nl.count;
     }
   if (nl.count == 0) return nullptr;
-  if (prof::enabled() || !w.use_graphs) return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+  if (prof::enabled() || !w.use_graphs) return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
   const unsigned long long key[kSweepKey] = {
       (unsigned long long)d.nx | ((unsigned long long)d.ny << 20) | ((unsigned long long)d.nz << 40),
       (unsigned long long)d.k | ((unsigned long long)cfg_of(d.CB, d.ST) << 20) | ((unsigned long long)d.Ne << 40),
@@ -2062,7 +2092,7 @@ const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const doubl
       (unsigned long long)(uintptr_t)w.bufs[B_F], (unsigned long long)(uintptr_t)w.bufs[B_GC],
       (unsigned long long)(uintptr_t)w.bufs[B_TOUT], (unsigned long long)(uintptr_t)w.bufs[B_BEMB],
       (unsigned long long)(uintptr_t)w.bufs[B_CF], (unsigned long long)d.ldF, 1ULL,
-      0ULL, 0ULL, 0ULL,
+      (unsigned long long)(uintptr_t)qo.qp, (unsigned long long)(uintptr_t)qo.coef, (unsigned long long)qo.first,
       0ULL};
   SweepGraphCache& gc = w.graphs;
   ++gc.clock;
@@ -2080,17 +2110,17 @@ const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const doubl
   if (!seen) {
     std::memcpy(gc.seen[gc.seen_next], key, sizeof(key));
     gc.seen_next = (gc.seen_next + 1) % kSweepGraphs;
-    return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+    return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
   }
   // second sighting: capture
   cudaGraph_t graph = nullptr;
   cudaStream_t cs = capture_stream(w);
   if (!cs || cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
-    return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+    return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
   }
   const long long launches0 = prof::launches();
-  const char* msg = solve_direct(cs, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+  const char* msg = solve_direct(cs, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
   const cudaError_t end = cudaStreamEndCapture(cs, &graph);
   cudaGraphExec_t exec = nullptr;
   if (msg || end != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
@@ -2098,7 +2128,7 @@ const char* solve_once(cudaStream_t s, const Dims& d, const cplx* Z, const doubl
     cudaGetLastError();
     prof::count_launch(launches0 - prof::launches());   // nothing of the capture ran
     if (msg) return msg;
-    return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, status);
+    return solve_direct(s, d, Z, A27, B27, w, Rreal, Rc, nl, qo, status);
   }
   cudaGraphDestroy(graph);
   int slot = 0;
@@ -2194,7 +2224,7 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
   std::vector<double> rel(Ne, 0.0), final_rel(Ne, 0.0);
   const int acc_blocks = (int)std::min<long long>(4096, (sG + 255) / 256);
   // first solve: Q_e = M~^{-1} RHS
-  if (const char* m = solve_once(s, d, Z, A27, B27, w, RHS, nullptr, active, stats, status))
+  if (const char* m = solve_once(s, d, Z, A27, B27, w, RHS, nullptr, active, QuadOut{Qp, coef, 1}, stats, status))
     return m;
   if (G) {
     k_mx_accumulate<<<dim3(acc_blocks, Ne), 256, 0, s>>>(sG, 1, buf<f2>(w, B_GC), G, buf<int>(w, B_ACTIVE));
@@ -2211,7 +2241,7 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
         prof::add_work(prof::FF_RESIDUAL, 216.0 * (double)d.N * k * nact);
         k_mx_residual_inc<true><<<rgrid, kResThreads, kResSmem, s>>>(
             d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<cplx>(w, B_R64), buf<double>(w, B_PART),
-            buf<int>(w, B_ACTIVE), RHS, nullptr, Qp, coef);
+            buf<int>(w, B_ACTIVE), RHS, nullptr);
         prof::end(s, prof::FF_RESIDUAL);
       } else if (steps == 0) {
         // the first residual in FP64 from Q_e itself
@@ -2219,7 +2249,7 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
         prof::add_work(prof::RESIDUAL, 216.0 * (double)d.N * k * nact);   // 108 FP64 FMAs per complex entry
         k_mx_residual<<<rgrid, kResThreads, kResSmem, s>>>(d, Z, A27, B27, RHS, buf<f2>(w, B_GC), buf<f2>(w, B_RC),
                                                            buf<cplx>(w, B_R64), buf<double>(w, B_PART),
-                                                           buf<int>(w, B_ACTIVE), nullptr, Qp, coef);
+                                                           buf<int>(w, B_ACTIVE), nullptr);
         prof::end(s, prof::RESIDUAL);
       } else {
         // later residuals move by the last correction, in double-float
@@ -2227,7 +2257,7 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
         prof::add_work(prof::FF_RESIDUAL, 216.0 * (double)d.N * k * nact);
         k_mx_residual_inc<false><<<rgrid, kResThreads, kResSmem, s>>>(
             d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<cplx>(w, B_R64), buf<double>(w, B_PART),
-            buf<int>(w, B_ACTIVE), nullptr, nullptr, Qp, coef);
+            buf<int>(w, B_ACTIVE), nullptr, nullptr);
         prof::end(s, prof::FF_RESIDUAL);
       }
     }
@@ -2250,7 +2280,7 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
     if (steps >= ir_max) return "iterative refinement did not reach the tolerance";
     cudaMemcpyAsync(w.bufs[B_ACTIVE], active.data(), sizeof(int) * Ne, cudaMemcpyHostToDevice, s);
     // only the unconverged nodes are swept again
-    if (const char* m = solve_once(s, d, Z, A27, B27, w, nullptr, buf<f2>(w, B_RC), active,
+    if (const char* m = solve_once(s, d, Z, A27, B27, w, nullptr, buf<f2>(w, B_RC), active, QuadOut{Qp, coef, 0},
                                    stats, status))
       return m;
     if (G) {
@@ -2456,13 +2486,13 @@ const char* mixed_loop(cudaStream_t s, Grid g, int Ne, const cplx* Z, const doub
       k_loop_begin<<<1, 64, 0, cs2>>>(st, lp.ir_tol, lp.early, active, Ne);
       prof::count_launch();
       hooks.rhs(cs2);
-      msg = solve_direct(cs2, d, Z, A27, B27, w, RHS, nullptr, all, status, active);
+      msg = solve_direct(cs2, d, Z, A27, B27, w, RHS, nullptr, all, QuadOut{Qp, coef, 1}, status, active);
       k_mx_residual<<<rgrid, kResThreads, kResSmem, cs2>>>(d, Z, A27, B27, RHS, buf<f2>(w, B_GC), buf<f2>(w, B_RC),
                                                             buf<cplx>(w, B_R64), buf<double>(w, B_PART), active,
-                                                            &st->ir_target, Qp, coef);
+                                                            &st->ir_target);
       k_mx_residual_inc<true><<<rgrid, kResThreads, kResSmem, cs2>>>(
           d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<cplx>(w, B_R64), buf<double>(w, B_PART), active,
-          RHS, &st->ir_target, Qp, coef);
+          RHS, &st->ir_target);
       k_mx_resnorm<<<Ne, 256, 0, cs2>>>(Ne, nblk, buf<double>(w, B_PART), buf<double>(w, B_REL), active);
       k_ir_control<<<1, 32, 0, cs2>>>(st, buf<double>(w, B_REL), active, Ne, lp.ir_max, lp.ir_tol, more);
       prof::count_launch(4);
@@ -2472,11 +2502,11 @@ const char* mixed_loop(cudaStream_t s, Grid g, int Ne, const cplx* Z, const doub
       c3 = ce == cudaSuccess;
       if (c3 && !msg) {
         n_inner0 = prof::launches();
-        msg = solve_direct(cs3, d, Z, A27, B27, w, nullptr, buf<f2>(w, B_RC), all, status,
+        msg = solve_direct(cs3, d, Z, A27, B27, w, nullptr, buf<f2>(w, B_RC), all, QuadOut{Qp, coef, 0}, status,
                            active);
         k_mx_residual_inc<false><<<rgrid, kResThreads, kResSmem, cs3>>>(
             d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<cplx>(w, B_R64), buf<double>(w, B_PART), active,
-            nullptr, nullptr, Qp, coef);
+            nullptr, nullptr);
         k_mx_resnorm<<<Ne, 256, 0, cs3>>>(Ne, nblk, buf<double>(w, B_PART), buf<double>(w, B_REL), active);
         k_ir_control<<<1, 32, 0, cs3>>>(st, buf<double>(w, B_REL), active, Ne, lp.ir_max, lp.ir_tol, more);
         prof::count_launch(3);
