@@ -24,6 +24,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -2002,22 +2004,27 @@ float time_solve_gemm(cudaStream_t s, const Dims& d0, MixedWork& w, int* status)
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
+  // rounds of kTuneRun back-to-back launches on successive layers, as a
+  // sweep issues them; the first round warms up, the fastest later one counts
+  constexpr int kTuneRun = 8, kTuneRounds = 3;
   float best = 1e30f;
-  for (int rep = 0; rep < 4; ++rep) {
-    const int t = rep % d.nz;
-    geo.a_row0 = t * d.n;
-    geo.a_row0_hi = (d.nz - 1 - t) * d.n;
+  for (int round = 0; round < kTuneRounds; ++round) {
     cudaEventRecord(a, s);
-    launch_tc<2 * CB, ST>(s, dim3(d.nblkCB, cdiv(d.n, 128), V), tmF, tmB, geo, epi, status);
+    for (int r = 0; r < kTuneRun; ++r) {
+      const int t = (round * kTuneRun + r) % d.nz;
+      geo.a_row0 = t * d.n;
+      geo.a_row0_hi = (d.nz - 1 - t) * d.n;
+      launch_tc<2 * CB, ST>(s, dim3(d.nblkCB, cdiv(d.n, 128), V), tmF, tmB, geo, epi, status);
+    }
     cudaEventRecord(b, s);
     cudaEventSynchronize(b);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, a, b);
-    if (rep > 0) best = std::min(best, ms);   // first launch warms up
+    if (round > 0) best = std::min(best, ms);
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  prof::count_launch(4);
+  prof::count_launch(kTuneRun * kTuneRounds);
   return best;
 }
 
@@ -2034,6 +2041,21 @@ int tuned_cfg(cudaStream_t s, const Dims& d, MixedWork& w, int* status) {
       if (kv.first == key) return kv.second;
   }
   int best_cfg = cfg_of(d.CB, d.ST);
+  // FEAST_SOLVE_TILE="CBxST" (e.g. 64x3) fixes the configuration instead of
+  // timing the candidates (reproducible profiles; timings under a profiler
+  // mean nothing)
+  if (const char* env = std::getenv("FEAST_SOLVE_TILE")) {
+    int cb = 0, st = 0;
+    if (std::sscanf(env, "%dx%d", &cb, &st) == 2) {
+      const int cfg = cfg_of(cb, st);
+      if (cfg == cfg_of(8, 4) || cfg == cfg_of(16, 4) || cfg == cfg_of(32, 4) || cfg == cfg_of(64, 3) ||
+          cfg == cfg_of(64, 4)) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tuned.push_back({key, cfg});
+        return cfg;
+      }
+    }
+  }
   float best = 1e30f;
   auto consider = [&](int cfg, float ms) {
     if (ms < best) {
