@@ -28,6 +28,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "mixed.cuh"
@@ -967,6 +968,8 @@ __global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, Chains ch, int ha
                                                        const f2* __restrict__ Rc, const f2* __restrict__ Tout,
                                                        f2* __restrict__ Gc, float* __restrict__ Bemb, NodeList nl,
                                                        const int* __restrict__ active) {
+  tc::grid_dep_wait();   // under programmatic dependent launch: the previous product is complete
+  tc::grid_dep_launch_dependents();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const int m0 = blockIdx.y * kCoupleCols, v = tc::nth_set_bit(nl.mask, (int)blockIdx.z);
   if (p >= d.n) return;
@@ -1013,6 +1016,8 @@ __global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, Chains ch, int ha
 __global__ void __launch_bounds__(128) k_mx_couple_bwd(Dims d, Chains ch, const f2* __restrict__ Cf,
                                                        const f2* __restrict__ Gc, float* __restrict__ Bemb,
                                                        NodeList nl, const int* __restrict__ active) {
+  tc::grid_dep_wait();   // as in the forward coupling
+  tc::grid_dep_launch_dependents();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const int m0 = blockIdx.y * kCoupleCols, v = tc::nth_set_bit(nl.mask, (int)blockIdx.z);
   if (p >= d.n) return;
@@ -1357,11 +1362,34 @@ cudaError_t tc_attr() {
       cudaErrorInvalidDevice);
 }
 
+#ifndef FEAST_PDL
+#define FEAST_PDL 1
+#endif
+// Launch with programmatic stream serialisation: the grid may start (and run
+// its set-up up to grid_dep_wait) while the previous grid in the stream
+// drains.  Used for the chains of dependent launches of the solve sweeps.
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = FEAST_PDL;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <int BN, int STAGES, class Epi>
 cudaError_t launch_tc(cudaStream_t s, dim3 grid, const CUtensorMap& a, const CUtensorMap& b, tc::Geom geo,
-                      const Epi& epi, int* status) {
+                      const Epi& epi, int* status, bool pdl = false) {
   constexpr size_t smem = tc::smem_bytes<BN, STAGES, Epi>();
   if (const cudaError_t e = tc_attr<BN, STAGES, Epi>()) return e;
+  if (pdl) return launch_pdl(tc::k_tc_gemm<BN, STAGES, Epi>, grid, dim3(tc::kThreads), smem, s, a, b, geo, epi, status);
   tc::k_tc_gemm<BN, STAGES, Epi><<<grid, tc::kThreads, smem, s>>>(a, b, geo, epi, status);
   return cudaGetLastError();
 }
@@ -1923,7 +1951,8 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     prof::begin(s, prof::SOLVE_GEMM);
     prof::add_work(prof::SOLVE_GEMM, 8.0 * d.n * (double)d.n * d.k * vl.count);
     const bool ok =
-        launch_tc<2 * CB, ST>(s, dim3(d.nblkCB, cdiv(d.n, 128), vl.count), tmF, tmB, geo, epi, status) == cudaSuccess;
+        launch_tc<2 * CB, ST>(s, dim3(d.nblkCB, cdiv(d.n, 128), vl.count), tmF, tmB, geo, epi, status, true) ==
+        cudaSuccess;
     prof::end(s, prof::SOLVE_GEMM);
     return ok;
   };
@@ -1949,8 +1978,8 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     const NodeList& vl = t < L1 ? both : one;
     prof::begin(s, prof::COUPLE);
     prof::add_work(prof::COUPLE, couple_bytes(vl.count, 40.0));
-    k_mx_couple_fwd<false><<<dim3(cdiv(d.n, 128), cdiv(d.k, kCoupleCols), vl.count), 128, 0, s>>>(
-        d, ch, t > 0, 0, 0, Cf, Rreal, Rc, Tout, Gc, Bemb, vl, dactive);
+    launch_pdl(k_mx_couple_fwd<false>, dim3(cdiv(d.n, 128), cdiv(d.k, kCoupleCols), vl.count), dim3(128), 0, s, d, ch,
+               t > 0 ? 1 : 0, 0, 0, Cf, Rreal, Rc, Tout, Gc, Bemb, vl, dactive);
     prof::end(s, prof::COUPLE);
     SolveEpi<CB> epi{Tout, (long long)d.n * d.k, d.n, d.n, d.k, 1.0f};
     if (!gemm(vl, t, d.nz - 1 - t, epi)) return "tcgen05 solve launch failed";
@@ -1961,8 +1990,8 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     const Chains ch{Ne, {K, K}, {0, 0}, 0};
     prof::begin(s, prof::COUPLE);
     prof::add_work(prof::COUPLE, couple_bytes(one.count, L1 > 0 ? 48.0 : 40.0));
-    k_mx_couple_fwd<true><<<dim3(cdiv(d.n, 128), cdiv(d.k, kCoupleCols), one.count), 128, 0, s>>>(
-        d, ch, L0 > 0, 1, L1 > 0, Cf, Rreal, Rc, Tout, Gc, Bemb, one, dactive);
+    launch_pdl(k_mx_couple_fwd<true>, dim3(cdiv(d.n, 128), cdiv(d.k, kCoupleCols), one.count), dim3(128), 0, s, d,
+               ch, L0 > 0 ? 1 : 0, 1, L1 > 0 ? 1 : 0, Cf, Rreal, Rc, Tout, Gc, Bemb, one, dactive);
     prof::end(s, prof::COUPLE);
     if (!gemm(one, K, K, back_epi(ch))) return "tcgen05 solve launch failed";
     launches += 2;
@@ -1973,8 +2002,8 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     const NodeList& vl = u < L1 ? both : one;
     prof::begin(s, prof::COUPLE);
     prof::add_work(prof::COUPLE, couple_bytes(vl.count, 32.0));
-    k_mx_couple_bwd<<<dim3(cdiv(d.n, 128), cdiv(d.k, kCoupleCols), vl.count), 128, 0, s>>>(d, ch, Cf, Gc, Bemb, vl,
-                                                                                          dactive);
+    launch_pdl(k_mx_couple_bwd, dim3(cdiv(d.n, 128), cdiv(d.k, kCoupleCols), vl.count), dim3(128), 0, s, d, ch, Cf,
+               Gc, Bemb, vl, dactive);
     prof::end(s, prof::COUPLE);
     if (!gemm(vl, K - 1 - u, K + 1 + u, back_epi(ch))) return "tcgen05 solve launch failed";
     launches += 2;

@@ -121,6 +121,15 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
+// Programmatic dependent launch: wait until the grid this one was launched
+// after (with programmatic stream serialisation) has completed and its
+// memory is visible; then let the next such grid start its own prologue.
+// Both are no-ops for a grid launched the ordinary way.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -299,7 +308,6 @@ __global__ void __launch_bounds__(kThreads)
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int e = geo.node_mask ? nth_set_bit(geo.node_mask, (int)blockIdx.z) : (int)blockIdx.z;
-  if (geo.active && !geo.active[geo.split > 0 && e >= geo.split ? e - geo.split : e]) return;   // uniform per CTA
   const int tm = blockIdx.y;
   int tn = (int)blockIdx.x + geo.tn_base;
   if (geo.tn_skip >= 0 && tn >= geo.tn_skip) ++tn;
@@ -318,8 +326,16 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // the set-up above overlaps the previous grid's tail under programmatic
+  // dependent launch; everything below may read its results
+  grid_dep_wait();
+  grid_dep_launch_dependents();
+  // a CTA of a node that the device-side refinement left out does nothing
+  // (uniform per CTA)
+  const bool skip = geo.active && !geo.active[geo.split > 0 && e >= geo.split ? e - geo.split : e];
 
-  if (warp == 0) {
+  if (skip) {
+  } else if (warp == 0) {
     if (lane == 0) {
       const bool hi = geo.split > 0 && e >= geo.split;
       const int ay = (hi ? geo.a_row0_hi + (e - geo.split) * geo.a_batch : geo.a_row0 + e * geo.a_batch) + tm * kBlockM;
