@@ -51,9 +51,6 @@ TRAFFIC = {
     # wide sweep update: 15 regular launches and the last panel's (which also
     # writes the TF32 solve copy) per layer
     "sweep_gemm": (15 * (158.4 + 68.1) + (167.9 + 207.7)) / 16 * 1e6,
-    "fp64_residual": (486.1 + 556.6) * 1e6 * 400 / 24,
-    # the later (incremental) residuals, 12 of the 14 launches of a solve
-    "ff_residual": (662.3 + 546.8) * 1e6 * 400 / 24,
 }
 
 

@@ -1085,15 +1085,16 @@ constexpr size_t kResSmem = sizeof(cplx) * 27 * kResRows;
 // only FP64 arithmetic of the kernel) for the first solve's Q_e, which is its
 // complex64 sweep output exactly: the block's 128 rows keep their 27
 // complex coefficients in shared memory while the threads sweep the columns.
-// Stores R in FP64 (R64, the start of the incremental residuals) and as
-// complex64 (the next correction's right-hand side), and per-block partial
-// sums of |R|^2 and |RHS|^2.
+// Stores R as a double-float pair, Rc + Rlo (Rc: the complex64 leading part,
+// the next correction's right-hand side; Rlo: the trailing part; together the
+// start of the incremental residuals), and per-block partial sums of |R|^2 and
+// |RHS|^2.
 __global__ void __launch_bounds__(kResThreads) k_mx_residual(Dims d, const cplx* __restrict__ Z,
                                                              const double* __restrict__ A27,
                                                              const double* __restrict__ B27,
                                                              const double* __restrict__ RHS,
                                                              const f2* __restrict__ Q, f2* __restrict__ Rc,
-                                                             cplx* __restrict__ R64, double* __restrict__ partial,
+                                                             f2* __restrict__ Rlo, double* __restrict__ partial,
                                                              const int* __restrict__ active,
                                                              const double* __restrict__ target) {
   extern __shared__ cplx rsm[];
@@ -1147,8 +1148,10 @@ __global__ void __launch_bounds__(kResThreads) k_mx_residual(Dims d, const cplx*
         aim = fma(-c.re, v.im, aim);
         aim = fma(-c.im, v.re, aim);
       }
-      Rc[e * sG + (long long)m * d.N + i] = f2{f64_to_f32_trunc(are), f64_to_f32_trunc(aim)};
-      R64[e * sG + (long long)m * d.N + i] = cplx{are, aim};
+      const float hre = f64_to_f32_trunc(are), him = f64_to_f32_trunc(aim);
+      Rc[e * sG + (long long)m * d.N + i] = f2{hre, him};
+      Rlo[e * sG + (long long)m * d.N + i] =
+          f2{f64_to_f32_trunc(are - f32_to_f64(hre)), f64_to_f32_trunc(aim - f32_to_f64(him))};
       rr += are * are + aim * aim;
       bb += b * b;
     }
@@ -1183,6 +1186,24 @@ __global__ void __launch_bounds__(kResThreads) k_mx_residual(Dims d, const cplx*
 // (SIAM J. Sci. Comput. 26, 2005) with the low coefficient part folded into the
 // error term.  The rounding-explicit intrinsics keep the compiler from fusing
 // the product into the sum, which would break the exact error terms.
+// Knuth's TwoSum: a + b = s + err exactly.
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+  return s;
+}
+
+// (h, l) <- (h + l) - (ph + pl) in double-float: the leading parts by TwoSum,
+// the trailing parts and its error added, then renormalised by TwoSum.
+__device__ __forceinline__ void ff_sub(float& h, float& l, float ph, float pl) {
+  float e1, e2;
+  const float sh = two_sum(h, -ph, e1);
+  const float t = __fadd_rn(__fsub_rn(l, pl), e1);
+  h = two_sum(sh, t, e2);
+  l = e2;
+}
+
 __device__ __forceinline__ void ff_axpy(float ch, float cl, float v, float& sh, float& sl) {
   const float p = __fmul_rn(ch, v);
   const float pe = __fmaf_rn(ch, v, -p);            // ch * v = p + pe exactly
@@ -1193,10 +1214,13 @@ __device__ __forceinline__ void ff_axpy(float ch, float cl, float v, float& sh, 
   sl = __fadd_rn(sl, __fadd_rn(err, __fmaf_rn(cl, v, pe)));
 }
 
-// R64 <- R64 - (Z_e B - A) delta, Rc <- complex64(R64), partial |R|^2 per block
-// (the |RHS|^2 partials of the first residual are kept).
+// R <- R - (Z_e B - A) delta with R = Rc + Rlo held as a double-float pair
+// (Rc, its complex64 leading part, is the next correction's right-hand side),
+// partial |R|^2 per block (the |RHS|^2 partials of the first residual are
+// kept).  The update itself stays in fp32 arithmetic: the FP64 pipe only
+// squares the leading parts for the norm.
 // kFirst: the first residual of a solve whose target is loose (>= 1e-9
-// relative): R64 starts from RHS instead, delta is the first solution Q_e,
+// relative): R starts from RHS instead, delta is the first solution Q_e,
 // and the |RHS|^2 partials are written.  The product's error, ~2^-48 kappa
 // ||Q_e|| (kappa ~ 300 here), is then far below the target.
 template <bool kFirst>
@@ -1204,7 +1228,7 @@ __global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, cons
                                                                  const double* __restrict__ A27,
                                                                  const double* __restrict__ B27,
                                                                  const f2* __restrict__ delta, f2* __restrict__ Rc,
-                                                                 cplx* __restrict__ R64, double* __restrict__ partial,
+                                                                 f2* __restrict__ Rlo, double* __restrict__ partial,
                                                                  const int* __restrict__ active,
                                                                  const double* __restrict__ RHS,
                                                                  const double* __restrict__ target) {
@@ -1288,19 +1312,22 @@ __global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, cons
         if (!has[j]) continue;
         const int mj = m + j * kGroups;
         const long long at = e * sG + (long long)mj * d.N + i;
-        cplx R;
+        f2 H, L;   // R = H + L
         if constexpr (kFirst) {
           const double b = RHS[(long long)mj * d.N + i];
-          R = cplx{b, 0.0};
-          bb += b * b;
+          H = f2{(float)b, 0.f};
+          L = f2{(float)(b - (double)H.x), 0.f};
+          bb = fma(b, b, bb);
         } else {
-          R = R64[at];
+          H = Rc[at];
+          L = Rlo[at];
         }
-        R.re -= (double)rh[j] + (double)rl[j];
-        R.im -= (double)ih[j] + (double)il[j];
-        R64[at] = R;
-        Rc[at] = f2{(float)R.re, (float)R.im};
-        rr += R.re * R.re + R.im * R.im;
+        ff_sub(H.x, L.x, rh[j], rl[j]);
+        ff_sub(H.y, L.y, ih[j], il[j]);
+        Rc[at] = H;
+        Rlo[at] = L;
+        const double hx = H.x, hy = H.y;
+        rr = fma(hx, hx, fma(hy, hy, rr));
       }
     }
   }
@@ -1395,7 +1422,7 @@ cudaError_t launch_tc(cudaStream_t s, dim3 grid, const CUtensorMap& a, const CUt
 }
 
 enum Buf { B_F = 0, B_T1, B_AOP, B_BOP, B_TC, B_PINV, B_GC, B_RC, B_BEMB, B_TOUT, B_PART, B_REL, B_ACTIVE, B_CF, B_FW,
-           B_R64, B_COUNT };
+           B_RLO, B_COUNT };
 static_assert(B_COUNT <= 16, "MixedWork holds 16 buffers");
 
 bool ensure(MixedWork& w, int idx, size_t bytes, cudaStream_t s, bool zero = false) {
@@ -2233,7 +2260,7 @@ static const char* solve_prepare(cudaStream_t s, Grid g, int Ne, int k, MixedWor
   if (!ensure(w, B_PART, sizeof(double) * 2 * (size_t)Ne * nblk, s)) return "out of device memory";
   if (!ensure(w, B_REL, sizeof(double) * Ne, s)) return "out of device memory";
   if (!ensure(w, B_ACTIVE, sizeof(int) * Ne, s)) return "out of device memory";
-  if (!ensure(w, B_R64, sizeof(cplx) * (size_t)Ne * sG, s)) return "out of device memory (residuals)";
+  if (!ensure(w, B_RLO, sizeof(f2) * (size_t)Ne * sG, s)) return "out of device memory (residuals)";
   *dout = d;
   return nullptr;
 }
@@ -2291,7 +2318,7 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
         prof::begin(s, prof::FF_RESIDUAL);
         prof::add_work(prof::FF_RESIDUAL, 216.0 * (double)d.N * k * nact);
         k_mx_residual_inc<true><<<rgrid, kResThreads, kResSmem, s>>>(
-            d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<cplx>(w, B_R64), buf<double>(w, B_PART),
+            d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<f2>(w, B_RLO), buf<double>(w, B_PART),
             buf<int>(w, B_ACTIVE), RHS, nullptr);
         prof::end(s, prof::FF_RESIDUAL);
       } else if (steps == 0) {
@@ -2299,7 +2326,7 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
         prof::begin(s, prof::RESIDUAL);
         prof::add_work(prof::RESIDUAL, 216.0 * (double)d.N * k * nact);   // 108 FP64 FMAs per complex entry
         k_mx_residual<<<rgrid, kResThreads, kResSmem, s>>>(d, Z, A27, B27, RHS, buf<f2>(w, B_GC), buf<f2>(w, B_RC),
-                                                           buf<cplx>(w, B_R64), buf<double>(w, B_PART),
+                                                           buf<f2>(w, B_RLO), buf<double>(w, B_PART),
                                                            buf<int>(w, B_ACTIVE), nullptr);
         prof::end(s, prof::RESIDUAL);
       } else {
@@ -2307,7 +2334,7 @@ const char* mixed_solve(cudaStream_t s, Grid g, int Ne, const cplx* Z, const dou
         prof::begin(s, prof::FF_RESIDUAL);
         prof::add_work(prof::FF_RESIDUAL, 216.0 * (double)d.N * k * nact);
         k_mx_residual_inc<false><<<rgrid, kResThreads, kResSmem, s>>>(
-            d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<cplx>(w, B_R64), buf<double>(w, B_PART),
+            d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<f2>(w, B_RLO), buf<double>(w, B_PART),
             buf<int>(w, B_ACTIVE), nullptr, nullptr);
         prof::end(s, prof::FF_RESIDUAL);
       }
@@ -2495,7 +2522,7 @@ const char* mixed_loop(cudaStream_t s, Grid g, int Ne, const cplx* Z, const doub
   }
   // the buffers and the tile width of the shape were set by the host-driven run
   Dims d = make_dims(g, Ne, k);
-  if (w.nz_factored != d.nz || w.ne_factored != Ne || !w.bufs[B_GC] || !w.bufs[B_R64]) return kNotCaptured;
+  if (w.nz_factored != d.nz || w.ne_factored != Ne || !w.bufs[B_GC] || !w.bufs[B_RLO]) return kNotCaptured;
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     const long long tkey = ((long long)d.n << 32) ^ ((long long)d.k << 8) ^ d.Ne;
@@ -2539,10 +2566,10 @@ const char* mixed_loop(cudaStream_t s, Grid g, int Ne, const cplx* Z, const doub
       hooks.rhs(cs2);
       msg = solve_direct(cs2, d, Z, A27, B27, w, RHS, nullptr, all, QuadOut{Qp, coef, 1}, status, active);
       k_mx_residual<<<rgrid, kResThreads, kResSmem, cs2>>>(d, Z, A27, B27, RHS, buf<f2>(w, B_GC), buf<f2>(w, B_RC),
-                                                            buf<cplx>(w, B_R64), buf<double>(w, B_PART), active,
+                                                            buf<f2>(w, B_RLO), buf<double>(w, B_PART), active,
                                                             &st->ir_target);
       k_mx_residual_inc<true><<<rgrid, kResThreads, kResSmem, cs2>>>(
-          d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<cplx>(w, B_R64), buf<double>(w, B_PART), active,
+          d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<f2>(w, B_RLO), buf<double>(w, B_PART), active,
           RHS, &st->ir_target);
       k_mx_resnorm<<<Ne, 256, 0, cs2>>>(Ne, nblk, buf<double>(w, B_PART), buf<double>(w, B_REL), active);
       k_ir_control<<<1, 32, 0, cs2>>>(st, buf<double>(w, B_REL), active, Ne, lp.ir_max, lp.ir_tol, more);
@@ -2556,7 +2583,7 @@ const char* mixed_loop(cudaStream_t s, Grid g, int Ne, const cplx* Z, const doub
         msg = solve_direct(cs3, d, Z, A27, B27, w, nullptr, buf<f2>(w, B_RC), all, QuadOut{Qp, coef, 0}, status,
                            active);
         k_mx_residual_inc<false><<<rgrid, kResThreads, kResSmem, cs3>>>(
-            d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<cplx>(w, B_R64), buf<double>(w, B_PART), active,
+            d, Z, A27, B27, buf<f2>(w, B_GC), buf<f2>(w, B_RC), buf<f2>(w, B_RLO), buf<double>(w, B_PART), active,
             nullptr, nullptr);
         k_mx_resnorm<<<Ne, 256, 0, cs3>>>(Ne, nblk, buf<double>(w, B_PART), buf<double>(w, B_REL), active);
         k_ir_control<<<1, 32, 0, cs3>>>(st, buf<double>(w, B_REL), active, Ne, lp.ir_max, lp.ir_tol, more);
