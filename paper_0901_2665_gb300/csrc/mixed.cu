@@ -779,17 +779,20 @@ struct SolveEpi {
   __device__ long long base(int e, long long stride) const {
     return node_rows ? node_of(ch, e) * stride + (long long)ch.layer[chain_of(ch, e)] * n : e * stride;
   }
-  // the old shares of this thread's row, loaded while the main loop runs
-  // (a refinement step reads them back)
+  // the old shares of this thread's row (a refinement step reads them back):
+  // the first kPre columns are loaded while the main loop runs; a wider tile
+  // loads each later group of 16 columns kPre columns ahead, inside the
+  // epilogue loop, into the register slots the finished group frees
+  static constexpr int kPre = CB <= 32 ? CB : 32;
   struct Pre {
-    double q[CB];
+    double q[kPre];
   };
   __device__ void prefetch(int e, int tm, int tn, int row, Pre& pre) const {
     const int p = tm * tc::kBlockM + row;
     const bool rd = qp && !qfirst && p < n;
     const double* q = qp ? qp + base(e, sQ) : nullptr;
 #pragma unroll
-    for (int t = 0; t < CB; ++t) {
+    for (int t = 0; t < kPre; ++t) {
       const int m = tn * CB + t;
       pre.q[t] = (rd && m < k) ? q[(long long)m * ldq + p] : 0.0;
     }
@@ -798,22 +801,35 @@ struct SolveEpi {
     const int p = tm * tc::kBlockM + row;
     f2* o = out + base(e, sOut);
     double* q = qp ? qp + base(e, sQ) : nullptr;
+    const bool rd = q && !qfirst && p < n;
     cplx ce{0.0, 0.0};
     if (qp) ce = coef[node_of(ch, e)];
+    double ring[kPre];
+#pragma unroll
+    for (int t = 0; t < kPre; ++t) ring[t] = pre.q[t];
 #pragma unroll
     for (int c0 = 0; c0 < CB; c0 += 16) {
       float re[16], im[16];
       tc::tmem_ld16(taddr + c0, re);
       tc::tmem_ld16(taddr + CB + c0, im);
       if (p >= n) continue;
+      constexpr int kW = CB < 16 ? CB : 16;
+      const int slot = c0 % kPre;
 #pragma unroll
-      for (int t = 0; t < 16; ++t) {
+      for (int t = 0; t < kW; ++t) {
         const int m = tn * CB + c0 + t;
-        if (c0 + t < CB && m < k) {
+        if (m < k) {
           const f2 x{alpha * re[t], alpha * im[t]};
           o[(long long)m * ldo + p] = x;
           // two FP64 FMAs; the conversions run on the integer pipe
-          if (q) q[(long long)m * ldq + p] = fma(ce.re, f32_to_f64(x.x), fma(-ce.im, f32_to_f64(x.y), pre.q[c0 + t]));
+          if (q) q[(long long)m * ldq + p] = fma(ce.re, f32_to_f64(x.x), fma(-ce.im, f32_to_f64(x.y), ring[slot + t]));
+        }
+      }
+      if (CB > kPre && c0 + kPre < CB) {
+#pragma unroll
+        for (int t = 0; t < kW; ++t) {
+          const int m = tn * CB + c0 + kPre + t;
+          ring[slot + t] = (rd && m < k) ? q[(long long)m * ldq + p] : 0.0;
         }
       }
     }
@@ -2089,7 +2105,22 @@ std::vector<std::pair<long long, int>> g_tuned;   // (n, k, Ne) key -> CB | ST <
 
 constexpr int cfg_of(int cb, int st) { return cb | st << 8; }
 
+// FEAST_SOLVE_TILE="CBxST" (e.g. 64x3) fixes the configuration of every
+// solve that starts while it is set, instead of timing the candidates
+// (reproducible profiles, since timings under a profiler mean nothing, and
+// tests of every configuration); 0 when unset or not a built configuration.
+int forced_cfg() {
+  const char* env = std::getenv("FEAST_SOLVE_TILE");
+  int cb = 0, st = 0;
+  if (!env || std::sscanf(env, "%dx%d", &cb, &st) != 2) return 0;
+  const int cfg = cfg_of(cb, st);
+  const bool built = cfg == cfg_of(8, 4) || cfg == cfg_of(16, 4) || cfg == cfg_of(32, 4) || cfg == cfg_of(64, 3) ||
+                     cfg == cfg_of(64, 4);
+  return built ? cfg : 0;
+}
+
 int tuned_cfg(cudaStream_t s, const Dims& d, MixedWork& w, int* status) {
+  if (const int cfg = forced_cfg()) return cfg;
   const long long key = ((long long)d.n << 32) ^ ((long long)d.k << 8) ^ d.Ne;
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -2097,21 +2128,6 @@ int tuned_cfg(cudaStream_t s, const Dims& d, MixedWork& w, int* status) {
       if (kv.first == key) return kv.second;
   }
   int best_cfg = cfg_of(d.CB, d.ST);
-  // FEAST_SOLVE_TILE="CBxST" (e.g. 64x3) fixes the configuration instead of
-  // timing the candidates (reproducible profiles; timings under a profiler
-  // mean nothing)
-  if (const char* env = std::getenv("FEAST_SOLVE_TILE")) {
-    int cb = 0, st = 0;
-    if (std::sscanf(env, "%dx%d", &cb, &st) == 2) {
-      const int cfg = cfg_of(cb, st);
-      if (cfg == cfg_of(8, 4) || cfg == cfg_of(16, 4) || cfg == cfg_of(32, 4) || cfg == cfg_of(64, 3) ||
-          cfg == cfg_of(64, 4)) {
-        std::lock_guard<std::mutex> lock(g_tune_mutex);
-        g_tuned.push_back({key, cfg});
-        return cfg;
-      }
-    }
-  }
   float best = 1e30f;
   auto consider = [&](int cfg, float ms) {
     if (ms < best) {
@@ -2526,9 +2542,10 @@ const char* mixed_loop(cudaStream_t s, Grid g, int Ne, const cplx* Z, const doub
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     const long long tkey = ((long long)d.n << 32) ^ ((long long)d.k << 8) ^ d.Ne;
-    int cfg = 0;
-    for (auto& kv : g_tuned)
-      if (kv.first == tkey) cfg = kv.second;
+    int cfg = forced_cfg();
+    if (!cfg)
+      for (auto& kv : g_tuned)
+        if (kv.first == tkey) cfg = kv.second;
     if (!cfg) return kNotCaptured;
     d = make_dims(g, Ne, k, cfg);
   }

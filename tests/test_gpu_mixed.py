@@ -79,6 +79,39 @@ def test_node_solve_mixed_full_cross_section_matches_oracle():
         assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
 
 
+SOLVE_TILES = ["16x4", "32x4", "64x3", "64x4"]
+
+
+@pytest.mark.parametrize("nx,ny,nz,k", [(32, 32, 3, 128), (16, 12, 5, 100)])
+def test_node_solve_mixed_every_solve_tile(monkeypatch, nx, ny, nz, k):
+    """Every built configuration of the solve GEMM (complex columns per CTA
+    tile x pipeline stages; the autotuner picks one by timing) solves to the
+    same bar: 32x32 (eight full row tiles) and 16x12 (a ragged row
+    tile; 100 columns: a ragged column tile at every width)."""
+    op = workloads.q1_operator(nx, ny, nz, workloads.gaussian_potential(4, 3, nx, ny, nz))
+    lam = oracle.closed_form_eigenvalues_v0(nx, ny, nz)
+    lmin, lmax = lam[0] - 3.0, lam[20]
+    _, _, _, Z, _ = oracle.contour_points(lmin, lmax, 8)
+    RHS = np.random.default_rng(k).standard_normal((op.N, k))
+    A = oracle.assemble(op.A27, nx, ny, nz)
+    B = oracle.assemble(op.B27, nx, ny, nz)
+    z = Z[1]
+    M = (z * B - A).astype(np.complex128)
+    ref = oracle.block_tridiag_factor(M, op.n, nz).solve(RHS.astype(np.complex128))
+    dop, keep = dev_op(op)
+    h = F().Handle(precision=F().FEAST_PREC_MIXED)
+    for tile in SOLVE_TILES:
+        monkeypatch.setenv("FEAST_SOLVE_TILE", tile)
+        Qe = torch.zeros((k, op.N), dtype=torch.complex128, device="cuda")
+        info = h.feast_node_solve(dop, complex(z), cm(RHS), Qe, k, precision=F().FEAST_PREC_MIXED)
+        got = back(Qe)
+        res = np.linalg.norm(M @ got - RHS) / np.linalg.norm(RHS)
+        assert res <= 1e-12, (tile, res)
+        assert info.ir_resid_max <= 1e-12, tile
+        assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max(), tile
+    h.close()
+
+
 def test_quadrature_mixed_matches_oracle():
     nx, ny, nz, G, seed = GRIDS[0]
     op = workloads.q1_operator(nx, ny, nz, workloads.gaussian_potential(G, seed, nx, ny, nz))
