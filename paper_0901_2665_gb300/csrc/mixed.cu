@@ -1086,15 +1086,22 @@ __global__ void k_mx_accumulate(long long total, int first, const f2* __restrict
   }
 }
 
-constexpr int kResRows = 128;      // grid rows per block
+#ifndef FEAST_RES_ROWS
+#define FEAST_RES_ROWS 128
+#endif
+constexpr int kResRows = FEAST_RES_ROWS;   // grid rows per block
 // Refinement targets at or above this take their first residual in
 // double-float as well (its error, ~1e-12 of ||RHS||, is far below them).
 constexpr double kFFirstTol = 1e-9;
 constexpr int kResThreads = 256;   // two column groups per row
 #ifndef FEAST_RES_COLS
-#define FEAST_RES_COLS 4
+#define FEAST_RES_COLS 3
 #endif
 constexpr int kResCols = FEAST_RES_COLS;   // columns per pass of a thread in the double-float residual
+#ifndef FEAST_RES_MIN_BLOCKS
+#define FEAST_RES_MIN_BLOCKS 3
+#endif
+constexpr int kResMinBlocks = FEAST_RES_MIN_BLOCKS;   // resident CTAs per SM the register budget allows
 constexpr size_t kResSmem = sizeof(cplx) * 27 * kResRows;
 
 // R_e = RHS - (Z_e B - A) Q_e in FP64 (108 FP64 FMAs per complex entry, the
@@ -1240,7 +1247,7 @@ __device__ __forceinline__ void ff_axpy(float ch, float cl, float v, float& sh, 
 // and the |RHS|^2 partials are written.  The product's error, ~2^-48 kappa
 // ||Q_e|| (kappa ~ 300 here), is then far below the target.
 template <bool kFirst>
-__global__ void __launch_bounds__(kResThreads, 2) k_mx_residual_inc(Dims d, const cplx* __restrict__ Z,
+__global__ void __launch_bounds__(kResThreads, kResMinBlocks) k_mx_residual_inc(Dims d, const cplx* __restrict__ Z,
                                                                  const double* __restrict__ A27,
                                                                  const double* __restrict__ B27,
                                                                  const f2* __restrict__ delta, f2* __restrict__ Rc,
