@@ -771,6 +771,7 @@ struct SolveEpi {
   long long sQ = 0, ldq = 0;   // node stride, column stride
   const cplx* coef = nullptr;  // Ne quadrature coefficients
   int qfirst = 0;              // 1: store (first solve), 0: accumulate (refinement)
+  int share_chains = 3;        // chains (bit c) whose rows add their shares here
   // node_rows: out and qp belong to the real node of virtual node e, at the
   // rows of its chain's layer (the backward sweep); else out is per virtual
   // node (the forward products)
@@ -787,10 +788,11 @@ struct SolveEpi {
   struct Pre {
     double q[kPre];
   };
+  __device__ bool shares(int e) const { return qp && ((share_chains >> chain_of(ch, e)) & 1); }
   __device__ void prefetch(int e, int tm, int tn, int row, Pre& pre) const {
     const int p = tm * tc::kBlockM + row;
-    const bool rd = qp && !qfirst && p < n;
-    const double* q = qp ? qp + base(e, sQ) : nullptr;
+    const bool rd = shares(e) && !qfirst && p < n;
+    const double* q = shares(e) ? qp + base(e, sQ) : nullptr;
 #pragma unroll
     for (int t = 0; t < kPre; ++t) {
       const int m = tn * CB + t;
@@ -800,10 +802,10 @@ struct SolveEpi {
   __device__ void operator()(int e, int tm, int tn, int row, uint32_t taddr, int, uint8_t*, const Pre& pre) const {
     const int p = tm * tc::kBlockM + row;
     f2* o = out + base(e, sOut);
-    double* q = qp ? qp + base(e, sQ) : nullptr;
+    double* q = shares(e) ? qp + base(e, sQ) : nullptr;
     const bool rd = q && !qfirst && p < n;
     cplx ce{0.0, 0.0};
-    if (qp) ce = coef[node_of(ch, e)];
+    if (q) ce = coef[node_of(ch, e)];
     double ring[kPre];
 #pragma unroll
     for (int t = 0; t < kPre; ++t) ring[t] = pre.q[t];
@@ -954,10 +956,18 @@ struct NodeList {
   unsigned long long mask;
 };
 
-// Writes the embedded, TF32-rounded RHS rows of complex column m.
-__device__ __forceinline__ void write_emb(const Dims& d, float* Bemb, int e, int p, int m, f2 g) {
+// Row of the embedded operand that holds the real parts of complex column m
+// of virtual node e (the imaginary parts' row is CB further).  The
+// kCoupleCols columns of a coupling thread lie in one CB block (CB is a
+// multiple of kCoupleCols), so their rows are consecutive.
+__device__ __forceinline__ long long emb_row(const Dims& d, int e, int m) {
   const long long blk = (long long)e * d.nblkCB + m / d.CB;
-  const long long rre = blk * 2 * d.CB + (m % d.CB);
+  return blk * 2 * d.CB + (m % d.CB);
+}
+
+// Writes the embedded, TF32-rounded RHS rows of the complex column whose
+// real-part row is rre.
+__device__ __forceinline__ void write_emb(const Dims& d, float* Bemb, long long rre, int p, f2 g) {
   float* re_row = Bemb + rre * d.ldB;
   float* im_row = Bemb + (rre + d.CB) * d.ldB;
   re_row[p] = tc::to_tf32(g.x);
@@ -1004,34 +1014,57 @@ __global__ void __launch_bounds__(128) k_mx_couple_fwd(Dims d, Chains ch, int ha
     c0[t] = has_prev ? Cf[((long long)e * 27 + prev_slot(c) + t) * d.N + row] : f2{0.f, 0.f};
     if constexpr (kTwo) c1[t] = two ? Cf[((long long)e * 27 + prev_slot(1) + t) * d.N + row] : f2{0.f, 0.f};
   }
-  for (int m = m0; m < m0 + kCoupleCols && m < d.k; ++m) {
-    f2 g = Rc ? Rc[e * sG + (long long)m * d.N + row] : f2{(float)Rreal[(long long)m * d.N + row], 0.f};
+  // all columns' loads are independent: a column past k repeats column k - 1
+  // (in bounds) and is not stored
+  f2 g[kCoupleCols];
+#pragma unroll
+  for (int j = 0; j < kCoupleCols; ++j) {
+    const int m = min(m0 + j, d.k - 1);
+    g[j] = Rc ? Rc[e * sG + (long long)m * d.N + row] : f2{(float)Rreal[(long long)m * d.N + row], 0.f};
     if (has_prev) {
       const f2* T = Tout + ((long long)v * d.k + m) * d.n;
 #pragma unroll
-      for (int t = 0; t < 9; ++t) f2fma(g, c0[t], T[off[t]]);
+      for (int t = 0; t < 9; ++t) f2fma(g[j], c0[t], T[off[t]]);
     }
     if constexpr (kTwo) {
       if (two) {
         const f2* T = Tout + ((long long)(v + ch.Ne) * d.k + m) * d.n;
 #pragma unroll
-        for (int t = 0; t < 9; ++t) f2fma(g, c1[t], T[off[t]]);
+        for (int t = 0; t < 9; ++t) f2fma(g[j], c1[t], T[off[t]]);
       }
     }
-    Gc[e * sG + (long long)m * d.N + row] = g;
-    write_emb(d, Bemb, v, p, m, g);
+  }
+  const long long r0 = emb_row(d, v, m0);
+#pragma unroll
+  for (int j = 0; j < kCoupleCols; ++j) {
+    if (m0 + j >= d.k) break;
+    Gc[e * sG + (long long)(m0 + j) * d.N + row] = g[j];
+    write_emb(d, Bemb, r0 + j, p, g[j]);
   }
 }
+
+// Where the backward sweep's quadrature shares go (Eq. 15): node e's share
+// Re{coef_e x} of a layer's solution x is added (first: stored) into qp by
+// the backward coupling that reads x as its x_next, on the FP64 pipe of a
+// kernel that leaves it idle; the layers no later coupling reads (the last
+// of each chain) take theirs in the solve product's epilogue.
+struct BwdShares {
+  double* qp = nullptr;        // [Ne][k][N]; nullptr: no shares
+  const cplx* coef = nullptr;  // Ne quadrature coefficients
+  int first = 0;               // 1: store (first solve), 0: accumulate
+  int mid = -1;                // layer whose share chain 0 alone adds (the middle layer)
+};
 
 // backward: s = g - U x_next on a chain's layer, x_next the solution of the
 // chain's next layer towards the middle (chain 0: layer + 1, coupled through
 // the dz = +1 slots; chain 1: layer - 1, the dz = -1 slots); the embedded s
-// goes to the virtual node's GEMM operand.  A layer without a next one (the
-// last layer of a one-ended elimination) takes s = g.  Threads as in the
-// forward coupling.
+// goes to the virtual node's GEMM operand, and x_next's quadrature share to
+// qs.qp (both chains read the middle layer: chain 0 adds its share).  A
+// layer without a next one (the last layer of a one-ended elimination) takes
+// s = g.  Threads as in the forward coupling.
 __global__ void __launch_bounds__(128) k_mx_couple_bwd(Dims d, Chains ch, const f2* __restrict__ Cf,
                                                        const f2* __restrict__ Gc, float* __restrict__ Bemb,
-                                                       NodeList nl, const int* __restrict__ active) {
+                                                       NodeList nl, const int* __restrict__ active, BwdShares qs) {
   tc::grid_dep_wait();   // as in the forward coupling
   tc::grid_dep_launch_dependents();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1051,18 +1084,42 @@ __global__ void __launch_bounds__(128) k_mx_couple_bwd(Dims d, Chains ch, const 
     off[t] = tap_offset(d, p, t);
     cv[t] = has_next ? Cf[((long long)e * 27 + prev_slot(1 - c) + t) * d.N + row] : f2{0.f, 0.f};
   }
-  for (int m = m0; m < m0 + kCoupleCols && m < d.k; ++m) {
+  const bool share = qs.qp && has_next && (c == 0 || next != qs.mid);
+  f2 sv[kCoupleCols], xn[kCoupleCols];
+#pragma unroll
+  for (int j = 0; j < kCoupleCols; ++j) {
+    const int m = min(m0 + j, d.k - 1);   // as in the forward coupling
     const f2* col = Gc + e * sG + (long long)m * d.N + row;
-    f2 sv = col[0];
+    sv[j] = col[0];
+    xn[j] = f2{0.f, 0.f};
     if (has_next) {
 #pragma unroll
       for (int t = 0; t < 9; ++t) {
         const f2 x = col[dn + off[t]];
-        sv.x -= cv[t].x * x.x - cv[t].y * x.y;
-        sv.y -= cv[t].x * x.y + cv[t].y * x.x;
+        sv[j].x -= cv[t].x * x.x - cv[t].y * x.y;
+        sv[j].y -= cv[t].x * x.y + cv[t].y * x.x;
       }
+      xn[j] = col[dn];   // x_next on this row (the centre tap)
     }
-    write_emb(d, Bemb, v, p, m, sv);
+  }
+  const long long r0 = emb_row(d, v, m0);
+#pragma unroll
+  for (int j = 0; j < kCoupleCols; ++j) {
+    if (m0 + j >= d.k) break;
+    write_emb(d, Bemb, r0 + j, p, sv[j]);
+  }
+  if (share) {
+    const cplx ce = qs.coef[e];
+    double* q = qs.qp + e * sG + (long long)next * d.n + p;
+    double old[kCoupleCols];
+#pragma unroll
+    for (int j = 0; j < kCoupleCols; ++j)
+      old[j] = (qs.first || m0 + j >= d.k) ? 0.0 : q[(long long)(m0 + j) * d.N];
+#pragma unroll
+    for (int j = 0; j < kCoupleCols; ++j) {
+      if (m0 + j >= d.k) break;
+      q[(long long)(m0 + j) * d.N] = fma(ce.re, (double)xn[j].x, fma(-ce.im, (double)xn[j].y, old[j]));
+    }
   }
 }
 
@@ -2008,19 +2065,27 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
   };
   // backward products x = -S' s into the nodes' solution columns (and the
   // quadrature shares)
-  auto back_epi = [&](const Chains& ch) {
+  // quadrature shares: in the epilogue only for the chains in share_chains
+  // (the layers no later backward coupling reads), else in the couplings
+  auto back_epi = [&](const Chains& ch, int share_chains) {
     SolveEpi<CB> epi{Gc, d.N * d.k, d.N, d.n, d.k, -1.0f};
     epi.node_rows = 1;
     epi.ch = ch;
-    if (qo.qp) {
+    if (qo.qp && share_chains) {
       epi.qp = qo.qp;
       epi.sQ = d.N * d.k;
       epi.ldq = d.N;
       epi.coef = qo.coef;
       epi.qfirst = qo.first;
+      epi.share_chains = share_chains;
     }
     return epi;
   };
+  BwdShares qs;
+  qs.qp = qo.qp;
+  qs.coef = qo.coef;
+  qs.first = qo.first;
+  qs.mid = K;
   int launches = 0;
   // forward sweep: g on each chain's layer, then t = S' g for its next layer
   for (int t = 0; t < L0; ++t) {
@@ -2043,7 +2108,8 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     launch_pdl(k_mx_couple_fwd<true>, dim3(cdiv(d.n, 128), cdiv(d.k, kCoupleCols), one.count), dim3(128), 0, s, d,
                ch, L0 > 0 ? 1 : 0, 1, L1 > 0 ? 1 : 0, Cf, Rreal, Rc, Tout, Gc, Bemb, one, dactive);
     prof::end(s, prof::COUPLE);
-    if (!gemm(one, K, K, back_epi(ch))) return "tcgen05 solve launch failed";
+    // x_K: read by the first backward coupling when there is one
+    if (!gemm(one, K, K, back_epi(ch, L0 > 0 ? 0 : 1))) return "tcgen05 solve launch failed";
     launches += 2;
   }
   // backward sweep out along both chains: x overwrites g
@@ -2053,9 +2119,11 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     prof::begin(s, prof::COUPLE);
     prof::add_work(prof::COUPLE, couple_bytes(vl.count, 32.0));
     launch_pdl(k_mx_couple_bwd, dim3(cdiv(d.n, 128), cdiv(d.k, kCoupleCols), vl.count), dim3(128), 0, s, d, ch, Cf,
-               Gc, Bemb, vl, dactive);
+               Gc, Bemb, vl, dactive, qs);
     prof::end(s, prof::COUPLE);
-    if (!gemm(vl, K - 1 - u, K + 1 + u, back_epi(ch))) return "tcgen05 solve launch failed";
+    // the last layer of each chain: no coupling reads its solution
+    const int last = (u == L0 - 1 ? 1 : 0) | (u == L1 - 1 ? 2 : 0);
+    if (!gemm(vl, K - 1 - u, K + 1 + u, back_epi(ch, last))) return "tcgen05 solve launch failed";
     launches += 2;
   }
   prof::count_launch(launches);

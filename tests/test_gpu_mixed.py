@@ -128,6 +128,27 @@ def test_quadrature_mixed_matches_oracle():
     assert np.abs(back(Q) - ref).max() <= 1e-8 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("nz", [1, 2, 3, 4, 7])
+def test_quadrature_mixed_every_layer_count(nz):
+    """Eq. 15 over few layers: the middle layer alone, chains of unequal
+    length and the last layer of each chain, whose shares come from the
+    product epilogue rather than a backward coupling -- every layer's share
+    is added exactly once."""
+    nx, ny, G, seed = 12, 11, 5, 4
+    op = workloads.q1_operator(nx, ny, nz, workloads.gaussian_potential(G, seed, nx, ny, nz))
+    lam = oracle.closed_form_eigenvalues_v0(nx, ny, nz)
+    lmin, lmax = lam[0] - 3.0, 0.5 * (lam[5] + lam[6])
+    k = 12
+    RHS = np.random.default_rng(nz).standard_normal((op.N, k))
+    A = oracle.assemble(op.A27, nx, ny, nz)
+    B = oracle.assemble(op.B27, nx, ny, nz)
+    dop, keep = dev_op(op)
+    Q = torch.zeros((k, op.N), dtype=torch.float64, device="cuda")
+    F().Handle().feast_quadrature(dop, lmin, lmax, 8, cm(RHS), Q, k, precision=F().FEAST_PREC_MIXED)
+    ref, _ = oracle.quadrature_subspace(A, B, RHS, lmin, lmax, 8, op.n, nz)
+    assert np.abs(back(Q) - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("key,seed,zero", [("q1_10x10x20/v0", 0, True)] +
                          [(f"q1_10x10x20/seed{s}", s, False) for s in range(5)])
 def test_feast_solve_mixed_matches_oracle(intervals, key, seed, zero):
