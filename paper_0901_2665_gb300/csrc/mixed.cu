@@ -7,11 +7,15 @@
 // S[i, j] -= sum_k T[i, k] L[j, k] (panel width 64) run as one real TF32 GEMM
 // on tcgen05 through the real embedding
 //   [Ur | Ui] = [Tr | Ti] [[Lr^T, Li^T], [-Li^T, Lr^T]],
-// and so do the block solves t = S' g.  Storage of S'_i is "row-split": row p
-// holds the n real parts, then the n imaginary parts, so a row is directly
-// the K-major A operand [Sr | Si] of the solve GEMM.
+// and so do the block solves t = S' g, with both operands as split bf16
+// pairs (x = x_hi + x_lo, 16 significant bits; three bf16 products each,
+// the same bytes as TF32): the refinement's contraction per step is set by
+// the solve's operand rounding far more than by the factor's.  Storage of
+// S'_i is "row-split": row p holds the n real parts, then the n imaginary
+// parts, so a row is directly the K-major A operand [Sr | Si] of the solve
+// GEMM.
 //
-// Solve: forward/backward sweeps in complex64 (TF32 products, fp32
+// Solve: forward/backward sweeps in complex64 (split-bf16 products, fp32
 // accumulation) give a correction d = M~^{-1} R; FP64 iterative refinement
 // Q_e += d, R = RHS - (Z_e B - A) Q_e repeats until ||R||/||RHS|| <= ir_tol
 // for every node (the first residual in FP64, the later ones updated by the
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(256) k_mx_schur2(Dims d, Chains ch, int has_pr
 
 // In-place output of a diagonal block of the recursive inversion:
 // -S[K,K]^{-1} back into the block of F and, for a block that no later step
-// changes, its TF32-rounded copy into the layer's solve operand Fr.
+// changes, its split bf16 pairs into the layer's solve operand Fr.
 struct LeafOut {
   float* F = nullptr;
   float* Fr = nullptr;
@@ -379,8 +383,9 @@ __global__ void __launch_bounds__(kPanel * (kPanel / RPT)) k_mx_pinv(Dims d, int
         Fw[at] = v[a].x;
         Fw[at + n] = v[a].y;
         if (Frw) {
-          Frw[at] = tc::to_tf32(v[a].x);
-          Frw[at + n] = tc::to_tf32(v[a].y);
+          float* frow = Frw + (long long)(k0 + i) * d.ldF;
+          tc::store_pair(frow, k0 + j, v[a].x);
+          tc::store_pair(frow, n + k0 + j, v[a].y);
         }
       }
     }
@@ -411,10 +416,27 @@ constexpr int kWideStages = FEAST_WIDE_STAGES;
 #endif
 constexpr int kPinvRpt = FEAST_PINV_RPT;   // rows per thread of the panel inverse
 
+#ifndef FEAST_FACTOR_KIND
+#define FEAST_FACTOR_KIND 2
+#endif
+// Operand kind of the sweep updates (k_tc_gemm KIND): 2, split bf16 pairs
+// (default); 0, TF32.
+constexpr int kFactorKind = FEAST_FACTOR_KIND;
+static_assert(kFactorKind == 0 || kFactorKind == 2, "sweep-update operand kind");
+
+// K-column kcol of a sweep-update operand row, in the operand kind's layout.
+__device__ __forceinline__ void store_factor_op(float* row, int kcol, float x) {
+  if constexpr (kFactorKind == 2)
+    tc::store_pair(row, kcol, x);
+  else
+    row[kcol] = tc::to_tf32(x);
+}
+
 // For panel K and this CTA's kRowsPerPanelCta rows i:  T[i, :] = S[i, K] Pinv  and
-// L[i, :] = S[i, K], written as the TF32-rounded GEMM operands
-// Aop = [Tr | Ti] (row i) and Bop (embedded L, rows in blocks of 64 complex
-// columns: 64 rows [Lr, -Li] then 64 rows [Li, Lr]), and in fp32 as Tc.
+// L[i, :] = S[i, K], written as the sweep updates' GEMM operands (split bf16
+// pairs, or TF32-rounded)  Aop = [Tr | Ti] (row i) and Bop (embedded L, rows
+// in blocks of 64 complex columns: 64 rows [Lr, -Li] then 64 rows
+// [Li, Lr]), and in fp32 as Tc.
 __global__ void __launch_bounds__(256) k_mx_panel_T(Dims d, int plane, int k0, int bw, const float* __restrict__ F,
                                                     const f2* __restrict__ PinvIn, float* __restrict__ Aop,
                                                     float* __restrict__ Bop, f2* __restrict__ Tc) {
@@ -459,17 +481,17 @@ __global__ void __launch_bounds__(256) k_mx_panel_T(Dims d, int plane, int k0, i
     const int i = r0 + r;
     if (i >= n) continue;
     float* arow = Aop + ((long long)e * n + i) * (2 * kPanel);
-    arow[c] = tc::to_tf32(acc[q].x);
-    arow[kPanel + c] = tc::to_tf32(acc[q].y);
+    store_factor_op(arow, c, acc[q].x);
+    store_factor_op(arow, kPanel + c, acc[q].y);
     Tc[((long long)e * n + i) * kPanel + c] = acc[q];
     const long long brow = ((long long)e * d.nblk64 + i / 64) * 128 + (i % 64);
     float* bre = Bop + brow * (2 * kPanel);
     float* bim = Bop + (brow + 64) * (2 * kPanel);
     const f2 l = Ls[r][c];
-    bre[c] = tc::to_tf32(l.x);
-    bre[kPanel + c] = tc::to_tf32(-l.y);
-    bim[c] = tc::to_tf32(l.y);
-    bim[kPanel + c] = tc::to_tf32(l.x);
+    store_factor_op(bre, c, l.x);
+    store_factor_op(bre, kPanel + c, -l.y);
+    store_factor_op(bim, c, l.y);
+    store_factor_op(bim, kPanel + c, l.x);
   }
 }
 
@@ -482,13 +504,13 @@ constexpr int kStageLd = tc::kBlockM + 1;   // staging row stride (floats): conf
 //   j in K, i not:   S[i, j]  = T[i, j - k0]
 //   both in K:       S[i, j]  = -Pinv[i - k0, j - k0]
 // The last panel writes every entry of the finished S'_i, so it also stores
-// the TF32-rounded (nearest) copy that the block solves read.
+// the split bf16 pairs that the block solves read.
 // The accumulator goes through shared memory (one half, real or imaginary,
 // at a time) so that the read-modify-write of S is coalesced along rows.
 struct SweepEpi {
   float* F;        // row-split fp32 working copy of the layer being swept, virtual-node stride sF floats
   long long sF;
-  float* Fr;       // last panel only: TF32-rounded copies of the finished S' (solve operand), node stride sFr
+  float* Fr;       // last panel only: split bf16 pairs of the finished S' (solve operand), node stride sFr
   long long sFr;
   int ldF, n, k0, bw;
   const f2* Tc;    // n x 64 per virtual node
@@ -544,7 +566,7 @@ struct SweepEpi {
             val = -(half ? p2.y : p2.x);
           }
           Fe[(long long)i * ldF + half * n + j] = val;
-          if (Fre) Fre[(long long)i * ldF + half * n + j] = tc::to_tf32(val);
+          if (Fre) tc::store_pair(Fre + (long long)i * ldF, half * n + j, val);
         }
       }
       tc::epilogue_sync();
@@ -560,18 +582,18 @@ struct SweepEpi {
 // start, so the load overlaps the main loop; each thread then updates its row
 // in shared memory (128-byte swizzle: chunk c of row r sits at c ^ (r & 7)) and
 // one thread stores the tile back with TMA (and, after the last panel, the
-// TF32-rounded copy).  The 3-D maps (row, layer plane) clip every box at the
+// solve copy as split bf16 pairs).  The 3-D maps (row, layer plane) clip every box at the
 // layer's n rows.
 struct SweepEpiTma {
   static constexpr size_t kTileBytes = 4 * 16384;
   static constexpr size_t kExtraSmem = kTileBytes + 64;
   CUtensorMap mapF;    // fp32 working layers: inner 2n, rows n, planes 2 per virtual node
-  CUtensorMap mapFr;   // TF32 solve copy: inner 2n, rows n, planes Ne*nz
+  CUtensorMap mapFr;   // solve copy (split bf16 pairs, fp32-sized rows): inner 2n, rows n, planes Ne*nz
   int plane;           // working plane of this step
   Chains ch;           // which node and layer virtual node e is
   int nz;
   int n, k0, bw;
-  int last;            // last panel: also store the TF32 copy
+  int last;            // last panel: also store the solve copy
   const f2* Tc;
   const f2* Pinv;
   __device__ int box_x(int b, int tn) const { return (b >> 1) * n + tn * 64 + (b & 1) * 32; }
@@ -693,17 +715,29 @@ struct SweepEpiTma {
     }
     if (last) {
       tc::epilogue_sync();   // the working-copy stores have read the tile
+      // each box row (32 K-columns, 16-byte chunk c at c ^ sw) becomes its
+      // split bf16 pairs: chunks 0-3 the leading parts, 4-7 the trailing
 #pragma unroll 1
       for (int b = 0; b < 4; ++b) {
-        float4* rowp = reinterpret_cast<float4*>(extra + b * 16384 + row * 128);
+        uint4* rowp = reinterpret_cast<uint4*>(extra + b * 16384 + row * 128);
+        float x[32];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          float4 x = rowp[c];
-          x.x = tc::to_tf32(x.x);
-          x.y = tc::to_tf32(x.y);
-          x.z = tc::to_tf32(x.z);
-          x.w = tc::to_tf32(x.w);
-          rowp[c] = x;
+          const uint4 u = rowp[c ^ sw];
+          x[4 * c] = __uint_as_float(u.x);
+          x[4 * c + 1] = __uint_as_float(u.y);
+          x[4 * c + 2] = __uint_as_float(u.z);
+          x[4 * c + 3] = __uint_as_float(u.w);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          uint4 h, l;
+          tc::split2(x[8 * c], x[8 * c + 1], h.x, l.x);
+          tc::split2(x[8 * c + 2], x[8 * c + 3], h.y, l.y);
+          tc::split2(x[8 * c + 4], x[8 * c + 5], h.z, l.z);
+          tc::split2(x[8 * c + 6], x[8 * c + 7], h.w, l.w);
+          rowp[c ^ sw] = h;
+          rowp[(4 + c) ^ sw] = l;
         }
       }
       tc::fence_proxy_async_smem();
@@ -850,7 +884,7 @@ struct SolveEpi {
 // virtual nodes; its epilogue writes C transposed (lanes are rows of C, so
 // the stores of a warp are contiguous) and/or as is, adds C^T into a
 // symmetric block instead, and copies the blocks that no later step changes
-// into the TF32 solve operand Fr.  Blocks stay fp32 in F and the workspaces;
+// into the solve operand Fr (split bf16 pairs).  Blocks stay fp32 in F and the workspaces;
 // the GEMM rounds its staged operands to TF32 (nearest).
 
 // Destination of a row-split block: element (r, c) of batch b at
@@ -872,7 +906,7 @@ struct InvEpi {
   InvDest r;           // C:   element (i, j) <- C[i, j]
   int add = 0;         // t += C^T instead of t = C^T
   int M = 0, N = 0;    // rows and columns of C
-  // final blocks: TF32 copies at offsets fr_t / fr_r of the layer's plane of
+  // final blocks: split bf16 pair copies at offsets fr_t / fr_r (in fp32 units) of the layer's plane of
   // Fr (row stride ld_fr, imaginary parts imoff_fr further); fr == nullptr: none
   float* fr = nullptr;
   long long fr_t = -1, fr_r = -1;
@@ -905,28 +939,29 @@ struct InvEpi {
             p[0] = xr;
             p[t.imoff] = xi;
             if (frp && fr_t >= 0) {
-              float* q = frp + fr_t + (long long)j * ld_fr + i;
-              q[0] = tc::to_tf32(xr);
-              q[imoff_fr] = tc::to_tf32(xi);
+              const long long at = fr_t + (long long)j * ld_fr + i;   // row at / ld_fr, K-column at % ld_fr
+              float* frow = frp + at / ld_fr * ld_fr;
+              tc::store_pair(frow, (int)(at % ld_fr), xr);
+              tc::store_pair(frow, (int)(at % ld_fr) + imoff_fr, xi);
             }
           }
         }
       }
       if (r.base) {
         float* p = r.base + b * r.bstride + (long long)i * r.ld + j0;
-        float* q = (frp && fr_r >= 0) ? frp + fr_r + (long long)i * ld_fr + j0 : nullptr;
-        const uintptr_t al = reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(p + r.imoff) |
-                             (q ? reinterpret_cast<uintptr_t>(q) | reinterpret_cast<uintptr_t>(q + imoff_fr) : 0);
-        if (j0 + 16 <= N && (al & 15) == 0) {
+        // the solve copy's row and first K-column of this run of columns
+        const long long qat = (frp && fr_r >= 0) ? fr_r + (long long)i * ld_fr + j0 : -1;
+        float* qrow = qat >= 0 ? frp + qat / ld_fr * ld_fr : nullptr;
+        const int qc = qat >= 0 ? (int)(qat % ld_fr) : 0;
+        const uintptr_t al = reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(p + r.imoff);
+        if (j0 + 16 <= N && (al & 15) == 0 && (qc & 3) == 0 && (imoff_fr & 3) == 0) {
 #pragma unroll
           for (int u = 0; u < 16; u += 4) {
             *reinterpret_cast<float4*>(p + u) = make_float4(re[u], re[u + 1], re[u + 2], re[u + 3]);
             *reinterpret_cast<float4*>(p + r.imoff + u) = make_float4(im[u], im[u + 1], im[u + 2], im[u + 3]);
-            if (q) {
-              *reinterpret_cast<float4*>(q + u) = make_float4(tc::to_tf32(re[u]), tc::to_tf32(re[u + 1]),
-                                                              tc::to_tf32(re[u + 2]), tc::to_tf32(re[u + 3]));
-              *reinterpret_cast<float4*>(q + imoff_fr + u) = make_float4(
-                  tc::to_tf32(im[u]), tc::to_tf32(im[u + 1]), tc::to_tf32(im[u + 2]), tc::to_tf32(im[u + 3]));
+            if (qrow) {
+              tc::store_pair4(qrow, qc + u, make_float4(re[u], re[u + 1], re[u + 2], re[u + 3]));
+              tc::store_pair4(qrow, qc + imoff_fr + u, make_float4(im[u], im[u + 1], im[u + 2], im[u + 3]));
             }
           }
         } else {
@@ -935,9 +970,9 @@ struct InvEpi {
             if (j0 + u < N) {
               p[u] = re[u];
               p[r.imoff + u] = im[u];
-              if (q) {
-                q[u] = tc::to_tf32(re[u]);
-                q[imoff_fr + u] = tc::to_tf32(im[u]);
+              if (qrow) {
+                tc::store_pair(qrow, qc + u, re[u]);
+                tc::store_pair(qrow, qc + imoff_fr + u, im[u]);
               }
             }
           }
@@ -965,15 +1000,15 @@ __device__ __forceinline__ long long emb_row(const Dims& d, int e, int m) {
   return blk * 2 * d.CB + (m % d.CB);
 }
 
-// Writes the embedded, TF32-rounded RHS rows of the complex column whose
-// real-part row is rre.
+// Writes the embedded RHS rows of the complex column whose real-part row is
+// rre, as split bf16 pairs (the solve product's operand layout).
 __device__ __forceinline__ void write_emb(const Dims& d, float* Bemb, long long rre, int p, f2 g) {
   float* re_row = Bemb + rre * d.ldB;
   float* im_row = Bemb + (rre + d.CB) * d.ldB;
-  re_row[p] = tc::to_tf32(g.x);
-  re_row[d.n + p] = tc::to_tf32(-g.y);
-  im_row[p] = tc::to_tf32(g.y);
-  im_row[d.n + p] = tc::to_tf32(g.x);
+  tc::store_pair(re_row, p, g.x);
+  tc::store_pair(re_row, d.n + p, -g.y);
+  tc::store_pair(im_row, p, g.y);
+  tc::store_pair(im_row, d.n + p, g.x);
 }
 
 constexpr int kCoupleCols = 4;   // right-hand-side columns per thread of the coupling kernels
@@ -1457,14 +1492,14 @@ bool make_map(CUtensorMap* map, const float* base, long long inner, long long ro
 
 // Shared-memory attribute of a GEMM instantiation, set once per device (and
 // before any stream capture: it is not a stream operation).
-template <int BN, int STAGES, class Epi>
+template <int BN, int STAGES, class Epi, int KIND = 0>
 cudaError_t tc_attr() {
   constexpr size_t smem = tc::smem_bytes<BN, STAGES, Epi>();
   static PerDevice<cudaError_t> attr;
   return attr.get(
       [] {
-        return cudaFuncSetAttribute(tc::k_tc_gemm<BN, STAGES, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem);
+        return cudaFuncSetAttribute(tc::k_tc_gemm<BN, STAGES, Epi, KIND>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       },
       cudaErrorInvalidDevice);
 }
@@ -1491,15 +1526,19 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-template <int BN, int STAGES, class Epi>
+template <int BN, int STAGES, class Epi, int KIND = 0>
 cudaError_t launch_tc(cudaStream_t s, dim3 grid, const CUtensorMap& a, const CUtensorMap& b, tc::Geom geo,
                       const Epi& epi, int* status, bool pdl = false) {
   constexpr size_t smem = tc::smem_bytes<BN, STAGES, Epi>();
-  if (const cudaError_t e = tc_attr<BN, STAGES, Epi>()) return e;
-  if (pdl) return launch_pdl(tc::k_tc_gemm<BN, STAGES, Epi>, grid, dim3(tc::kThreads), smem, s, a, b, geo, epi, status);
-  tc::k_tc_gemm<BN, STAGES, Epi><<<grid, tc::kThreads, smem, s>>>(a, b, geo, epi, status);
+  if (const cudaError_t e = tc_attr<BN, STAGES, Epi, KIND>()) return e;
+  if (pdl)
+    return launch_pdl(tc::k_tc_gemm<BN, STAGES, Epi, KIND>, grid, dim3(tc::kThreads), smem, s, a, b, geo, epi, status);
+  tc::k_tc_gemm<BN, STAGES, Epi, KIND><<<grid, tc::kThreads, smem, s>>>(a, b, geo, epi, status);
   return cudaGetLastError();
 }
+
+// Operand kind of the block-solve products (split bf16 pairs, see k_tc_gemm).
+constexpr int kSolveKind = 2;
 
 enum Buf { B_F = 0, B_T1, B_AOP, B_BOP, B_TC, B_PINV, B_GC, B_RC, B_BEMB, B_TOUT, B_PART, B_REL, B_ACTIVE, B_CF, B_FW,
            B_RLO, B_COUNT };
@@ -1759,7 +1798,10 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
   if (!encode_fn()) return "cuTensorMapEncodeTiled is not available from the driver";
   const int V = 2 * Ne;   // virtual nodes (two chains)
   const size_t fbytes = sizeof(float) * (size_t)Ne * d.nz * d.n * d.ldF;
-  if (!ensure(w, B_F, fbytes, s)) return "out of device memory (mixed factors)";
+  const long long flayout = (long long)d.n << 32 | d.ldF;
+  const bool f_new = w.sizes[B_F] < fbytes || !w.bufs[B_F] || w.fr_layout != flayout;
+  if (!ensure(w, B_F, fbytes, s, f_new)) return "out of device memory (mixed factors)";
+  w.fr_layout = flayout;
   if (!ensure(w, B_FW, sizeof(float) * (size_t)V * 2 * d.n * d.ldF, s)) return "out of device memory (working layers)";
   if (!ensure(w, B_T1, sizeof(float) * (size_t)V * d.n * d.ldF, s)) return "out of device memory (schur scratch)";
   // The recursive block inversion needs 16-byte aligned imaginary halves of
@@ -1791,7 +1833,7 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
   }
   cudaStream_t s2 = w.side;
   // The row-split padding [2n, ldF) is never read (the tensor maps stop at 2n).
-  float* Fr = buf<float>(w, B_F);    // TF32-rounded S'_i of every layer (solve operand)
+  float* Fr = buf<float>(w, B_F);    // S'_i of every layer as split bf16 pairs (solve operand)
   float* F = buf<float>(w, B_FW);    // fp32 working layers (ping-pong per virtual node)
   f2* Cf = buf<f2>(w, B_CF);
   const int K = d.K, L0 = K, L1 = d.nz - 1 - K;   // middle layer, chain lengths
@@ -1862,12 +1904,13 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
         SweepEpiTma epi{mapF, mapFr, ch.wplane, ch, d.nz, d.n, k0, bw, last ? 1 : 0, Tc[q], Pv[q]};
         // the narrow update (one column tile, few CTAs, on the critical path)
         // pipelines its K-blocks; the wide one keeps two CTAs per SM instead
-        err = count == 1 ? launch_tc<128, 4>(st, grid, tmA[q], tmB[q], geo, epi, status)
-                         : launch_tc<128, kWideStages>(st, grid, tmA[q], tmB[q], geo, epi, status);
+        err = count == 1 ? launch_tc<128, 4, SweepEpiTma, kFactorKind>(st, grid, tmA[q], tmB[q], geo, epi, status)
+                         : launch_tc<128, kWideStages, SweepEpiTma, kFactorKind>(st, grid, tmA[q], tmB[q], geo, epi,
+                                                                                 status);
       } else {
         SweepEpi epi{F + (long long)ch.wplane * d.n * d.ldF, sF, last ? Fr : nullptr, sFr, d.ldF, d.n, k0, bw,
                      Tc[q], Pv[q], ch};
-        err = launch_tc<128, 2>(st, grid, tmA[q], tmB[q], geo, epi, status);
+        err = launch_tc<128, 2, SweepEpi, kFactorKind>(st, grid, tmA[q], tmB[q], geo, epi, status);
       }
       prof::end(st, cls);
       prof::count_launch();
@@ -1977,8 +2020,8 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
     } else {
       if (w.factor_graph) cudaGraphExecDestroy(w.factor_graph);
       w.factor_graph = nullptr;
-      if (tc_attr<128, kWideStages, SweepEpiTma>() || tc_attr<128, 4, SweepEpiTma>() || tc_attr<128, 2, SweepEpi>() ||
-          cg_attr<InvEpi>())
+      if (tc_attr<128, kWideStages, SweepEpiTma, kFactorKind>() || tc_attr<128, 4, SweepEpiTma, kFactorKind>() ||
+          tc_attr<128, 2, SweepEpi, kFactorKind>() || cg_attr<InvEpi>())
         return "tcgen05 sweep-update attribute rejected";
       cudaGraph_t graph = nullptr;
       cudaGraphExec_t exec = nullptr;
@@ -2034,8 +2077,10 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
   float* Bemb = buf<float>(w, B_BEMB);
   const int Ne = d.Ne, V = 2 * Ne;
   CUtensorMap tmF, tmB;
-  if (!make_map(&tmF, F, 2 * d.n, (long long)Ne * d.nz * d.n, d.ldF, 128)) return "tensor map (factors) rejected";
-  if (!make_map(&tmB, Bemb, 2 * d.n, (long long)V * d.nblkCB * 2 * CB, d.ldB, 2 * CB))
+  // split-pair rows: the maps span whole 128-byte blocks (a ragged last
+  // block's trailing parts sit past 2n; its unused columns are zero)
+  if (!make_map(&tmF, F, d.ldF, (long long)Ne * d.nz * d.n, d.ldF, 128)) return "tensor map (factors) rejected";
+  if (!make_map(&tmB, Bemb, d.ldB, (long long)V * d.nblkCB * 2 * CB, d.ldB, 2 * CB))
     return "tensor map (rhs) rejected";
   const int nk = (2 * d.n + tc::kBlockK - 1) / tc::kBlockK;
   const f2* Cf = buf<f2>(w, B_CF);
@@ -2058,7 +2103,8 @@ const char* solve_sweeps(cudaStream_t s, const Dims& d, const cplx* Z, const dou
     prof::begin(s, prof::SOLVE_GEMM);
     prof::add_work(prof::SOLVE_GEMM, 8.0 * d.n * (double)d.n * d.k * vl.count);
     const bool ok =
-        launch_tc<2 * CB, ST>(s, dim3(d.nblkCB, cdiv(d.n, 128), vl.count), tmF, tmB, geo, epi, status, true) ==
+        launch_tc<2 * CB, ST, SolveEpi<CB>, kSolveKind>(s, dim3(d.nblkCB, cdiv(d.n, 128), vl.count), tmF, tmB, geo,
+                                                         epi, status, true) ==
         cudaSuccess;
     prof::end(s, prof::SOLVE_GEMM);
     return ok;
@@ -2142,8 +2188,8 @@ float time_solve_gemm(cudaStream_t s, const Dims& d0, MixedWork& w, int* status)
   d.nblkCB = (d.k + CB - 1) / CB;
   const int V = d.K < d.nz - 1 ? 2 * d.Ne : d.Ne;
   CUtensorMap tmF, tmB;
-  if (!make_map(&tmF, buf<float>(w, B_F), 2 * d.n, (long long)d.Ne * d.nz * d.n, d.ldF, 128)) return 1e30f;
-  if (!make_map(&tmB, buf<float>(w, B_BEMB), 2 * d.n, (long long)V * d.nblkCB * 2 * CB, d.ldB, 2 * CB)) return 1e30f;
+  if (!make_map(&tmF, buf<float>(w, B_F), d.ldF, (long long)d.Ne * d.nz * d.n, d.ldF, 128)) return 1e30f;
+  if (!make_map(&tmB, buf<float>(w, B_BEMB), d.ldB, (long long)V * d.nblkCB * 2 * CB, d.ldB, 2 * CB)) return 1e30f;
   const int nk = (2 * d.n + tc::kBlockK - 1) / tc::kBlockK;
   SolveEpi<CB> epi{buf<f2>(w, B_TOUT), (long long)d.n * d.k, d.n, d.n, d.k, 1.0f};
   tc::Geom geo{0, d.nz * d.n, 0, d.nblkCB * 2 * CB, nk};
@@ -2161,7 +2207,8 @@ float time_solve_gemm(cudaStream_t s, const Dims& d0, MixedWork& w, int* status)
       const int t = (round * kTuneRun + r) % d.nz;
       geo.a_row0 = t * d.n;
       geo.a_row0_hi = (d.nz - 1 - t) * d.n;
-      launch_tc<2 * CB, ST>(s, dim3(d.nblkCB, cdiv(d.n, 128), V), tmF, tmB, geo, epi, status);
+      launch_tc<2 * CB, ST, SolveEpi<CB>, kSolveKind>(s, dim3(d.nblkCB, cdiv(d.n, 128), V), tmF, tmB, geo, epi,
+                                                      status);
     }
     cudaEventRecord(b, s);
     cudaEventSynchronize(b);
@@ -2327,9 +2374,11 @@ static const char* solve_prepare(cudaStream_t s, Grid g, int Ne, int k, MixedWor
   // embedded RHS operand, sized for every tile width (rows of columns >= k
   // stay zero; re-zeroed when the column count changes)
   const size_t bemb = sizeof(float) * (size_t)2 * Ne * (2 * (size_t)k + 128) * d.ldB;
-  const bool shape_changed = w.sizes[B_BEMB] < bemb || w.bemb_k != k;
+  const long long blayout = (long long)d.n << 32 | d.ldB;
+  const bool shape_changed = w.sizes[B_BEMB] < bemb || w.bemb_k != k || w.bemb_layout != blayout;
   if (!ensure(w, B_BEMB, bemb, s, shape_changed)) return "out of device memory";
   w.bemb_k = k;
+  w.bemb_layout = blayout;
   d = make_dims(g, Ne, k, tuned_cfg(s, d, w, status));
   if (shape_changed) cudaMemsetAsync(w.bufs[B_BEMB], 0, bemb, s);
   const long long nblk = cdiv(d.N, kResRows);

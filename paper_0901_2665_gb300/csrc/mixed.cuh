@@ -68,6 +68,9 @@ struct MixedWork {
   size_t sizes[20] = {};
   int nz_factored = 0, ne_factored = 0;   // shape of the factors held
   int bemb_k = 0;                         // right-hand sides the RHS operand was zeroed for
+  // row layouts (n, row stride) the solve operands were zeroed for: the
+  // split-pair rows must read zeros past 2n in a ragged last block
+  long long fr_layout = -1, bemb_layout = -1;
   cudaStream_t side = nullptr;            // lookahead stream of the factorisation
   cudaEvent_t ev_narrow = nullptr, ev_side = nullptr;
   SweepGraphCache graphs;

@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -205,6 +206,37 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
+// Split bf16 pairs (the KIND 2 operand layout of k_tc_gemm): a row keeps the
+// byte size of its fp32 form; each 128-byte block of 32 K-columns holds their
+// bf16 leading parts hi = bf16(x) (nearest), then their trailing parts
+// lo = bf16(x - hi).  K-column c's leading part is bf16 element
+// 64 (c / 32) + c % 32 of the row, its trailing part 32 elements further.
+__device__ __forceinline__ void store_pair(float* row, int kcol, float x) {
+  __nv_bfloat16* r = reinterpret_cast<__nv_bfloat16*>(row) + ((kcol >> 5) << 6) + (kcol & 31);
+  const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+  r[0] = hi;
+  r[32] = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// Leading and trailing parts of two values, packed (first value low).
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - __low2float(h), b - __high2float(h));
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// Four consecutive K-columns kcol..kcol+3 (kcol a multiple of 4, the row
+// 16-byte aligned): two 8-byte stores.
+__device__ __forceinline__ void store_pair4(float* row, int kcol, float4 x) {
+  uint2 h, l;
+  split2(x.x, x.y, h.x, l.x);
+  split2(x.z, x.w, h.y, l.y);
+  uint2* r = reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(row) + ((kcol >> 5) << 6) + (kcol & 31));
+  r[0] = h;
+  r[8] = l;   // 32 bf16 further
+}
+
 // Geometry of a batched launch: grid (n tiles, m tiles, batch).  The A tile
 // of CTA (x, tm, e) starts at row a_row0 + e*a_batch + tm*128 of A's tensor
 // map, the B tile at row b_row0 + e*b_batch + tn*BN with tn = x + tn_base,
@@ -290,6 +322,12 @@ __device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 1, 128;
 // KIND 0: fp32 operands read as TF32 (kind::tf32); KIND 1: BF16 operands
 // (kind::f16).  A K-block is one 128-byte swizzle row either way: 32 fp32 or
 // 64 bf16 elements; geo.nk counts K-blocks.
+// KIND 2: split BF16 pairs.  Each 128-byte row holds 32 K-columns as their
+// bf16 leading parts x_hi = bf16(x) (bytes 0-63) then their trailing parts
+// x_lo = bf16(x - x_hi) (bytes 64-127), so that x_hi + x_lo carries 16
+// significant bits, and C += A_hi B_hi + A_hi B_lo + A_lo B_hi: six
+// kind::f16 MMAs of K = 16 per K-block (the dropped A_lo B_lo is below the
+// pairs' own rounding).  A K-block then covers 32 K-columns, as for TF32.
 template <int BN, int STAGES, class Epi, int KIND = 0>
 __global__ void __launch_bounds__(kThreads)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Geom geo,
@@ -346,7 +384,7 @@ __global__ void __launch_bounds__(kThreads)
         const uint32_t ph = (kb / kStages) & 1;
         if (kb >= kStages && !mbar_wait(&empty[s], ph ^ 1, status, abort_flag)) break;
         mbar_arrive_expect_tx(&full[s], S::kStageBytes);
-        constexpr int kElems = KIND == 0 ? kBlockK : 2 * kBlockK;   // elements per 128-byte row
+        constexpr int kElems = KIND == 1 ? 2 * kBlockK : kBlockK;   // map elements (32 bit for KIND 2) per row
         tma_load_2d(sA + s * kATileBytes, &tmA, &full[s], kb * kElems, ay);
         tma_load_2d(sB + s * S::kBTileBytes, &tmB, &full[s], kb * kElems, by);
         issued = kb + 1;
@@ -362,6 +400,7 @@ __global__ void __launch_bounds__(kThreads)
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = KIND == 0 ? idesc_tf32(kBlockM, BN) : idesc_bf16(kBlockM, BN);
+      static_assert(KIND >= 0 && KIND <= 2, "operand kind");
       for (int kb = 0; kb < geo.nk; ++kb) {
         const int s = kb % kStages;
         const uint32_t ph = (kb / kStages) & 1;
@@ -369,12 +408,23 @@ __global__ void __launch_bounds__(kThreads)
         tc_fence_after();
         const uint32_t a0 = smem_u32(sA + s * kATileBytes);
         const uint32_t b0 = smem_u32(sB + s * S::kBTileBytes);
+        if constexpr (KIND == 2) {
+          // (A byte offset, B byte offset) of the six 32-byte K steps:
+          // hi x hi, hi x lo, lo x hi over both halves of the 32 columns
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {   // four 32-byte K steps per 128-byte row
-          if constexpr (KIND == 0)
-            mma_tf32(tmem, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc, (kb | kk) != 0);
-          else
-            mma_bf16(tmem, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc, (kb | kk) != 0);
+          for (int t = 0; t < 6; ++t) {
+            const uint32_t ao = (t >= 4 ? 64u : 0u) + (t & 1) * 32u;
+            const uint32_t bo = (t >= 2 && t < 4 ? 64u : 0u) + (t & 1) * 32u;
+            mma_bf16(tmem, sdesc_sw128(a0 + ao), sdesc_sw128(b0 + bo), idesc, (kb | t) != 0);
+          }
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {   // four 32-byte K steps per 128-byte row
+            if constexpr (KIND == 0)
+              mma_tf32(tmem, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc, (kb | kk) != 0);
+            else
+              mma_bf16(tmem, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc, (kb | kk) != 0);
+          }
         }
         mma_commit(&empty[s]);
       }
