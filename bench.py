@@ -35,7 +35,7 @@ UNIT = "eigenpairs/s"
 WORKLOAD = "q1_32x32x400_fp64"
 INTERVAL_KEY = "q1_32x32x400/seed0"
 Y_SEED = 1000
-TF32_NOMINAL_RATIO = 1.1 / 2.25       # dense TF32 / BF16 tensor rate (nominal)
+PAIR_PRODUCTS = 3                     # bf16 MMAs per split-pair product (hi*hi + hi*lo + lo*hi)
 FP64_PEAK_TFLOPS = 1.25               # GB300 FP64 rate (CUDA cores and tensor cores alike)
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 FP32_LANES = 152 * 128                # FP32 lanes of a GB300 (152 SMs x 128)
@@ -45,21 +45,16 @@ FF_OPS_PER_ENTRY = 27 * 4 * 11        # fp32 instructions per complex entry of t
 # current kernels (profiles/kernels_*_q1_32x32x24_mixed.md; the residual kernels
 # were captured on 24 of 400 layers and scaled by 400/24, their traffic being
 # proportional to the rows).  An entry is removed when its kernel changes.
-TRAFFIC = {
-    # 16 virtual nodes per launch (two chains of 8 nodes)
-    "solve_gemm": (167.9 + 4.6) * 1e6,
-    # wide sweep update: 15 regular launches and the last panel's (which also
-    # writes the TF32 solve copy) per layer
-    "sweep_gemm": (15 * (158.4 + 68.1) + (167.9 + 207.7)) / 16 * 1e6,
-}
+TRAFFIC = {}
 
 
 def roofline(name, ms, flops, launches, pk, pk_src):
     """Roofline object of one kernel class from its summed device time and
     algorithmic work (216 flops per complex entry for the residuals)."""
     achieved = flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
-    if name == "fp64_residual":
-        roof = {"kernel": "k_mx_residual (FP64 refinement residual)", "bound": "alu", "unit": "TFLOP/s",
+    if name in ("fp64_residual", "fp64_path"):
+        kern = "k_mx_residual (FP64 refinement residual)" if name == "fp64_residual" else "plain FP64 path"
+        roof = {"kernel": kern, "bound": "alu", "unit": "TFLOP/s",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "peak_source": "GB300 FP64 rate (derived)"}
     elif name in ("panel_inverse", "panel_product", "schur"):
         # fp32 CUDA-core arithmetic (complex FMAs counted as 8 flops)
@@ -79,8 +74,8 @@ def roofline(name, ms, flops, launches, pk, pk_src):
                 "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (derived)"}
     else:
         roof = {"kernel": name, "bound": "tensor", "unit": "TFLOP/s", "achieved": achieved,
-                "peak": pk["bf16_tflops_sustained"] * TF32_NOMINAL_RATIO,
-                "peak_source": f"{pk_src} bf16 sustained x TF32/BF16 nominal ratio"}
+                "peak": pk["bf16_tflops_sustained"] / PAIR_PRODUCTS,
+                "peak_source": f"{pk_src} bf16 sustained / {PAIR_PRODUCTS} (bf16 MMAs per split-pair product)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     if roof["bound"] == "hbm":
         roof["bytes_per_launch"] = flops / launches if launches else None
@@ -472,7 +467,7 @@ def run_ours(args):
     if not rank0:
         return None
     pk, pk_src = peaks()
-    tf32_peak = pk["bf16_tflops_sustained"] * TF32_NOMINAL_RATIO
+    pair_peak = pk["bf16_tflops_sustained"] / PAIR_PRODUCTS
     names = F.KERNEL_CLASSES
     kernels = {}
     for c in range(len(names)):
@@ -497,7 +492,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "tf32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16x3+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": "Q1 FE 32x32x400 (N=409600, 400 layers of 1024), 32 Gaussians seed 0, "
                                "lowest 100 eigenpairs, M0=128, Ne=8, tol 1e-12",
                    "precision": args.precision, "parallelism": f"replicas x{world}",
@@ -514,7 +509,7 @@ def run_ours(args):
         "phase_ms_profiled": ({"factor": rp.info.t_factor_ms, "solve": rp.info.t_solve_ms,
                                "rayleigh_ritz": rp.info.t_rr_ms} if rp is not None else None),
         "loop_graph": bool(last.info.loop_graphs),
-        "block_lu_tflops": lu, "block_lu_frac_tf32": (lu / tf32_peak) if lu else None,
+        "block_lu_tflops": lu, "block_lu_frac": (lu / pair_peak) if lu else None,
         "roofline": roof, "kernels": kernels, "gpu_launches": int(launches), "clocks": clk,
         "e2e": e2e, "fp64_gpu": fp64,
         "cpu_baseline": cpu_baseline_obj(cpu) if cpu and "value" in cpu else cpu,
@@ -641,7 +636,7 @@ def run_batched(args):
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "tf32+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
         "config": {"workload": f"{len(ops)} independent Q1 FE instances, cross sections 16/24/32, 50-400 layers, "
                                "M0 32/64/128, 8 Gaussians each, certified intervals (~0.75 M0 pairs), Ne=8, tol 1e-12",
                    "form": "batched (feast_solve_batched, memory-bounded workers, largest first)",
@@ -726,7 +721,7 @@ def run_ne_sweep(args):
     return {"metric": METRIC, "value": next(x for x in rows if x["Ne"] == 8)["eigenpairs_per_s"], "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": next(x for x in rows if x["Ne"] == 8)["ms_per_solve"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "tf32+f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
             "config": {"workload": "Q1 FE 32x32x400, lowest 100 eigenpairs, M0=128, tol 1e-12, mixed; "
                                    "contour nodes Ne = 4, 8, 16", "form": "node-count sweep (Table III)"},
             "by_ne": rows, "best_ne": best["Ne"], "clocks": clk}
@@ -789,7 +784,7 @@ def run_warm_sequence(args):
     ok = all(x["resid_warm"] <= 1e-10 for x in warm)
     return {"metric": METRIC, "value": found / (ms_w * 1e-3) if ok else 0.0, "unit": UNIT, "n_gpus": world,
             "steps": len(warm), "warmup": args.warmup, "ms_per_step": ms_w, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "tf32+f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
             "config": {"workload": "Q1 FE 32x32x400, potential amplitudes scaled by 1 + 0.01 t, interval of t = 0, "
                                    "M0=128, Ne=8, tol 1e-12, mixed", "form": "warm-started sequence (Sec. IV.C)"},
             "random_start_ms": sum(x["ms_random"] for x in warm) / len(warm), "sequence": rows, "clocks": clk}

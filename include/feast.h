@@ -89,7 +89,7 @@ typedef struct {
                          from SplitMix64 output col*N + row of this seed */
   int profile;        /* 1: time the main kernel classes with CUDA events (feast_info.kernel_ms) */
   int ir_early;       /* MIXED, random start (Y0 == NULL) only: 1 (default) loosens the refinement
-                         target of loop 1 to 1e-5 and of loop 2 to 1e-8 (never below ir_tol); a
+                         target of loop 1 to 1e-4 and of loop 2 to 1e-8 (never below ir_tol); a
                          loop with a loosened target never ends the iteration.  0, or a given
                          start block: ir_tol in every loop. */
   int inner_solver;   /* FEAST_INNER_DIRECT (default): the node systems are factorised once and

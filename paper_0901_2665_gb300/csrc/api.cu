@@ -732,7 +732,7 @@ feast_status feast_solve(feast_handle* h, const feast_operator* op, double lmin,
       // refinement target of this loop: loosened in loops 1 and 2 (their subspace
       // is still far from converged, so their solves need less accuracy)
       double ir_loop = h->opt.ir_tol;
-      if (early && loop <= 2) ir_loop = std::max(ir_loop, loop == 1 ? 1e-5 : 1e-8);
+      if (early && loop <= 2) ir_loop = std::max(ir_loop, early_tol(loop));
       const bool exact_loop = ir_loop <= h->opt.ir_tol;
       node_solves_and_quadrature(h, v, Ne, prec, h->RHS.as<double>(), M0, ir_loop, h->Q.as<double>());
       ck(cudaEventRecord(h->ev[3], s), "event");

@@ -2527,8 +2527,7 @@ __global__ void k_loop_begin(LoopState* st, double ir_tol, int early, int* activ
   if (threadIdx.x == 0) {
     const int L = ++st->loop;
     double t = ir_tol;
-    if (early && L == 1) t = fmax(ir_tol, 1e-5);
-    if (early && L == 2) t = fmax(ir_tol, 1e-8);
+    if (early && L <= 2) t = fmax(ir_tol, early_tol(L));
     st->ir_target = t;
     st->ir_step = 0;
   }

@@ -50,6 +50,14 @@ struct LoopState {
 };
 
 // Fixed parameters of such a graph.
+#ifndef FEAST_EARLY_TOL1
+#define FEAST_EARLY_TOL1 1e-4
+#endif
+// Refinement targets of loops 1 and 2 from a random start (options.ir_early):
+// their subspaces are still far from converged, so their solves need less
+// accuracy (never below options.ir_tol).
+__host__ __device__ constexpr double early_tol(int loop) { return loop == 1 ? FEAST_EARLY_TOL1 : 1e-8; }
+
 struct LoopParams {
   double lmin, lmax, tol, ir_tol;
   int early;            // loosened refinement targets in loops 1 and 2

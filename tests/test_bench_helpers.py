@@ -16,7 +16,7 @@ PK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 @pytest.mark.parametrize("name,bound,unit", [
     ("solve_gemm", "tensor", "TFLOP/s"), ("sweep_gemm", "tensor", "TFLOP/s"), ("sweep_narrow", "tensor", "TFLOP/s"),
-    ("fp64_residual", "alu", "TFLOP/s"), ("ff_residual", "alu", "T fp32 instr/s"),
+    ("fp64_residual", "alu", "TFLOP/s"), ("fp64_path", "alu", "TFLOP/s"), ("ff_residual", "alu", "T fp32 instr/s"),
     ("panel_inverse", "alu", "TFLOP/s"), ("panel_product", "alu", "TFLOP/s"), ("schur", "alu", "TFLOP/s"),
     ("solve_coupling", "hbm", "GB/s")])
 def test_roofline_classes(name, bound, unit):
@@ -24,15 +24,15 @@ def test_roofline_classes(name, bound, unit):
     assert roof["bound"] == bound and roof["unit"] == unit
     assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
     if bound == "tensor":
-        # TF32 peak: the sustained bf16 figure times the nominal TF32/BF16 ratio
-        assert roof["peak"] == pytest.approx(1700.0 * 1.1 / 2.25)
+        # split-pair products: three bf16 MMAs per product at the sustained bf16 rate
+        assert roof["peak"] == pytest.approx(1700.0 / 3)
         assert roof["achieved"] == pytest.approx(2.0e12 / 10e-3 / 1e12)
         assert roof["flops_per_launch"] == pytest.approx(2.0e10)
     if bound == "hbm":
         assert roof["peak"] == 6800.0
         assert roof["achieved"] == pytest.approx(2.0e12 / 10e-3 / 1e9)
         assert roof["bytes_per_launch"] == pytest.approx(2.0e10)
-    if name == "fp64_residual":
+    if name in ("fp64_residual", "fp64_path"):
         assert roof["peak"] == bench.FP64_PEAK_TFLOPS
 
 
