@@ -45,7 +45,16 @@ FF_OPS_PER_ENTRY = 27 * 4 * 11        # fp32 instructions per complex entry of t
 # current kernels (profiles/kernels_*_q1_32x32x24_mixed.md; the residual kernels
 # were captured on 24 of 400 layers and scaled by 400/24, their traffic being
 # proportional to the rows).  An entry is removed when its kernel changes.
-TRAFFIC = {}
+TRAFFIC = {
+    # 16 virtual nodes per launch (two chains of 8 nodes)
+    "solve_gemm": (167.9 + 3.0) * 1e6,
+    # wide sweep update: 15 regular launches and the last panel's (which also
+    # writes the solve copy) per layer
+    "sweep_gemm": (15 * (158.4 + 68.5) + (168.0 + 208.1)) / 16 * 1e6,
+    "fp64_residual": (426.6 + 365.0) * 1e6 * 400 / 24,
+    # the later (incremental) residuals
+    "ff_residual": (646.6 + 353.8) * 1e6 * 400 / 24,
+}
 
 
 def roofline(name, ms, flops, launches, pk, pk_src):
