@@ -132,7 +132,7 @@ typedef struct {
   double kernel_ms[FEAST_KERNEL_CLASSES];
   long long kernel_launches[FEAST_KERNEL_CLASSES];
   double kernel_flops[FEAST_KERNEL_CLASSES];   /* algorithmic flops of each class (complex FMA = 8 real flops;
-                               a TF32 product counts once) */
+                               a split-pair tensor-core product counts once) */
   long long sweep_graphs;   /* MIXED: forward/backward sweep pairs replayed from captured CUDA graphs
                                (0 with options.profile, which times the kernels one by one) */
   int inner_iters_max;      /* COCG: most iterations of one loop's node solves */

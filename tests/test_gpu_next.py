@@ -144,8 +144,8 @@ def test_interval_slicing_gives_the_union(precision):
 
 
 def test_inexact_inner_solves_still_converge(intervals):
-    """Sec. IV.C: with node solves accurate only to 1e-3 (the first TF32 solve,
-    no refinement step) and a trace tolerance of 1e-8, FEAST still converges:
+    """Sec. IV.C: with node solves accurate only to 1e-3 (the first mixed
+    solve, at most one refinement step) and a trace tolerance of 1e-8, FEAST still converges:
     the eigenvalues to about the square of the solve error, the residuals to
     about the solve error."""
     wl = workloads.WORKLOADS["q1_10x10x20_fp64"]
