@@ -357,13 +357,15 @@ __global__ void __launch_bounds__(1024) k_reduced_eig(int m, const double* __res
 // rotations.  The rotations, their order (round-robin pairs, m' - 1 steps a
 // sweep), the skip criteria and the sweep cap are those of jacobi_block.  One
 // step of the sweep:
-//   1. CTA r computes the rotations of the pairs k = r, r + CL, ... from the
-//      current matrix (a_pp, a_qq, a_pq read from their owners' shared
-//      memory) and stores (c, s) into the shared memory of every CTA;
-//      cluster barrier;
+//   1. every CTA computes the rotations of all pairs from the current matrix
+//      (a_pp, a_qq, a_pq read from their owners' shared memory): the same
+//      IEEE operations on the same values, so every CTA holds the same (c, s)
+//      without a broadcast or a barrier;
 //   2. every CTA copies the partner row of each of its rows, forms its rows
 //      of J^T A and then of (J^T A) J into the second buffer and applies the
-//      column rotations to its rows of V; cluster barrier; the buffers swap.
+//      column rotations to its rows of V; cluster barrier (after it every
+//      CTA's new rows are complete and no CTA reads the old buffer any more);
+//      the buffers swap.
 namespace cg = cooperative_groups;
 
 constexpr int kClThreads = 256;
@@ -440,8 +442,8 @@ __device__ int jacobi_cluster(cg::cluster_group& cl, const ClLayout& L, ClSmem& 
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (tid == 0) *S.flag = 0;
     for (int step = 0; step < mp - 1; ++step) {
-      // 1. this CTA's rotations, broadcast to the cluster
-      for (int k = rank + CL * tid; k < L.npairs; k += CL * nth) {
+      // 1. all rotations of the step, computed by every CTA
+      for (int k = tid; k < L.npairs; k += nth) {
         int p, q;
         rr_pair(k, step, mp, p, q);
         double c = 1.0, sn = 0.0;
@@ -456,12 +458,10 @@ __device__ int jacobi_cluster(cg::cluster_group& cl, const ClLayout& L, ClSmem& 
             sn = t * c;
           }
         }
-        for (int d = 0; d < CL; ++d) {
-          cl.map_shared_rank(S.rc, d)[k] = c;
-          cl.map_shared_rank(S.rs, d)[k] = sn;
-        }
+        S.rc[k] = c;
+        S.rs[k] = sn;
       }
-      cl.sync();
+      __syncthreads();
       // 2. per-index rotation tables
       for (int k = tid; k < L.npairs; k += nth) {
         int p, q;
