@@ -437,15 +437,20 @@ def run_ours(args):
         barrier(world)
         t0 = time.perf_counter()
         e2e_found = 0
+        each, graphs = [], []
         for _ in range(args.e2e_steps):
+            t1 = time.perf_counter()
             r = h_e2e.feast_solve(hop, iv["lmin"], iv["lmax"], M0, Ne, wl.tol, None, lam_h, X_h, res_h, allow=())
             if r.m_found == M and float(res_h[:M].max()) <= 1e-10:
                 e2e_found += r.m_found
+            each.append(round((time.perf_counter() - t1) * 1e3, 1))
+            graphs.append(r.info.loop_graphs)
         t_e2e = allreduce_max(time.perf_counter() - t0, world)
         e2e_total = allreduce_sum(e2e_found, world)
         h_e2e.close()
         e2e = {"value": e2e_total / t_e2e, "unit": UNIT, "steps": args.e2e_steps,
-               "h2d_bytes_per_step": 2 * 27 * N * 8, "d2h_bytes_per_step": N * M0 * 8 + 2 * M0 * 8}
+               "h2d_bytes_per_step": 2 * 27 * N * 8, "d2h_bytes_per_step": N * M0 * 8 + 2 * M0 * 8,
+               "ms_each": each, "loop_graph": graphs}
 
     # ---- plain FP64 GPU path (the comparison baseline), timed like the
     # headline: warm-up solves on the same handle first, kernel timing off,
