@@ -410,6 +410,14 @@ constexpr bool kFactorPanelSweep = FEAST_FACTOR_RECURSIVE == 0;
 #endif
 // pipeline stages of the wide sweep update (1: two CTAs per SM)
 constexpr int kWideStages = FEAST_WIDE_STAGES;
+#ifndef FEAST_NARROW_STAGES
+#define FEAST_NARROW_STAGES 1
+#endif
+// pipeline stages of the narrow update (the next panel's column tile).  One
+// stage (about 97 KB of shared memory) leaves room on its SM for a CTA of the
+// concurrent wide update, which is the factor's critical path; with four the
+// narrow update is 3 us faster but the wide update loses those SMs.
+constexpr int kNarrowStages = FEAST_NARROW_STAGES;
 
 #ifndef FEAST_PINV_RPT
 #define FEAST_PINV_RPT 16
@@ -1902,9 +1910,9 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
       const dim3 grid(count, cdiv(d.n, 128), nv);
       if (tma_rmw) {
         SweepEpiTma epi{mapF, mapFr, ch.wplane, ch, d.nz, d.n, k0, bw, last ? 1 : 0, Tc[q], Pv[q]};
-        // the narrow update (one column tile, few CTAs, on the critical path)
-        // pipelines its K-blocks; the wide one keeps two CTAs per SM instead
-        err = count == 1 ? launch_tc<128, 4, SweepEpiTma, kFactorKind>(st, grid, tmA[q], tmB[q], geo, epi, status)
+        // the narrow update (one column tile) with kNarrowStages, the wide
+        // one with kWideStages (both one by default, so that their CTAs share SMs)
+        err = count == 1 ? launch_tc<128, kNarrowStages, SweepEpiTma, kFactorKind>(st, grid, tmA[q], tmB[q], geo, epi, status)
                          : launch_tc<128, kWideStages, SweepEpiTma, kFactorKind>(st, grid, tmA[q], tmB[q], geo, epi,
                                                                                  status);
       } else {
@@ -2020,7 +2028,7 @@ const char* mixed_factor(cudaStream_t s, Grid g, int Ne, const cplx* Z, const do
     } else {
       if (w.factor_graph) cudaGraphExecDestroy(w.factor_graph);
       w.factor_graph = nullptr;
-      if (tc_attr<128, kWideStages, SweepEpiTma, kFactorKind>() || tc_attr<128, 4, SweepEpiTma, kFactorKind>() ||
+      if (tc_attr<128, kWideStages, SweepEpiTma, kFactorKind>() || tc_attr<128, kNarrowStages, SweepEpiTma, kFactorKind>() ||
           tc_attr<128, 2, SweepEpi, kFactorKind>() || cg_attr<InvEpi>())
         return "tcgen05 sweep-update attribute rejected";
       cudaGraph_t graph = nullptr;
