@@ -409,6 +409,7 @@ def run_ours(args):
     value, t_max, _ = job_throughput(found, t_ms, world)
     valid = all(ok for _, ok in results)
     last = results[-1][0]
+    h.close()   # the timed handle's work space (factors, graphs) is not needed by the legs below
     rp = None
     if not args.profile_timed:
         # per-class kernel times from one profiled solve after the timed steps

@@ -593,7 +593,10 @@ struct SweepEpi {
 // solve copy as split bf16 pairs).  The 3-D maps (row, layer plane) clip every box at the
 // layer's n rows.
 struct SweepEpiTma {
-  static constexpr size_t kTileBytes = 4 * 16384;
+  // the S tile goes through shared memory in two column halves of 32
+  // complex columns (a real-part and an imaginary-part box of 16 KB each):
+  // 32 KB instead of 64 lets three CTAs share an SM
+  static constexpr size_t kTileBytes = 2 * 16384;
   static constexpr size_t kExtraSmem = kTileBytes + 64;
   CUtensorMap mapF;    // fp32 working layers: inner 2n, rows n, planes 2 per virtual node
   CUtensorMap mapFr;   // solve copy (split bf16 pairs, fp32-sized rows): inner 2n, rows n, planes Ne*nz
@@ -604,30 +607,24 @@ struct SweepEpiTma {
   int last;            // last panel: also store the solve copy
   const f2* Tc;
   const f2* Pinv;
-  __device__ int box_x(int b, int tn) const { return (b >> 1) * n + tn * 64 + (b & 1) * 32; }
+  // box of column half hc: real parts (part 0) or imaginary parts (part 1)
+  __device__ int box_x(int part, int hc, int tn) const { return part * n + tn * 64 + hc * 32; }
+  __device__ void load_half(int hc, int e, int tm, int tn, uint8_t* extra, uint64_t* bar) const {
+    tc::mbar_arrive_expect_tx(bar, (uint32_t)kTileBytes);
+#pragma unroll
+    for (int part = 0; part < 2; ++part)
+      tc::tma_load_3d(extra + part * 16384, &mapF, bar, box_x(part, hc, tn), tm * tc::kBlockM, e * 2 + plane);
+  }
   __device__ void prologue(int e, int tm, int tn, int ept, uint8_t* extra, int*, volatile int*) const {
     if (ept != 0) return;
     uint64_t* bar = reinterpret_cast<uint64_t*>(extra + kTileBytes);
     tc::mbar_init(bar, 1);
     tc::fence_barrier_init();
-    tc::mbar_arrive_expect_tx(bar, (uint32_t)kTileBytes);
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-      tc::tma_load_3d(extra + b * 16384, &mapF, bar, box_x(b, tn), tm * tc::kBlockM, e * 2 + plane);
+    load_half(0, e, tm, tn, extra, bar);
   }
   __device__ void run(int e, int tm, int tn, int row, uint32_t taddr, int ept, uint8_t* stage, uint8_t* extra,
                       int* status, volatile int* abort_flag) const {
     uint64_t* bar = reinterpret_cast<uint64_t*>(extra + kTileBytes);
-    // bounded wait for the tile, even when the main loop gave up, so that no
-    // copy into shared memory is in flight when the CTA exits
-    bool ok = false;
-    for (long long it = 0; it < tc::kWaitLimit && !ok; ++it) ok = tc::mbar_try_wait(bar, 0);
-    if (!ok) {
-      *abort_flag = 1;
-      atomicExch(status, (int)DEV_TIMEOUT);
-    }
-    tc::epilogue_sync();
-    if (*abort_flag) return;   // uniform: read after the barrier
     const f2* T = Tc + (long long)e * n * kPanel;
     const f2* Pi = Pinv + (long long)e * kPanel * kPanel;
     const int i = tm * tc::kBlockM + row;
@@ -636,126 +633,145 @@ struct SweepEpiTma {
     const int sw = row & 7;
     const bool strip = tn * 64 == k0;   // the panel's own columns: every entry is T or -Pinv
     const bool rowsK = tm * tc::kBlockM < k0 + bw && k0 < tm * tc::kBlockM + tc::kBlockM;
-    if (strip) {
-      // row i: T[i, :] (or -Pinv[i - k0, :] on the pivot rows), 16 columns at a time
+    // pivot rows of this tile: S[i, j] = T[j, i - k0], staged in shared
+    // memory (the free pipeline stage) with coalesced loads
+    f2* Ts = reinterpret_cast<f2*>(stage);   // [64 columns j][64]
+    if (!strip && rowsK) {
+      const float4* src = reinterpret_cast<const float4*>(T + (long long)tn * 64 * kPanel);
+      float4* dstp = reinterpret_cast<float4*>(Ts);
+      const int rows_avail = min(64, n - tn * 64);
+      for (int t = ept; t < 64 * kPanel / 2; t += 128)
+        dstp[t] = (t / (kPanel / 2) < rows_avail) ? src[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 #pragma unroll 1
-      for (int c0 = 0; c0 < 64; c0 += 16) {
-        f2 val[16];
-        if (iok) {
-          const float4* src = reinterpret_cast<const float4*>(inI ? Pi + (long long)(i - k0) * kPanel + c0
-                                                                  : T + (long long)i * kPanel + c0);
-          float4 q[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) q[u] = src[u];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            val[2 * u] = f2{q[u].x, q[u].y};
-            val[2 * u + 1] = f2{q[u].z, q[u].w};
-          }
-          if (inI)
-#pragma unroll
-            for (int t = 0; t < 16; ++t) val[t] = f2{-val[t].x, -val[t].y};
-        } else {
-#pragma unroll
-          for (int t = 0; t < 16; ++t) val[t] = f2{0.f, 0.f};
-        }
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          float4* rowp = reinterpret_cast<float4*>(extra + (half * 2 + (c0 >> 5)) * 16384 + row * 128);
-          const int q0 = (c0 & 31) >> 2;
-#pragma unroll
-          for (int qq = 0; qq < 4; ++qq) {
-            float4 x;
-            x.x = half ? val[qq * 4].y : val[qq * 4].x;
-            x.y = half ? val[qq * 4 + 1].y : val[qq * 4 + 1].x;
-            x.z = half ? val[qq * 4 + 2].y : val[qq * 4 + 2].x;
-            x.w = half ? val[qq * 4 + 3].y : val[qq * 4 + 3].x;
-            rowp[(q0 + qq) ^ sw] = x;
-          }
-        }
+    for (int hc = 0; hc < 2; ++hc) {
+      // bounded wait for this half (phase hc), also when the main loop gave
+      // up, so that no copy into shared memory is in flight when the CTA exits
+      bool ok = false;
+      for (long long it = 0; it < tc::kWaitLimit && !ok; ++it) ok = tc::mbar_try_wait(bar, (uint32_t)hc);
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(status, (int)DEV_TIMEOUT);
       }
-    } else {
-      // pivot rows of this tile: S[i, j] = T[j, i - k0], staged in shared
-      // memory (the free pipeline stage) with coalesced loads
-      f2* Ts = reinterpret_cast<f2*>(stage);   // [64 columns j][64]
-      if (rowsK) {
-        const float4* src = reinterpret_cast<const float4*>(T + (long long)tn * 64 * kPanel);
-        float4* dstp = reinterpret_cast<float4*>(Ts);
-        const int rows_avail = min(64, n - tn * 64);
-        for (int t = ept; t < 64 * kPanel / 2; t += 128)
-          dstp[t] = (t / (kPanel / 2) < rows_avail) ? src[t] : make_float4(0.f, 0.f, 0.f, 0.f);
-        tc::epilogue_sync();
+      tc::epilogue_sync();   // also: Ts staged
+      if (*abort_flag) {   // uniform: read after the barrier
+        if (ept == 0) tc::bulk_wait();   // the first half's stores, if any
+        return;
       }
 #pragma unroll 1
-      for (int half = 0; half < 2; ++half) {
-#pragma unroll 1
-        for (int c0 = 0; c0 < 64; c0 += 16) {
-          float v[16];
-          tc::tmem_ld16(taddr + half * 64 + c0, v);
-          float4* rowp = reinterpret_cast<float4*>(extra + (half * 2 + (c0 >> 5)) * 16384 + row * 128);
-          const int q0 = (c0 & 31) >> 2;
+      for (int c0 = hc * 32; c0 < hc * 32 + 32; c0 += 16) {
+        const int q0 = (c0 & 31) >> 2;
+        if (strip) {
+          // row i: T[i, :] (or -Pinv[i - k0, :] on the pivot rows), 16 columns at a time
+          f2 val[16];
+          if (iok) {
+            const float4* src = reinterpret_cast<const float4*>(inI ? Pi + (long long)(i - k0) * kPanel + c0
+                                                                    : T + (long long)i * kPanel + c0);
+            float4 q[8];
 #pragma unroll
-          for (int qq = 0; qq < 4; ++qq) {
-            float4 cur = rowp[(q0 + qq) ^ sw];
-            float* cv = reinterpret_cast<float*>(&cur);
+            for (int u = 0; u < 8; ++u) q[u] = src[u];
 #pragma unroll
-            for (int t4 = 0; t4 < 4; ++t4) {
-              const int t = qq * 4 + t4;
-              if (inI) {
-                const f2 t2 = Ts[(c0 + t) * kPanel + (i - k0)];
-                cv[t4] = half ? t2.y : t2.x;
-              } else {
-                cv[t4] -= v[t];
-              }
+            for (int u = 0; u < 8; ++u) {
+              val[2 * u] = f2{q[u].x, q[u].y};
+              val[2 * u + 1] = f2{q[u].z, q[u].w};
             }
-            rowp[(q0 + qq) ^ sw] = cur;
+            if (inI)
+#pragma unroll
+              for (int t = 0; t < 16; ++t) val[t] = f2{-val[t].x, -val[t].y};
+          } else {
+#pragma unroll
+            for (int t = 0; t < 16; ++t) val[t] = f2{0.f, 0.f};
           }
-        }
-      }
-    }
-    tc::fence_proxy_async_smem();
-    tc::epilogue_sync();
-    if (ept == 0) {
 #pragma unroll
-      for (int b = 0; b < 4; ++b) tc::tma_store_3d(&mapF, extra + b * 16384, box_x(b, tn), tm * tc::kBlockM, e * 2 + plane);
-      tc::bulk_commit();
-      tc::bulk_wait_read();
-    }
-    if (last) {
-      tc::epilogue_sync();   // the working-copy stores have read the tile
-      // each box row (32 K-columns, 16-byte chunk c at c ^ sw) becomes its
-      // split bf16 pairs: chunks 0-3 the leading parts, 4-7 the trailing
+          for (int part = 0; part < 2; ++part) {
+            float4* rowp = reinterpret_cast<float4*>(extra + part * 16384 + row * 128);
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+              float4 x;
+              x.x = part ? val[qq * 4].y : val[qq * 4].x;
+              x.y = part ? val[qq * 4 + 1].y : val[qq * 4 + 1].x;
+              x.z = part ? val[qq * 4 + 2].y : val[qq * 4 + 2].x;
+              x.w = part ? val[qq * 4 + 3].y : val[qq * 4 + 3].x;
+              rowp[(q0 + qq) ^ sw] = x;
+            }
+          }
+        } else {
 #pragma unroll 1
-      for (int b = 0; b < 4; ++b) {
-        uint4* rowp = reinterpret_cast<uint4*>(extra + b * 16384 + row * 128);
-        float x[32];
+          for (int part = 0; part < 2; ++part) {
+            float v[16];
+            tc::tmem_ld16(taddr + part * 64 + c0, v);
+            float4* rowp = reinterpret_cast<float4*>(extra + part * 16384 + row * 128);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const uint4 u = rowp[c ^ sw];
-          x[4 * c] = __uint_as_float(u.x);
-          x[4 * c + 1] = __uint_as_float(u.y);
-          x[4 * c + 2] = __uint_as_float(u.z);
-          x[4 * c + 3] = __uint_as_float(u.w);
-        }
+            for (int qq = 0; qq < 4; ++qq) {
+              float4 cur = rowp[(q0 + qq) ^ sw];
+              float* cv = reinterpret_cast<float*>(&cur);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          uint4 h, l;
-          tc::split2(x[8 * c], x[8 * c + 1], h.x, l.x);
-          tc::split2(x[8 * c + 2], x[8 * c + 3], h.y, l.y);
-          tc::split2(x[8 * c + 4], x[8 * c + 5], h.z, l.z);
-          tc::split2(x[8 * c + 6], x[8 * c + 7], h.w, l.w);
-          rowp[c ^ sw] = h;
-          rowp[(4 + c) ^ sw] = l;
+              for (int t4 = 0; t4 < 4; ++t4) {
+                const int t = qq * 4 + t4;
+                if (inI) {
+                  const f2 t2 = Ts[(c0 + t) * kPanel + (i - k0)];
+                  cv[t4] = part ? t2.y : t2.x;
+                } else {
+                  cv[t4] -= v[t];
+                }
+              }
+              rowp[(q0 + qq) ^ sw] = cur;
+            }
+          }
         }
       }
       tc::fence_proxy_async_smem();
       tc::epilogue_sync();
       if (ept == 0) {
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-          tc::tma_store_3d(&mapFr, extra + b * 16384, box_x(b, tn), tm * tc::kBlockM,
-                           node_of(ch, e) * nz + ch.layer[chain_of(ch, e)]);
+        for (int part = 0; part < 2; ++part)
+          tc::tma_store_3d(&mapF, extra + part * 16384, box_x(part, hc, tn), tm * tc::kBlockM, e * 2 + plane);
         tc::bulk_commit();
+        tc::bulk_wait_read();
+      }
+      if (last) {
+        tc::epilogue_sync();   // the working-copy stores have read the half
+        // each box row (32 K-columns, 16-byte chunk c at c ^ sw) becomes its
+        // split bf16 pairs: chunks 0-3 the leading parts, 4-7 the trailing
+#pragma unroll 1
+        for (int part = 0; part < 2; ++part) {
+          uint4* rowp = reinterpret_cast<uint4*>(extra + part * 16384 + row * 128);
+          float x[32];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const uint4 u = rowp[c ^ sw];
+            x[4 * c] = __uint_as_float(u.x);
+            x[4 * c + 1] = __uint_as_float(u.y);
+            x[4 * c + 2] = __uint_as_float(u.z);
+            x[4 * c + 3] = __uint_as_float(u.w);
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            uint4 h, l;
+            tc::split2(x[8 * c], x[8 * c + 1], h.x, l.x);
+            tc::split2(x[8 * c + 2], x[8 * c + 3], h.y, l.y);
+            tc::split2(x[8 * c + 4], x[8 * c + 5], h.z, l.z);
+            tc::split2(x[8 * c + 6], x[8 * c + 7], h.w, l.w);
+            rowp[c ^ sw] = h;
+            rowp[(4 + c) ^ sw] = l;
+          }
+        }
+        tc::fence_proxy_async_smem();
+        tc::epilogue_sync();
+        if (ept == 0) {
+#pragma unroll
+          for (int part = 0; part < 2; ++part)
+            tc::tma_store_3d(&mapFr, extra + part * 16384, box_x(part, hc, tn), tm * tc::kBlockM,
+                             node_of(ch, e) * nz + ch.layer[chain_of(ch, e)]);
+          tc::bulk_commit();
+          tc::bulk_wait_read();
+        }
+      }
+      if (hc == 0) {
+        // the stores have read the first half (thread 0 waited above): the
+        // second half reuses its shared memory
+        tc::epilogue_sync();
+        if (ept == 0) load_half(1, e, tm, tn, extra, bar);
       }
     }
     if (ept == 0) tc::bulk_wait();
