@@ -50,7 +50,7 @@ TRAFFIC = {
     "solve_gemm": (167.9 + 3.0) * 1e6,
     # wide sweep update: 15 regular launches and the last panel's (which also
     # writes the solve copy) per layer
-    "sweep_gemm": (15 * (158.4 + 68.5) + (168.0 + 208.1)) / 16 * 1e6,
+    "sweep_gemm": (15 * (160.2 + 67.7) + (176.3 + 207.2)) / 16 * 1e6,
     "fp64_residual": (426.6 + 365.0) * 1e6 * 400 / 24,
     # the later (incremental) residuals
     "ff_residual": (646.6 + 353.8) * 1e6 * 400 / 24,
