@@ -50,6 +50,7 @@ constexpr int kPanel = 64;   // sweep panel width (complex columns)
 #endif
 // rows per CTA of the panel product (each CTA stages the 64 x 64 inverse)
 constexpr int kRowsPerPanelCta = FEAST_PANEL_ROWS;
+static_assert(kRowsPerPanelCta % 8 == 0, "eight row groups of the panel product");
 
 struct f2 {
   float x, y;
@@ -470,36 +471,45 @@ __global__ void __launch_bounds__(256) k_mx_panel_T(Dims d, int plane, int k0, i
     Ls[r][m] = x;
   }
   __syncthreads();
-  // thread -> column c, rows r0 + rq + 4q (q < kRowsPerPanelCta / 4): the
-  // Pinv loads of a warp are 32 consecutive entries, the L loads a broadcast
-  constexpr int kRowsPerThread = kRowsPerPanelCta / 4;
-  const int c = tid % kPanel, rq = tid / kPanel;
-  f2 acc[kRowsPerThread];
+  // thread -> columns c and c + 32, rows r0 + rq + 8q (q < kRowsPerPanelCta
+  // / 8): per m two Pinv loads (32 consecutive entries a warp) and one L
+  // broadcast per row feed four complex FMAs
+  constexpr int kRowsPerThread = kRowsPerPanelCta / 8;
+  const int c = tid % 32, rq = tid / 32;
+  f2 acc[kRowsPerThread][2];
 #pragma unroll
-  for (int q = 0; q < kRowsPerThread; ++q) acc[q] = f2{0.f, 0.f};
+  for (int q = 0; q < kRowsPerThread; ++q) acc[q][0] = acc[q][1] = f2{0.f, 0.f};
 #pragma unroll 8
   for (int m = 0; m < kPanel; ++m) {
-    const f2 pv = Ps[m][c];
+    const f2 pv0 = Ps[m][c], pv1 = Ps[m][c + 32];
 #pragma unroll
-    for (int q = 0; q < kRowsPerThread; ++q) f2fma(acc[q], Ls[rq + 4 * q][m], pv);
+    for (int q = 0; q < kRowsPerThread; ++q) {
+      const f2 l = Ls[rq + 8 * q][m];
+      f2fma(acc[q][0], l, pv0);
+      f2fma(acc[q][1], l, pv1);
+    }
   }
 #pragma unroll
   for (int q = 0; q < kRowsPerThread; ++q) {
-    const int r = rq + 4 * q;
+    const int r = rq + 8 * q;
     const int i = r0 + r;
     if (i >= n) continue;
     float* arow = Aop + ((long long)e * n + i) * (2 * kPanel);
-    store_factor_op(arow, c, acc[q].x);
-    store_factor_op(arow, kPanel + c, acc[q].y);
-    Tc[((long long)e * n + i) * kPanel + c] = acc[q];
     const long long brow = ((long long)e * d.nblk64 + i / 64) * 128 + (i % 64);
     float* bre = Bop + brow * (2 * kPanel);
     float* bim = Bop + (brow + 64) * (2 * kPanel);
-    const f2 l = Ls[r][c];
-    store_factor_op(bre, c, l.x);
-    store_factor_op(bre, kPanel + c, -l.y);
-    store_factor_op(bim, c, l.y);
-    store_factor_op(bim, kPanel + c, l.x);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int cc = c + 32 * h;
+      store_factor_op(arow, cc, acc[q][h].x);
+      store_factor_op(arow, kPanel + cc, acc[q][h].y);
+      Tc[((long long)e * n + i) * kPanel + cc] = acc[q][h];
+      const f2 l = Ls[r][cc];
+      store_factor_op(bre, cc, l.x);
+      store_factor_op(bre, kPanel + cc, -l.y);
+      store_factor_op(bim, cc, l.y);
+      store_factor_op(bim, kPanel + cc, l.x);
+    }
   }
 }
 
