@@ -63,6 +63,13 @@ typedef enum {
   FEAST_ERR_NONFINITE = 10       /* a predicted start block holds a non-finite value */
 } feast_status;
 
+/* Precision of the node solves (Fig. 2 step 2).
+ * FEAST_PREC_FP64: block factor and solves in FP64.
+ * FEAST_PREC_MIXED: block factor and solves on the tensor cores with split
+ *   bf16 pair operands (x = bf16(x) + bf16(remainder), 16 significant bits;
+ *   fp32 elsewhere), refined in FP64 / double-float until each node's
+ *   relative residual meets options.ir_tol; right-hand side, Gram products
+ *   and Q*Phi in double-float; reduced eigensolve and final residuals in FP64. */
 enum { FEAST_PREC_FP64 = 0, FEAST_PREC_MIXED = 1 };
 
 /*
