@@ -4,7 +4,7 @@
 // Factor: the same unpivoted block elimination as the FP64 path (Schur
 // complements through the layer couplings, symmetric block sweep inversion
 // S'_i = -S_i^{-1}), carried in fp32 complex.  The sweep's trailing updates
-// S[i, j] -= sum_k T[i, k] L[j, k] (panel width 64) run as one real TF32 GEMM
+// S[i, j] -= sum_k T[i, k] L[j, k] (panel width 64) run as one real GEMM
 // on tcgen05 through the real embedding
 //   [Ur | Ui] = [Tr | Ti] [[Lr^T, Li^T], [-Li^T, Lr^T]],
 // and so do the block solves t = S' g, with both operands as split bf16
@@ -251,7 +251,8 @@ struct LeafOut {
 };
 
 // 1/a for complex fp32 with scaling, from approximate reciprocals (a couple
-// of ulp, far below the TF32 rounding the factors are used at): on the panel
+// of ulp, far below the 2^-17 of the split bf16 pairs the factors are used
+// as): on the panel
 // inverse's critical path every pivot waits for one of these.
 __device__ __forceinline__ f2 f2inv_fast(f2 a) {
   const float rs = __fdividef(1.0f, fmaxf(fabsf(a.x), fabsf(a.y)));
@@ -805,8 +806,10 @@ __device__ __forceinline__ double f32_to_f64(float x) {
 
 // fp64 -> fp32 by truncation of the mantissa, on the integer pipe: for the
 // complex64 copy of the FP64 refinement residual (whose FP64 pipe is its
-// bound), which only feeds the next correction's right-hand side (rounded
-// to TF32 there), so a one-ulp truncation error is immaterial.  (The
+// bound): the truncated value is the leading part of the resident residual
+// pair, whose trailing part takes the remainder (so the pair still holds R
+// to about 2^-47), and it feeds the next correction's right-hand side as
+// split bf16 pairs (16 bits), where a one-ulp truncation is immaterial.  (The
 // double-float residual and the couplings keep the conversion instructions:
 // they are bound by instruction issue, where the integer sequence costs more.)  Magnitudes below 2^-126 become a signed
 // zero, above the fp32 range an infinity; NaN stays NaN.

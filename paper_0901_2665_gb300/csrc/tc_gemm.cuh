@@ -1,7 +1,8 @@
-// tcgen05 TF32 GEMM for sm_103a: D (128 x BN per CTA, fp32 in TMEM) =
-// sum_k A[m, k] B[n, k] with A and B K-major fp32 operands loaded by TMA into
+// tcgen05 GEMM for sm_103a: D (128 x BN per CTA, fp32 in TMEM) =
+// sum_k A[m, k] B[n, k] with A and B K-major operands loaded by TMA into
 // 128-byte-swizzled shared memory, one elected thread issuing
-// tcgen05.mma.kind::tf32 (M = 128, N = BN, K = 8 per instruction), and a
+// tcgen05.mma (M = 128, N = BN; kind::tf32 on fp32 operands, kind::f16 on
+// BF16 operands or on split BF16 pairs, see KIND below), and a
 // caller-supplied epilogue that reads the accumulator back with tcgen05.ld.
 //
 // Warp roles (192 threads): warp 0 = TMA producer, warp 1 = TMEM owner and
